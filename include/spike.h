@@ -1,0 +1,154 @@
+/*
+ * spike.h -- C ABI of libspike.so, a GB300-native recursive SPIKE banded solver.
+ *
+ * Problem (Sec. 2.1): find X in  A X = F  or  A^T X = F  (Sec. 4), where A is an
+ * n x n band matrix with kl sub- and ku super-diagonals and F, X are n x nrhs.
+ * A is partitioned into p diagonal blocks A_i with couplings B_i / C_i
+ * (Sec. 2.1, Eq. "partitioning"), factored as A = D S (Eq. "spikes"), the
+ * reduced system is solved recursively (Sec. 2.2) for any worker count p
+ * (Sec. 3: 2^m partitions, r of them split in two and run as a SPIKE 2x2 pair),
+ * and the factorization is reused for the transpose solve (Sec. 4).  Blocks are
+ * factored without pivoting (LU, UL for the last block, with diagonal
+ * boosting, Sec. 2.3) or with partial pivoting (Sec. 5.1, UL via Q A Q, Sec. 5.2).
+ *
+ * Storage conventions (all column-major, 0-based, FP64):
+ *   band : A(i,j) at band[j*ldab + ku + i - j] for max(0,j-ku) <= i <= min(n-1,j+kl)
+ *          (the LAPACK band layout; ldab >= kl+ku+1).  Other entries are ignored.
+ *   F    : F(i,c) at F[c*ldf + i], ldf >= n.  Overwritten by X.
+ * Pointers may be device memory or host memory (pageable or pinned); host
+ * buffers are staged through device memory inside the call.
+ *
+ * Return codes: 0 on success.  -i: argument i is invalid (LAPACK info style,
+ * arguments counted from 1).  SPIKE_E* (below): allocation, CUDA or internal
+ * failures.  A positive value i from spike_factor in pivoting mode means the
+ * pivot candidates of global column i-1 were all exactly zero (A singular);
+ * the handle is still returned and spike_solve on it returns the same i.
+ *
+ * Threading: a handle may be used by one host thread at a time.  All GPU work
+ * of a handle is issued on its stream (spike_set_stream / options.stream).
+ */
+#ifndef SPIKE_H_
+#define SPIKE_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPIKE_OK 0
+#define SPIKE_ENOMEM (-1001)   /* device or host allocation failed */
+#define SPIKE_ECUDA (-1002)    /* a CUDA call failed (message via spike_last_cuda_error) */
+#define SPIKE_EHANDLE (-1003)  /* NULL or freed handle */
+#define SPIKE_ENOTSUP (-1004)  /* unsupported combination (e.g. bandwidth above the library limit) */
+#define SPIKE_ENOGPU (-1005)   /* no CUDA device available */
+
+/* Largest half-bandwidth max(kl, ku) the kernels accept. */
+#define SPIKE_MAX_K 512
+
+typedef struct spike_ctx *spike_handle;
+
+/* Options for spike_factor_ex / spike_plan.  Zero-initialise for defaults. */
+typedef struct {
+  /* Machine constant K = K2/K1 of the load-balancing model (Sec. 3.3, Eq.
+   * R13_calculation): solve cost per row and RHS column over factor cost per row
+   * and band column.  <= 0 selects 2.0, the value for kernels whose factor and
+   * sweep steps run at the same FP64 rate (one k x k update per factored column
+   * versus one k-wide update per column of a two-sweep solve). */
+  double K;
+  /* Expected nrhs used to size partitions (n_rhs/k in Eqs. R13/R12_calculation).
+   * 0 selects the factorization-dominated limit n_rhs/k -> 0 (Eq. ratiof). */
+  int32_t nrhs_hint;
+  int32_t reserved0;
+  /* cudaStream_t for all work of the handle; NULL = the legacy default stream. */
+  void *stream;
+  int64_t reserved[4];
+} spike_options;
+
+/* Description of a partition plan / factorization. */
+typedef struct {
+  int64_t n;
+  int32_t kl, ku, k;        /* k = max(kl, ku): couplings are padded to k x k (Sec. 2.1) */
+  int32_t p_requested;      /* worker count t asked for */
+  int32_t p_effective;      /* t actually used (t = 2^(m+1)-1 runs as 2^(m+1)-2, Sec. 3.1; lowered
+                               further if a block would be shorter than 2k rows) */
+  int32_t m;                /* P = 2^m partitions (Sec. 3.1) */
+  int32_t P;
+  int32_t r;                /* partitions 2..r+1 (1-based) are split into a SPIKE 2x2 pair */
+  int32_t leaves;           /* P + r blocks actually factored (one GPU CTA each) */
+  int32_t levels;           /* merge levels of the reduced system (1 for the 2x2 pairs if r>0, plus m) */
+  int32_t pivot;
+  int64_t n1, n2, n3;       /* sizes of first/last, 2x2 and single inner partitions (Sec. 3.3) */
+  double R12, R13;          /* balance ratios used (Eqs. R12/R13_calculation) */
+  double K;                 /* balance constant used */
+  int64_t boosts;           /* non-pivoting mode: number of boosted (near-zero) pivots (Sec. 2.3) */
+  int64_t zero_pivot_col;   /* pivoting mode: 1-based global column of the first all-zero pivot column, 0 if none */
+  int64_t device_bytes;     /* device memory held by the handle */
+} spike_info;
+
+/* Compute the partition plan for (n, kl, ku, p) without touching a GPU (Sec. 3.1, 3.3).
+ * leaf_offsets (may be NULL) receives leaves+1 entries: block b covers global rows
+ * [leaf_offsets[b], leaf_offsets[b+1]).  leaf_flags (may be NULL) receives one int per
+ * block: bit0 = factored as UL (reversed LU), bit1 = top half of a 2x2 pair,
+ * bit2 = bottom half of a 2x2 pair.  Arrays must hold at least p+1 entries.
+ * Returns 0 or -i for an invalid argument i. */
+int spike_plan(int64_t n, int kl, int ku, int p, const spike_options *opt, spike_info *out,
+               int64_t *leaf_offsets, int32_t *leaf_flags);
+
+/* Factor A (Sec. 2.1-2.3, 3, 5).  band: device or host pointer, layout above with
+ * ldab = kl+ku+1, read-only, owned by the caller, only read during the call.
+ * p: worker count (>= 1).  pivot: 0 = non-pivoting LU/UL with diagonal boosting,
+ * 1 = partial pivoting.  On success *out receives a new handle (free with
+ * spike_free).  The call blocks until the factorization is complete. */
+int spike_factor(const double *band, int64_t n, int kl, int ku, int p, int pivot, spike_handle *out);
+
+/* As spike_factor with an explicit leading dimension ldab >= kl+ku+1 and options
+ * (opt may be NULL). */
+int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int kl, int ku, int p, int pivot,
+                    const spike_options *opt, spike_handle *out);
+
+/* Overwrite F (n x nrhs, ldf = n) with X solving A X = F (trans 'N') or A^T X = F
+ * (trans 'T'), reusing the factorization (Sec. 4).  F: device or host pointer owned
+ * by the caller.  For device F the call is asynchronous on the handle's stream;
+ * for host F it returns after X has been copied back. */
+int spike_solve(spike_handle h, double *F, int nrhs, char trans);
+
+/* As spike_solve with an explicit leading dimension ldf >= n. */
+int spike_solve_ex(spike_handle h, double *F, int64_t ldf, int nrhs, char trans);
+
+/* Set the cudaStream_t used by the handle (NULL = legacy default stream). */
+int spike_set_stream(spike_handle h, void *stream);
+
+/* Describe a handle (plan, boosts, zero pivot, memory). */
+int spike_get_info(spike_handle h, spike_info *out);
+
+/* Copy the k x k spike tips of merge level `level` (0 = the blocks' own spikes,
+ * Eq. "spikes") to host memory: leaves x {V_t, V_b, W_t, W_b} x k x k, row-major
+ * per tip.  Tips that the method never forms (V_t of the first block, W_b of the
+ * last, and V / W of groups that contain the last / first block) read as zero.
+ * For inspection and tests. */
+int spike_get_tips(spike_handle h, int level, double *host_dst);
+
+/* Backward error of a computed solution, on the GPU in FP64 from the ORIGINAL
+ * band (device pointer, ldab >= kl+ku+1): for each column c,
+ *   berr[c] = ||op(A) x_c - f_c||_inf / (||op(A)||_inf * ||x_c||_inf).
+ * X, F: device pointers, n x nrhs with leading dimension n.  berr: host array of
+ * nrhs doubles.  Uses the stream of `stream` (NULL = legacy default) and
+ * synchronises it before returning.  Allocates a small device scratch buffer. */
+int spike_backward_error(const double *band, int64_t ldab, int64_t n, int kl, int ku, const double *X,
+                         const double *F, int nrhs, char trans, void *stream, double *berr);
+
+/* Release a handle and all its device memory.  NULL is ignored. */
+void spike_free(spike_handle h);
+
+/* Static description of a return code. */
+const char *spike_strerror(int code);
+
+/* Text of the last CUDA error seen by the calling thread inside the library. */
+const char *spike_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPIKE_H_ */

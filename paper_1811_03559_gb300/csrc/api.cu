@@ -1,0 +1,1045 @@
+// C ABI of libspike.so: handle lifecycle, workspace and the launch pipelines of
+// the factorization (Sec. 2.1-2.3, 3, 5) and of the N / T solves (Sec. 2.1, 2.2, 4).
+//
+// Frames: every vector (F, X, the scratch H and the reduced right-hand sides Y)
+// is stored in the GLOBAL row order; each leaf kernel reads its block through a
+// view whose row stride is -1 for the reversed (UL) blocks.  Spike tips and the
+// reduced unknowns are always in global orientation.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstring>
+#include <functional>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace spk;
+
+namespace {
+
+thread_local std::string g_cuda_err;
+
+#define SP_CUDA(x)                                                       \
+  do {                                                                   \
+    cudaError_t e_ = (cudaError_t)(x);                                   \
+    if (e_ != cudaSuccess) {                                             \
+      g_cuda_err = std::string(#x) + ": " + cudaGetErrorString(e_);      \
+      return SPIKE_ECUDA;                                                \
+    }                                                                    \
+  } while (0)
+
+#define SP_TRY(x)                      \
+  do {                                 \
+    int r_ = (x);                      \
+    if (r_ != 0) return r_;            \
+  } while (0)
+
+constexpr uint32_t kMagic = 0x5350494bu;  // "SPIK"
+constexpr double kBoostEps = 1.4901161193847656e-08;  // 2^-26: boost threshold relative to max|a_ij|
+
+// Host-side arena of descriptors: everything a pipeline launches is laid out
+// here, uploaded once, and referenced by offset.
+struct Arena {
+  std::vector<char> h;
+  template <typename T>
+  size_t put(const std::vector<T> &v) {
+    size_t off = (h.size() + 255) & ~size_t(255);
+    h.resize(off + v.size() * sizeof(T));
+    if (!v.empty()) memcpy(h.data() + off, v.data(), v.size() * sizeof(T));
+    return off;
+  }
+};
+
+// A batch of GEMM descriptors with tile bookkeeping.
+struct GemmBatch {
+  std::vector<GemmDesc> d;
+  int tiles = 0;
+  void add(GemmDesc g) {
+    if (g.M <= 0 || g.N <= 0) return;
+    g.tiles_n = (g.N + GEMM_TILE - 1) / GEMM_TILE;
+    g.tile0 = tiles;
+    tiles += ((g.M + GEMM_TILE - 1) / GEMM_TILE) * g.tiles_n;
+    d.push_back(g);
+  }
+};
+
+GemmDesc gd(const double *A, int64_t a_rs, int64_t a_cs, const double *B, int64_t b_rs, int64_t b_cs,
+            const double *C0, int64_t c0_rs, int64_t c0_cs, double *C, int64_t c_rs, int64_t c_cs, int M, int N,
+            int K, double alpha, double beta) {
+  GemmDesc g;
+  memset(&g, 0, sizeof(g));
+  g.A = A;
+  g.a_rs = a_rs;
+  g.a_cs = a_cs;
+  g.B = B;
+  g.b_rs = b_rs;
+  g.b_cs = b_cs;
+  g.C0 = C0;
+  g.c0_rs = c0_rs;
+  g.c0_cs = c0_cs;
+  g.C = C;
+  g.c_rs = c_rs;
+  g.c_cs = c_cs;
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.alpha = alpha;
+  g.beta = beta;
+  return g;
+}
+
+struct TrsBatch {
+  std::vector<TrsDesc> d;
+  int tiles = 0, maxn = 0;
+  void add(const double *lu, const int *ipiv, int n, int lda, double *b, int64_t ldb, int ncols, int trans,
+           double alpha) {
+    if (ncols <= 0) return;
+    TrsDesc t;
+    memset(&t, 0, sizeof(t));
+    t.lu = lu;
+    t.ipiv = ipiv;
+    t.n = n;
+    t.lda = lda;
+    t.b = b;
+    t.ldb = ldb;
+    t.ncols = ncols;
+    t.trans = trans;
+    t.alpha = alpha;
+    t.tile0 = tiles;
+    tiles += (ncols + 15) / 16;
+    maxn = std::max(maxn, n);
+    d.push_back(t);
+  }
+};
+
+}  // namespace
+
+struct spike_ctx {
+  uint32_t magic = kMagic;
+  Plan pl;
+  int k = 0, ldf = 0, dofs = 0, pivot = 0, NL = 0, nleaves = 0;
+  cudaStream_t stream = nullptr;
+  // persistent device memory (one allocation, carved)
+  char *mem = nullptr;
+  size_t mem_bytes = 0;
+  double *fb = nullptr, *dinv = nullptr, *couple = nullptr, *spk = nullptr, *mlu = nullptr, *ident = nullptr;
+  int *ipiv = nullptr, *mpiv = nullptr;
+  unsigned long long *status = nullptr;
+  std::vector<LeafDev> hl;
+  std::vector<int64_t> merge_off;         // first merge index of each level
+  std::vector<std::vector<int>> schur;    // per level, per merge: 1 = Schur-complement path
+  int total_merges = 0;
+  int64_t boosts = 0, zero_col = 0;
+  int nan_flag = 0;
+  // solve scratch (grown on demand)
+  char *scr = nullptr;
+  size_t scr_bytes = 0;
+  char *dargs = nullptr;
+  size_t dargs_bytes = 0;
+};
+
+static bool valid(spike_handle h) { return h && h->magic == kMagic; }
+
+static int ensure(char **p, size_t *cap, size_t need, cudaStream_t s) {
+  if (need <= *cap) return 0;
+  if (*p) SP_CUDA(cudaFreeAsync(*p, s));
+  *p = nullptr;
+  *cap = 0;
+  size_t want = need + need / 4 + 4096;
+  cudaError_t e = cudaMallocAsync((void **)p, want, s);
+  if (e != cudaSuccess) {
+    g_cuda_err = std::string("cudaMallocAsync: ") + cudaGetErrorString(e);
+    *p = nullptr;
+    return SPIKE_ENOMEM;
+  }
+  *cap = want;
+  return 0;
+}
+
+static bool is_device_ptr(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// pointer into the spike-tip store: level lv, spike s (0 V, 1 W), leaf i, tip t (0 top, 1 bottom)
+static inline double *TIP(spike_ctx *c, int lv, int s, int i, int t) {
+  return c->spk + tip_index(lv, s, i, t, c->nleaves, c->k);
+}
+
+static void fill_info(const Plan &pl, spike_info *o) {
+  memset(o, 0, sizeof(*o));
+  o->n = pl.n;
+  o->kl = pl.kl;
+  o->ku = pl.ku;
+  o->k = pl.k;
+  o->p_requested = pl.t_req;
+  o->p_effective = pl.t_eff;
+  o->m = pl.m;
+  o->P = pl.P;
+  o->r = pl.r;
+  o->leaves = pl.nleaves;
+  o->levels = (int)pl.levels.size();
+  o->pivot = pl.pivot;
+  o->n1 = pl.n1;
+  o->n2 = pl.n2;
+  o->n3 = pl.n3;
+  o->R12 = pl.R12;
+  o->R13 = pl.R13;
+  o->K = pl.K;
+}
+
+static int map_plan_rc(int rc) {
+  // make_plan: -1 n, -2 kl, -3 ku, -4 t  ->  ABI argument positions of spike_factor_ex
+  switch (rc) {
+    case -1: return -3;
+    case -2: return -4;
+    case -3: return -5;
+    case -4: return -6;
+    default: return rc;
+  }
+}
+
+extern "C" int spike_plan(int64_t n, int kl, int ku, int p, const spike_options *opt, spike_info *out,
+                          int64_t *leaf_offsets, int32_t *leaf_flags) {
+  if (!out) return -6;
+  Plan pl;
+  const int rc = make_plan(n, kl, ku, p, opt ? opt->K : 0.0, opt ? opt->nrhs_hint : 0, pl);
+  if (rc != 0) return rc;  // -1 n, -2 kl, -3 ku, -4 p, or SPIKE_ENOTSUP
+  fill_info(pl, out);
+  for (int i = 0; i < pl.nleaves; ++i) {
+    if (leaf_offsets) leaf_offsets[i] = pl.leaves[i].start;
+    if (leaf_flags)
+      leaf_flags[i] = (pl.leaves[i].rev ? 1 : 0) | (pl.leaves[i].half == 1 ? 2 : 0) | (pl.leaves[i].half == 2 ? 4 : 0);
+  }
+  if (leaf_offsets) leaf_offsets[pl.nleaves] = n;
+  return 0;
+}
+
+// view of leaf i's rows of a global-frame column-major array (local row 0 first)
+struct View {
+  double *p;
+  int64_t rs, cs;
+};
+static View leaf_view(const LeafDev &L, double *base, int64_t ld) {
+  if (L.rev) return View{base + L.start + L.len - 1, -1, ld};
+  return View{base + L.start, 1, ld};
+}
+
+static SweepDesc sdesc(spike_ctx *c, int i, int r0, int r1, int ncols, View g, const double *gb, View gbv,
+                       double gbs, View x) {
+  const LeafDev &L = c->hl[i];
+  SweepDesc d;
+  memset(&d, 0, sizeof(d));
+  d.fb = c->fb + L.start * (int64_t)c->ldf;
+  d.dinv = c->dinv + L.start;
+  d.ipiv = c->ipiv ? c->ipiv + L.start : nullptr;
+  d.nl = L.len;
+  d.r0 = r0;
+  d.r1 = r1;
+  d.ncols = ncols;
+  d.ga = g.p;
+  d.ga_rs = g.rs;
+  d.ga_cs = g.cs;
+  d.gb = gb;
+  d.gb_rs = gbv.rs;
+  d.gb_cs = gbv.cs;
+  d.gb_scale = gbs;
+  d.x = x.p;
+  d.x_rs = x.rs;
+  d.x_cs = x.cs;
+  return d;
+}
+
+// Upload an arena and run the recorded launches.
+struct Pipeline {
+  cudaStream_t st = nullptr;
+  Arena ar;
+  std::vector<std::function<int(char *)>> ops;
+  int run(spike_ctx *c) {
+    if (!ar.h.empty()) {
+      SP_TRY(ensure(&c->dargs, &c->dargs_bytes, ar.h.size(), c->stream));
+      SP_CUDA(cudaMemcpyAsync(c->dargs, ar.h.data(), ar.h.size(), cudaMemcpyHostToDevice, c->stream));
+    }
+    for (auto &op : ops) {
+      const int rc = op(c->dargs);
+      if (rc != 0) {
+        g_cuda_err = std::string("kernel launch: ") + cudaGetErrorString((cudaError_t)rc);
+        return SPIKE_ECUDA;
+      }
+    }
+    return 0;
+  }
+  void gemm(GemmBatch &b) {
+    if (b.d.empty()) return;
+    const size_t off = ar.put(b.d);
+    const int nd = (int)b.d.size(), tiles = b.tiles;
+    cudaStream_t s = st;
+    ops.push_back([=](char *base) { return launch_gemm((GemmDesc *)(base + off), nd, tiles, s); });
+  }
+  void sweep(int kind, std::vector<SweepDesc> &v, int kw, int ldf, int dofs, bool piv, int kpiv) {
+    if (v.empty()) return;
+    const size_t off = ar.put(v);
+    const int nd = (int)v.size();
+    cudaStream_t s = st;
+    ops.push_back([=](char *base) {
+      if (piv) return launch_piv_sweep(kind, (SweepDesc *)(base + off), nd, kpiv, ldf, dofs, s);
+      return launch_sweep(kind, (SweepDesc *)(base + off), nd, kw, ldf, dofs, 0, s);
+    });
+  }
+  void trs(TrsBatch &b) {
+    if (b.d.empty()) return;
+    const size_t off = ar.put(b.d);
+    const int nd = (int)b.d.size(), tiles = b.tiles, maxn = b.maxn;
+    cudaStream_t s = st;
+    ops.push_back([=](char *base) { return launch_getrs((TrsDesc *)(base + off), nd, tiles, maxn, s); });
+  }
+};
+
+// ============================================================== factor
+static int factor_reduced_level(spike_ctx *c, int lv, char *tmp, size_t tmp_bytes);
+
+extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int kl, int ku, int p, int pivot,
+                               const spike_options *opt, spike_handle *out) {
+  if (!out) return -9;
+  *out = nullptr;
+  if (!band) return -1;
+  if (n < 1) return -3;
+  if (kl < 0) return -4;
+  if (ku < 0) return -5;
+  if (ldab < (int64_t)kl + ku + 1) return -2;
+  if (p < 1) return -6;
+  if (pivot != 0 && pivot != 1) return -7;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return SPIKE_ENOGPU;
+  }
+  Plan pl;
+  int rc = make_plan(n, kl, ku, p, opt ? opt->K : 0.0, opt ? opt->nrhs_hint : 0, pl);
+  if (rc != 0) return map_plan_rc(rc);
+  pl.pivot = pivot;
+
+  spike_ctx *c = new spike_ctx();
+  c->pl = pl;
+  c->stream = opt ? (cudaStream_t)opt->stream : nullptr;
+  c->k = pl.k;
+  c->pivot = pivot;
+  c->dofs = pivot ? 2 * pl.k : pl.k;
+  c->ldf = (c->dofs + pl.k + 1 + 1) & ~1;
+  c->nleaves = pl.nleaves;
+  c->NL = (int)pl.levels.size();
+  const int k = c->k, nlv = c->nleaves;
+  const int64_t kk = (int64_t)k * k;
+  cudaStream_t s = c->stream;
+
+  auto fail = [&](int code) {
+    spike_free(c);
+    return code;
+  };
+
+  // leaves
+  c->hl.resize(nlv);
+  std::vector<int64_t> zoff(nlv);
+  int64_t zacc = 0, maxlen = 0;
+  for (int i = 0; i < nlv; ++i) {
+    const Leaf &L = pl.leaves[i];
+    LeafDev d;
+    d.start = L.start;
+    d.len = L.len;
+    d.rev = L.rev;
+    d.top_nbr = L.rev ? L.has_next : L.has_prev;
+    d.bot_nbr = L.rev ? L.has_prev : L.has_next;
+    d.pad = 0;
+    c->hl[i] = d;
+    zoff[i] = zacc;
+    zacc += L.len * 2 * (int64_t)k;
+    maxlen = std::max(maxlen, L.len);
+  }
+  int64_t nmerge = 0;
+  c->merge_off.resize(c->NL + 1);
+  for (int lv = 0; lv < c->NL; ++lv) {
+    c->merge_off[lv] = nmerge;
+    nmerge += (int64_t)pl.levels[lv].size();
+  }
+  c->merge_off[c->NL] = nmerge;
+  c->total_merges = (int)nmerge;
+  c->schur.assign(c->NL, {});
+
+  // persistent memory layout
+  const int nspk = std::max(c->NL, 1);
+  size_t off = 0;
+  auto carve = [&](size_t bytes) {
+    size_t o = off;
+    off = (off + bytes + 255) & ~size_t(255);
+    return o;
+  };
+  const size_t o_fb = carve(sizeof(double) * (size_t)n * c->ldf);
+  const size_t o_dinv = carve(sizeof(double) * (size_t)n);
+  const size_t o_ipiv = pivot ? carve(sizeof(int) * (size_t)n) : 0;
+  const size_t o_cpl = carve(sizeof(double) * (size_t)nlv * 2 * kk);
+  const size_t o_spk = carve(sizeof(double) * (size_t)nspk * 2 * nlv * 2 * kk);
+  const size_t o_mlu = carve(sizeof(double) * (size_t)std::max<int64_t>(nmerge, 1) * 4 * kk);
+  const size_t o_mpiv = carve(sizeof(int) * (size_t)std::max<int64_t>(nmerge, 1) * 2 * k);
+  const size_t o_id = carve(sizeof(double) * (size_t)kk);
+  const size_t o_st = carve(sizeof(unsigned long long) * 8);
+  c->mem_bytes = off;
+  {
+    cudaError_t e = cudaMallocAsync((void **)&c->mem, c->mem_bytes, s);
+    if (e != cudaSuccess) {
+      g_cuda_err = std::string("cudaMallocAsync: ") + cudaGetErrorString(e);
+      c->mem = nullptr;
+      return fail(SPIKE_ENOMEM);
+    }
+  }
+  c->fb = (double *)(c->mem + o_fb);
+  c->dinv = (double *)(c->mem + o_dinv);
+  c->ipiv = pivot ? (int *)(c->mem + o_ipiv) : nullptr;
+  c->couple = (double *)(c->mem + o_cpl);
+  c->spk = (double *)(c->mem + o_spk);
+  c->mlu = (double *)(c->mem + o_mlu);
+  c->mpiv = (int *)(c->mem + o_mpiv);
+  c->ident = (double *)(c->mem + o_id);
+  c->status = (unsigned long long *)(c->mem + o_st);
+
+  // factor-time scratch: staged band (host input), Z, per-merge temporaries, arg buffer
+  const bool band_dev = is_device_ptr(band);
+  size_t soff = 0;
+  auto scarve = [&](size_t bytes) {
+    size_t o = soff;
+    soff = (soff + bytes + 255) & ~size_t(255);
+    return o;
+  };
+  const size_t s_band = band_dev ? 0 : scarve(sizeof(double) * (size_t)n * ldab);
+  const size_t s_z = scarve(sizeof(double) * (size_t)zacc);
+  const size_t s_zoff = scarve(sizeof(int64_t) * (size_t)nlv);
+  const size_t s_leaf = scarve(sizeof(LeafDev) * (size_t)nlv);
+  size_t maxm = 1;
+  for (auto &lvv : pl.levels) maxm = std::max(maxm, lvv.size());
+  const size_t s_tmp = scarve(sizeof(double) * maxm * 5 * kk);
+  const size_t tmp_bytes = sizeof(double) * maxm * 5 * kk;
+  char *fscr = nullptr;
+  {
+    cudaError_t e = cudaMallocAsync((void **)&fscr, soff, s);
+    if (e != cudaSuccess) {
+      g_cuda_err = std::string("cudaMallocAsync: ") + cudaGetErrorString(e);
+      return fail(SPIKE_ENOMEM);
+    }
+  }
+  auto fail2 = [&](int code) {
+    cudaFreeAsync(fscr, s);
+    return fail(code);
+  };
+  const double *dband = band;
+  if (!band_dev) {
+    double *b = (double *)(fscr + s_band);
+    if (cudaMemcpyAsync(b, band, sizeof(double) * (size_t)n * ldab, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      g_cuda_err = "cudaMemcpyAsync band";
+      return fail2(SPIKE_ECUDA);
+    }
+    dband = b;
+  }
+  double *zbuf = (double *)(fscr + s_z);
+  int64_t *dzoff = (int64_t *)(fscr + s_zoff);
+  LeafDev *dleaf = (LeafDev *)(fscr + s_leaf);
+  char *tmp = fscr + s_tmp;
+
+  // identity and status init
+  {
+    std::vector<double> id((size_t)kk, 0.0);
+    for (int i = 0; i < k; ++i) id[(size_t)i * k + i] = 1.0;
+    unsigned long long st[8] = {0, ULLONG_MAX, 0, 0, 0, 0, 0, 0};
+    if (cudaMemcpyAsync(c->ident, id.data(), sizeof(double) * kk, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(c->status, st, sizeof(st), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(dzoff, zoff.data(), sizeof(int64_t) * nlv, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(dleaf, c->hl.data(), sizeof(LeafDev) * nlv, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(zbuf, 0, sizeof(double) * (size_t)zacc, s) != cudaSuccess ||
+        cudaMemsetAsync(c->spk, 0, sizeof(double) * (size_t)nspk * 2 * nlv * 2 * kk, s) != cudaSuccess) {
+      g_cuda_err = "initialisation copies";
+      return fail2(SPIKE_ECUDA);
+    }
+  }
+  // 1. repack the band into per-leaf LU storage; couplings; Z right-hand sides
+  if ((rc = launch_repack(dband, ldab, kl, ku, n, k, c->ldf, c->dofs, dleaf, nlv, c->fb, &c->status[3], s,
+                          maxlen)) != 0 ||
+      (rc = launch_couplings(dband, ldab, kl, ku, n, k, dleaf, nlv, c->couple, s)) != 0 ||
+      (rc = launch_zinit(dleaf, nlv, k, c->couple, zbuf, dzoff, pivot, s)) != 0) {
+    g_cuda_err = std::string("setup kernels: ") + cudaGetErrorString((cudaError_t)rc);
+    return fail2(SPIKE_ECUDA);
+  }
+  // 2. block factorizations (+ fused L-sweep of the top spike when not pivoting)
+  rc = pivot ? launch_factor_piv(dleaf, nlv, k, c->ldf, c->fb, c->dinv, c->ipiv, c->status, s)
+             : launch_factor_nopiv(dleaf, nlv, k, c->ldf, c->fb, c->dinv, zbuf, dzoff, &c->status[3], kBoostEps,
+                                   c->status, s);
+  if (rc != 0) {
+    g_cuda_err = std::string("factor kernel: ") + cudaGetErrorString((cudaError_t)rc);
+    return fail2(SPIKE_ECUDA);
+  }
+  // 3. spike sweeps (Sec. 2.3: truncated for the first/last blocks, three full sweeps for middle ones)
+  {
+    Pipeline pp;
+    pp.st = s;
+    std::vector<SweepDesc> ltop, lbot, ub;
+    for (int i = 0; i < nlv; ++i) {
+      const LeafDev &L = c->hl[i];
+      const int nl = (int)L.len;
+      const bool mid = L.top_nbr && L.bot_nbr;
+      View zt{zbuf + zoff[i], 1, L.len}, zb{zbuf + zoff[i] + (int64_t)k * L.len, 1, L.len};
+      View none{nullptr, 0, 0};
+      if (pivot && mid) ltop.push_back(sdesc(c, i, 0, nl, k, zt, nullptr, none, 0.0, zt));
+      if (L.bot_nbr) lbot.push_back(sdesc(c, i, pivot ? nl - 2 * k : nl - k, nl, k, zb, nullptr, none, 0.0, zb));
+      if (mid) ub.push_back(sdesc(c, i, 0, nl, 2 * k, zt, nullptr, none, 0.0, zt));
+      else if (L.bot_nbr) ub.push_back(sdesc(c, i, nl - k, nl, k, zb, nullptr, none, 0.0, zb));
+    }
+    pp.sweep(LN, ltop, k, c->ldf, c->dofs, true, k);
+    pp.sweep(LN, lbot, k, c->ldf, c->dofs, pivot != 0, k);
+    pp.sweep(UN, ub, pivot ? 2 * k : k, c->ldf, c->dofs, false, k);
+    if ((rc = pp.run(c)) != 0) return fail2(rc);
+  }
+  if ((rc = launch_tips0(dleaf, nlv, k, zbuf, dzoff, c->spk, s)) != 0) {
+    g_cuda_err = std::string("tips kernel: ") + cudaGetErrorString((cudaError_t)rc);
+    return fail2(SPIKE_ECUDA);
+  }
+  // 4. recursive reduced system factorization
+  for (int lv = 0; lv < c->NL; ++lv) {
+    if ((rc = factor_reduced_level(c, lv, tmp, tmp_bytes)) != 0) return fail2(rc);
+  }
+  // 5. status
+  unsigned long long st[8];
+  if (cudaMemcpyAsync(st, c->status, sizeof(st), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    g_cuda_err = std::string("factor: ") + cudaGetErrorString(cudaGetLastError());
+    return fail2(SPIKE_ECUDA);
+  }
+  cudaFreeAsync(fscr, s);
+  c->boosts = (int64_t)st[0];
+  c->zero_col = (st[1] == ULLONG_MAX) ? 0 : (int64_t)st[1];
+  c->nan_flag = (int)st[2];
+  *out = c;
+  if (pivot && c->zero_col) return (int)std::min<int64_t>(c->zero_col, INT_MAX);
+  return 0;
+}
+
+extern "C" int spike_factor(const double *band, int64_t n, int kl, int ku, int p, int pivot, spike_handle *out) {
+  return spike_factor_ex(band, (int64_t)kl + ku + 1, n, kl, ku, p, pivot, nullptr, out);
+}
+
+// One merge level of the reduced system (Sec. 2.2): for each pair of adjacent
+// groups L = [a,b), R = [b,c) factor the 2k x 2k interface
+//   M = [ I  V_{b-1,bot} ; W_{b,top}  I ]
+// and form the merged group's spikes (Eqs. RED_SYS_RECB / RED_SYS_W):
+//   [alpha; beta] = M^{-1} [0; V_{b,top}],  [gamma; delta] = M^{-1} [W_{b-1,bot}; 0]
+//   V'_L = -V_L beta,   V'_R = V_R - W_R alpha,   W'_L = W_L - V_L delta,   W'_R = -W_R gamma
+// (interface tips V'_{b,top} = beta, W'_{b,top} = delta come from the 2k solve).
+// When |W_{b,top}| <= 1 the pivoted LU of M keeps the identity rows for the first k
+// columns, so M = [I 0; W I][I V; 0 S] with S = I - W V: only S is LU-factored
+// (same pivot decisions as partial pivoting on M), otherwise M itself is.
+static int factor_reduced_level(spike_ctx *c, int lv, char *tmp, size_t tmp_bytes) {
+  (void)tmp_bytes;
+  const Plan &pl = c->pl;
+  const auto &ms = pl.levels[lv];
+  const int nm = (int)ms.size();
+  const int k = c->k;
+  const int64_t kk = (int64_t)k * k;
+  cudaStream_t s = c->stream;
+  int rc;
+  // flags: one device round trip per level
+  {
+    std::vector<const double *> w(nm);
+    for (int m = 0; m < nm; ++m) w[m] = TIP(c, lv, 1, ms[m].b, 0);
+    Arena ar;
+    const size_t ow = ar.put(w);
+    const size_t of = ar.put(std::vector<int>(nm, 0));
+    SP_TRY(ensure(&c->dargs, &c->dargs_bytes, ar.h.size(), s));
+    SP_CUDA(cudaMemcpyAsync(c->dargs, ar.h.data(), ar.h.size(), cudaMemcpyHostToDevice, s));
+    if ((rc = launch_noswap_flags((const double *const *)(c->dargs + ow), k, nm, (int *)(c->dargs + of), s)) != 0) {
+      g_cuda_err = std::string("noswap: ") + cudaGetErrorString((cudaError_t)rc);
+      return SPIKE_ECUDA;
+    }
+    std::vector<int> f(nm);
+    SP_CUDA(cudaMemcpyAsync(f.data(), c->dargs + of, sizeof(int) * nm, cudaMemcpyDeviceToHost, s));
+    SP_CUDA(cudaStreamSynchronize(s));
+    c->schur[lv] = f;
+  }
+  const std::vector<int> &sc = c->schur[lv];
+  const bool last = (lv + 1 >= c->NL);
+  Pipeline pp;
+  pp.st = s;
+  GemmBatch gA, gB, gC;
+  std::vector<LuDesc> lus;
+  TrsBatch tr;
+  int maxn = 0;
+  for (int m = 0; m < nm; ++m) {
+    const Merge &mg = ms[m];
+    const int64_t gm = c->merge_off[lv] + m;
+    double *lu = c->mlu + gm * 4 * kk;
+    int *piv = c->mpiv + gm * 2 * k;
+    double *slot = (double *)tmp + (int64_t)m * 5 * kk;  // [alpha; beta; gamma; delta; T]
+    double *al = slot, *be = slot + kk, *ga = slot + 2 * kk, *de = slot + 3 * kk, *Tm = slot + 4 * kk;
+    const double *Vlb = TIP(c, lv, 0, mg.b - 1, 1), *Wrt = TIP(c, lv, 1, mg.b, 0);
+    const double *Vrt = TIP(c, lv, 0, mg.b, 0), *Wlb = TIP(c, lv, 1, mg.b - 1, 1);
+    LuDesc L;
+    memset(&L, 0, sizeof(L));
+    L.a = lu;
+    L.ipiv = piv;
+    L.active = 1;
+    if (sc[m]) {
+      gA.add(gd(Wrt, k, 1, Vlb, k, 1, c->ident, k, 1, lu, k, 1, k, k, k, -1.0, 1.0));  // S = I - W V
+      if (mg.hasW) gA.add(gd(Wrt, k, 1, Wlb, k, 1, nullptr, 0, 0, Tm, k, 1, k, k, k, 1.0, 0.0));
+      if (mg.hasV) gA.add(gd(nullptr, 0, 0, nullptr, 0, 0, Vrt, k, 1, be, k, 1, k, k, 0, 0.0, 1.0));
+      L.n = k;
+      L.lda = k;
+      if (mg.hasV) tr.add(lu, piv, k, k, be, k, k, 0, 1.0);
+      if (mg.hasW) tr.add(lu, piv, k, k, Tm, k, k, 0, -1.0);  // delta = -S^{-1} W_rt W_lb
+      if (mg.hasV) gB.add(gd(Vlb, k, 1, be, k, 1, nullptr, 0, 0, al, k, 1, k, k, k, -1.0, 0.0));
+      if (mg.hasW) {
+        gB.add(gd(Vlb, k, 1, Tm, k, 1, Wlb, k, 1, ga, k, 1, k, k, k, -1.0, 1.0));
+        gB.add(gd(nullptr, 0, 0, nullptr, 0, 0, Tm, k, 1, de, k, 1, k, k, 0, 0.0, 1.0));
+      }
+    } else {
+      const int n2 = 2 * k;
+      gA.add(gd(nullptr, 0, 0, nullptr, 0, 0, c->ident, k, 1, lu, n2, 1, k, k, 0, 0.0, 1.0));
+      gA.add(gd(nullptr, 0, 0, nullptr, 0, 0, Vlb, k, 1, lu + k, n2, 1, k, k, 0, 0.0, 1.0));
+      gA.add(gd(nullptr, 0, 0, nullptr, 0, 0, Wrt, k, 1, lu + (int64_t)k * n2, n2, 1, k, k, 0, 0.0, 1.0));
+      gA.add(gd(nullptr, 0, 0, nullptr, 0, 0, c->ident, k, 1, lu + (int64_t)k * n2 + k, n2, 1, k, k, 0, 0.0, 1.0));
+      if (mg.hasV) {
+        gA.add(gd(nullptr, 0, 0, nullptr, 0, 0, nullptr, 0, 0, al, k, 1, k, k, 0, 0.0, 0.0));
+        gA.add(gd(nullptr, 0, 0, nullptr, 0, 0, Vrt, k, 1, be, k, 1, k, k, 0, 0.0, 1.0));
+        tr.add(lu, piv, n2, n2, al, k, k, 0, 1.0);
+      }
+      if (mg.hasW) {
+        gA.add(gd(nullptr, 0, 0, nullptr, 0, 0, Wlb, k, 1, ga, k, 1, k, k, 0, 0.0, 1.0));
+        gA.add(gd(nullptr, 0, 0, nullptr, 0, 0, nullptr, 0, 0, de, k, 1, k, k, 0, 0.0, 0.0));
+        tr.add(lu, piv, n2, n2, ga, k, k, 0, 1.0);
+      }
+      L.n = n2;
+      L.lda = n2;
+    }
+    maxn = std::max(maxn, L.n);
+    lus.push_back(L);
+    if (!last) {
+      const int a = mg.a, b = mg.b, cc = mg.c;
+      const int ML = 2 * (b - a) * k, MR = (2 * (cc - b) - 1) * k, MA = 2 * (cc - a) * k;
+      if (mg.hasV) {
+        gC.add(gd(TIP(c, lv, 0, a, 0), k, 1, be, k, 1, nullptr, 0, 0, TIP(c, lv + 1, 0, a, 0), k, 1, ML, k, k, -1.0,
+                  0.0));
+        gC.add(gd(TIP(c, lv, 1, b, 1), k, 1, al, k, 1, TIP(c, lv, 0, b, 1), k, 1, TIP(c, lv + 1, 0, b, 1), k, 1, MR,
+                  k, k, -1.0, 1.0));
+        gC.add(gd(nullptr, 0, 0, nullptr, 0, 0, be, k, 1, TIP(c, lv + 1, 0, b, 0), k, 1, k, k, 0, 0.0, 1.0));
+      } else {
+        gC.add(gd(nullptr, 0, 0, nullptr, 0, 0, nullptr, 0, 0, TIP(c, lv + 1, 0, a, 0), k, 1, MA, k, 0, 0.0, 0.0));
+      }
+      if (mg.hasW) {
+        gC.add(gd(TIP(c, lv, 0, a, 0), k, 1, de, k, 1, TIP(c, lv, 1, a, 0), k, 1, TIP(c, lv + 1, 1, a, 0), k, 1, ML,
+                  k, k, -1.0, 1.0));
+        gC.add(gd(TIP(c, lv, 1, b, 1), k, 1, ga, k, 1, nullptr, 0, 0, TIP(c, lv + 1, 1, b, 1), k, 1, MR, k, k, -1.0,
+                  0.0));
+        gC.add(gd(nullptr, 0, 0, nullptr, 0, 0, de, k, 1, TIP(c, lv + 1, 1, b, 0), k, 1, k, k, 0, 0.0, 1.0));
+      } else {
+        gC.add(gd(nullptr, 0, 0, nullptr, 0, 0, nullptr, 0, 0, TIP(c, lv + 1, 1, a, 0), k, 1, MA, k, 0, 0.0, 0.0));
+      }
+    }
+  }
+  pp.gemm(gA);
+  {
+    const size_t off = pp.ar.put(lus);
+    const int nd = (int)lus.size();
+    unsigned long long *st = c->status;
+    pp.ops.push_back([=](char *base) { return launch_getrf((LuDesc *)(base + off), nd, maxn, st, s); });
+  }
+  pp.trs(tr);
+  pp.gemm(gB);
+  if (!last) {
+    // untouched groups of this level keep their spikes: copy the whole level first
+    double *src = TIP(c, lv, 0, 0, 0), *dst = TIP(c, lv + 1, 0, 0, 0);
+    const size_t bytes = sizeof(double) * (size_t)2 * c->nleaves * 2 * kk;
+    pp.ops.push_back([=](char *) { return (int)cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s); });
+    pp.gemm(gC);
+  }
+  return pp.run(c);
+}
+
+// ================================================================ solve
+extern "C" int spike_solve_ex(spike_handle h, double *F, int64_t ldf, int nrhs, char trans) {
+  if (!valid(h)) return SPIKE_EHANDLE;
+  if (!F) return -2;
+  spike_ctx *c = h;
+  const int64_t n = c->pl.n;
+  if (ldf < n) return -3;
+  if (nrhs < 0) return -4;
+  const int tr = (trans == 'N' || trans == 'n') ? 0 : ((trans == 'T' || trans == 't' || trans == 'C' || trans == 'c') ? 1 : -1);
+  if (tr < 0) return -5;
+  if (c->pivot && c->zero_col) return (int)std::min<int64_t>(c->zero_col, INT_MAX);
+  if (nrhs == 0) return 0;
+  const int k = c->k, nlv = c->nleaves, m = nrhs;
+  const int64_t kk = (int64_t)k * k, km = (int64_t)k * m;
+  cudaStream_t s = c->stream;
+
+  // scratch: [staged F][H][Y][merge temps]
+  const bool fdev = is_device_ptr(F);
+  size_t off = 0;
+  auto carve = [&](size_t bytes) {
+    size_t o = off;
+    off = (off + bytes + 255) & ~size_t(255);
+    return o;
+  };
+  const size_t o_f = fdev ? 0 : carve(sizeof(double) * (size_t)n * m);
+  const size_t o_h = carve(sizeof(double) * (size_t)n * m);
+  const size_t o_y = carve(sizeof(double) * (size_t)nlv * 2 * km);
+  size_t maxm = 1;
+  for (auto &lvv : c->pl.levels) maxm = std::max(maxm, lvv.size());
+  const size_t o_t = carve(sizeof(double) * maxm * 2 * km);
+  SP_TRY(ensure(&c->scr, &c->scr_bytes, off, s));
+  double *Fd = F;
+  int64_t ld = ldf;
+  if (!fdev) {
+    Fd = (double *)(c->scr + o_f);
+    ld = n;
+    SP_CUDA(cudaMemcpy2DAsync(Fd, sizeof(double) * n, F, sizeof(double) * ldf, sizeof(double) * n, m,
+                              cudaMemcpyHostToDevice, s));
+  }
+  double *H = (double *)(c->scr + o_h);
+  double *Y = (double *)(c->scr + o_y);
+  double *TM = (double *)(c->scr + o_t);
+  auto YB = [&](int i, int t) { return Y + ((int64_t)i * 2 + t) * km; };  // k x m row-major block
+
+  Pipeline pp;
+  pp.st = s;
+  View none{nullptr, 0, 0};
+  const bool piv = c->pivot != 0;
+  const int kwU = piv ? 2 * k : k;
+  auto memset_op = [&](void *p, size_t bytes) {
+    pp.ops.push_back([=](char *) { return (int)cudaMemsetAsync(p, 0, bytes, s); });
+  };
+  memset_op(H, sizeof(double) * (size_t)n * m);
+  memset_op(Y, sizeof(double) * (size_t)nlv * 2 * km);
+  // tip rows of a global-frame column-major array as a k x m matrix view
+  auto rows_view = [&](double *base, int64_t ldx, int64_t row0) { return View{base + row0, 1, ldx}; };
+
+  if (tr == 0) {
+    // ---------------- D stage (Eq. Dstage) with the sweep savings of Sec. 2.3
+    std::vector<SweepDesc> sa, sb;
+    for (int i = 0; i < nlv; ++i) {
+      const LeafDev &L = c->hl[i];
+      const int nl = (int)L.len;
+      const View fv = leaf_view(L, Fd, ld), hv = leaf_view(L, H, n);
+      sa.push_back(sdesc(c, i, 0, nl, m, fv, nullptr, none, 0, fv));  // F <- L^{-1} F
+      if (L.top_nbr && L.bot_nbr) sb.push_back(sdesc(c, i, 0, nl, m, fv, nullptr, none, 0, hv));
+      else if (L.bot_nbr) sb.push_back(sdesc(c, i, nl - k, nl, m, fv, nullptr, none, 0, hv));
+    }
+    pp.sweep(LN, sa, k, c->ldf, c->dofs, piv, k);
+    pp.sweep(UN, sb, kwU, c->ldf, c->dofs, false, k);
+    // gather Y tips (global rows) from H
+    GemmBatch g0;
+    for (int i = 0; i < nlv; ++i) {
+      const LeafDev &L = c->hl[i];
+      if (i > 0) g0.add(gd(nullptr, 0, 0, nullptr, 0, 0, H + L.start, 1, n, YB(i, 0), m, 1, k, m, 0, 0.0, 1.0));
+      if (i + 1 < nlv)
+        g0.add(gd(nullptr, 0, 0, nullptr, 0, 0, H + L.start + L.len - k, 1, n, YB(i, 1), m, 1, k, m, 0, 0.0, 1.0));
+    }
+    pp.gemm(g0);
+    // ---------------- reduced system, levels ascending: D^[1]^-1 ... (Eqs. D1Inverse, S2Inverse)
+    for (int lv = 0; lv < c->NL; ++lv) {
+      const auto &ms = c->pl.levels[lv];
+      GemmBatch g1, g2, g3;
+      TrsBatch ts;
+      for (int mi = 0; mi < (int)ms.size(); ++mi) {
+        const Merge &mg = ms[mi];
+        const int64_t gm = c->merge_off[lv] + mi;
+        const double *lu = c->mlu + gm * 4 * kk;
+        const int *pv = c->mpiv + gm * 2 * k;
+        double *ta = TM + (int64_t)mi * 2 * km, *tb = ta + km;  // [a; b]
+        const double *Vlb = TIP(c, lv, 0, mg.b - 1, 1), *Wrt = TIP(c, lv, 1, mg.b, 0);
+        if (c->schur[lv][mi]) {
+          // b = S^{-1} (y_{b,top} - W y_{b-1,bot});  a = y_{b-1,bot} - V b
+          g1.add(gd(Wrt, k, 1, YB(mg.b - 1, 1), m, 1, YB(mg.b, 0), m, 1, tb, m, 1, k, m, k, -1.0, 1.0));
+          ts.add(lu, pv, k, k, tb, m, m, 0, 1.0);
+          g2.add(gd(Vlb, k, 1, tb, m, 1, YB(mg.b - 1, 1), m, 1, ta, m, 1, k, m, k, -1.0, 1.0));
+        } else {
+          g1.add(gd(nullptr, 0, 0, nullptr, 0, 0, YB(mg.b - 1, 1), m, 1, ta, m, 1, k, m, 0, 0.0, 1.0));
+          g1.add(gd(nullptr, 0, 0, nullptr, 0, 0, YB(mg.b, 0), m, 1, tb, m, 1, k, m, 0, 0.0, 1.0));
+          ts.add(lu, pv, 2 * k, 2 * k, ta, m, m, 0, 1.0);
+        }
+        // updates: y_L -= V_L b (all L tips but (b-1,bot)), y_R -= W_R a (all R tips but (b,top))
+        const int ML = (2 * (mg.b - mg.a) - 1) * k, MR = (2 * (mg.c - mg.b) - 1) * k;
+        g3.add(gd(TIP(c, lv, 0, mg.a, 0), k, 1, tb, m, 1, YB(mg.a, 0), m, 1, YB(mg.a, 0), m, 1, ML, m, k, -1.0, 1.0));
+        g3.add(gd(TIP(c, lv, 1, mg.b, 1), k, 1, ta, m, 1, YB(mg.b, 1), m, 1, YB(mg.b, 1), m, 1, MR, m, k, -1.0, 1.0));
+        g3.add(gd(nullptr, 0, 0, nullptr, 0, 0, ta, m, 1, YB(mg.b - 1, 1), m, 1, k, m, 0, 0.0, 1.0));
+        g3.add(gd(nullptr, 0, 0, nullptr, 0, 0, tb, m, 1, YB(mg.b, 0), m, 1, k, m, 0, 0.0, 1.0));
+      }
+      pp.gemm(g1);
+      pp.trs(ts);
+      pp.gemm(g2);
+      pp.gemm(g3);
+    }
+    // ---------------- retrieval (Eqs. one/two/three): X_i = U^{-1}(L^{-1}F - L^{-1}[R_top x_top; 0; R_bot x_bot])
+    memset_op(H, sizeof(double) * (size_t)n * m);
+    GemmBatch gc;
+    std::vector<SweepDesc> sc, sd;
+    for (int i = 0; i < nlv; ++i) {
+      const LeafDev &L = c->hl[i];
+      const int nl = (int)L.len;
+      const View fv = leaf_view(L, Fd, ld), hv = leaf_view(L, H, n);
+      const double *Rt = c->couple + (int64_t)i * 2 * kk, *Rb = Rt + kk;
+      if (L.top_nbr) {
+        const double *xn = L.rev ? YB(i + 1, 0) : YB(i - 1, 1);
+        gc.add(gd(Rt, k, 1, xn, m, 1, nullptr, 0, 0, hv.p, hv.rs, hv.cs, k, m, k, 1.0, 0.0));
+      }
+      if (L.bot_nbr) {
+        const double *xn = L.rev ? YB(i - 1, 1) : YB(i + 1, 0);
+        gc.add(gd(Rb, k, 1, xn, m, 1, nullptr, 0, 0, hv.p + (int64_t)(nl - k) * hv.rs, hv.rs, hv.cs, k, m, k, 1.0,
+                  0.0));
+      }
+      if (L.top_nbr && L.bot_nbr) sc.push_back(sdesc(c, i, 0, nl, m, hv, nullptr, none, 0, hv));
+      else if (L.bot_nbr) sc.push_back(sdesc(c, i, piv ? nl - 2 * k : nl - k, nl, m, hv, nullptr, none, 0, hv));
+      sd.push_back(sdesc(c, i, 0, nl, m, fv, hv.p, hv, -1.0, fv));
+    }
+    pp.gemm(gc);
+    pp.sweep(LN, sc, k, c->ldf, c->dofs, piv, k);
+    pp.sweep(UN, sd, kwU, c->ldf, c->dofs, false, k);
+  } else {
+    // ---------------- transpose: S^T Y = F then D^T X = Y (Sec. 4.1, 4.2)
+    GemmBatch g0, gz;
+    for (int i = 0; i < nlv; ++i) {
+      const LeafDev &L = c->hl[i];
+      if (i > 0) {
+        const View v = rows_view(Fd, ld, L.start);
+        g0.add(gd(nullptr, 0, 0, nullptr, 0, 0, v.p, v.rs, v.cs, YB(i, 0), m, 1, k, m, 0, 0.0, 1.0));
+        gz.add(gd(nullptr, 0, 0, nullptr, 0, 0, nullptr, 0, 0, v.p, v.rs, v.cs, k, m, 0, 0.0, 0.0));
+      }
+      if (i + 1 < nlv) {
+        const View v = rows_view(Fd, ld, L.start + L.len - k);
+        g0.add(gd(nullptr, 0, 0, nullptr, 0, 0, v.p, v.rs, v.cs, YB(i, 1), m, 1, k, m, 0, 0.0, 1.0));
+        gz.add(gd(nullptr, 0, 0, nullptr, 0, 0, nullptr, 0, 0, v.p, v.rs, v.cs, k, m, 0, 0.0, 0.0));
+      }
+    }
+    pp.gemm(g0);
+    pp.gemm(gz);
+    std::vector<SweepDesc> sa, sb;
+    for (int i = 0; i < nlv; ++i) {
+      const LeafDev &L = c->hl[i];
+      const int nl = (int)L.len;
+      const View fv = leaf_view(L, Fd, ld), hv = leaf_view(L, H, n);
+      sa.push_back(sdesc(c, i, 0, nl, m, fv, nullptr, none, 0, fv));  // w = U^{-T} [0; F~; 0]
+      const int r0 = (L.top_nbr && L.bot_nbr) ? 0 : (piv ? nl - 2 * k : nl - k);
+      if (L.bot_nbr) sb.push_back(sdesc(c, i, r0, nl, m, piv ? hv : fv, nullptr, none, 0, hv));
+    }
+    pp.sweep(UT, sa, kwU, c->ldf, c->dofs, false, k);
+    if (piv) {
+      // the pivoted L^T sweep runs in place: copy w into H first
+      double *Fp = Fd;
+      const int64_t ldp = ld;
+      pp.ops.push_back([=](char *) {
+        return (int)cudaMemcpy2DAsync(H, sizeof(double) * n, Fp, sizeof(double) * ldp, sizeof(double) * n, m,
+                                      cudaMemcpyDeviceToDevice, s);
+      });
+    }
+    pp.sweep(LT, sb, k, c->ldf, c->dofs, piv, k);
+    // G tips: y_{j+1,top} -= Bhat_j^T z_{j,bot}, y_{j-1,bot} -= Chat_j^T z_{j,top} (Eqs. G_in_transpose_1/2)
+    GemmBatch gg;
+    for (int j = 0; j < nlv; ++j) {
+      const LeafDev &L = c->hl[j];
+      const int nl = (int)L.len;
+      const View hv = leaf_view(L, H, n);
+      const double *Rt = c->couple + (int64_t)j * 2 * kk, *Rb = Rt + kk;
+      if (L.top_nbr) {
+        double *tgt = L.rev ? YB(j + 1, 0) : YB(j - 1, 1);
+        gg.add(gd(Rt, 1, k, hv.p, hv.rs, hv.cs, tgt, m, 1, tgt, m, 1, k, m, k, -1.0, 1.0));
+      }
+      if (L.bot_nbr) {
+        double *tgt = L.rev ? YB(j - 1, 1) : YB(j + 1, 0);
+        gg.add(gd(Rb, 1, k, hv.p + (int64_t)(nl - k) * hv.rs, hv.rs, hv.cs, tgt, m, 1, tgt, m, 1, k, m, k, -1.0, 1.0));
+      }
+    }
+    pp.gemm(gg);
+    // ---------------- transposed reduced system, levels descending (Sec. 4.3)
+    for (int lv = c->NL - 1; lv >= 0; --lv) {
+      const auto &ms = c->pl.levels[lv];
+      GemmBatch g1, g2, g3, g4;
+      TrsBatch ts;
+      for (int mi = 0; mi < (int)ms.size(); ++mi) {
+        const Merge &mg = ms[mi];
+        const int64_t gm = c->merge_off[lv] + mi;
+        const double *lu = c->mlu + gm * 4 * kk;
+        const int *pv = c->mpiv + gm * 2 * k;
+        double *s2 = TM + (int64_t)mi * 2 * km, *s1 = s2 + km;  // [g2; g1] -> [s2; s1]
+        const double *Vlb = TIP(c, lv, 0, mg.b - 1, 1), *Wrt = TIP(c, lv, 1, mg.b, 0);
+        const int KL = 2 * (mg.b - mg.a) * k, KR = 2 * (mg.c - mg.b) * k;
+        // g1 = V_L^T y_L, g2 = W_R^T y_R (stacked tips)
+        g1.add(gd(TIP(c, lv, 0, mg.a, 0), 1, k, YB(mg.a, 0), m, 1, nullptr, 0, 0, s1, m, 1, k, m, KL, 1.0, 0.0));
+        g1.add(gd(TIP(c, lv, 1, mg.b, 0), 1, k, YB(mg.b, 0), m, 1, nullptr, 0, 0, s2, m, 1, k, m, KR, 1.0, 0.0));
+        if (c->schur[lv][mi]) {
+          // s1 = S^{-T} (g1 - V^T g2);  s2 = g2 - W^T s1
+          g2.add(gd(Vlb, 1, k, s2, m, 1, s1, m, 1, s1, m, 1, k, m, k, -1.0, 1.0));
+          ts.add(lu, pv, k, k, s1, m, m, 1, 1.0);
+          g3.add(gd(Wrt, 1, k, s1, m, 1, s2, m, 1, s2, m, 1, k, m, k, -1.0, 1.0));
+        } else {
+          ts.add(lu, pv, 2 * k, 2 * k, s2, m, m, 1, 1.0);  // M^T [s2; s1] = [g2; g1]
+        }
+        // y_{b,top} -= s1;  y_{b-1,bot} -= s2
+        g4.add(gd(c->ident, k, 1, s1, m, 1, YB(mg.b, 0), m, 1, YB(mg.b, 0), m, 1, k, m, k, -1.0, 1.0));
+        g4.add(gd(c->ident, k, 1, s2, m, 1, YB(mg.b - 1, 1), m, 1, YB(mg.b - 1, 1), m, 1, k, m, k, -1.0, 1.0));
+      }
+      pp.gemm(g1);
+      pp.gemm(g2);
+      pp.trs(ts);
+      pp.gemm(g3);
+      pp.gemm(g4);
+    }
+    // ---------------- D^T stage (Eq. sweeps_in_D): X_i = L^{-T}(w + U^{-T}[y_top; 0; y_bot])
+    memset_op(H, sizeof(double) * (size_t)n * m);
+    GemmBatch gp;
+    std::vector<SweepDesc> sc, sd;
+    for (int i = 0; i < nlv; ++i) {
+      const LeafDev &L = c->hl[i];
+      const int nl = (int)L.len;
+      const View fv = leaf_view(L, Fd, ld), hv = leaf_view(L, H, n);
+      if (i > 0) gp.add(gd(nullptr, 0, 0, nullptr, 0, 0, YB(i, 0), m, 1, H + L.start, 1, n, k, m, 0, 0.0, 1.0));
+      if (i + 1 < nlv)
+        gp.add(gd(nullptr, 0, 0, nullptr, 0, 0, YB(i, 1), m, 1, H + L.start + L.len - k, 1, n, k, m, 0, 0.0, 1.0));
+      if (L.top_nbr && L.bot_nbr) sc.push_back(sdesc(c, i, 0, nl, m, hv, nullptr, none, 0, hv));
+      else if (L.bot_nbr) sc.push_back(sdesc(c, i, nl - k, nl, m, hv, nullptr, none, 0, hv));
+      SweepDesc d = sdesc(c, i, 0, nl, m, fv, nullptr, none, 0, fv);
+      if (!piv) {
+        d.gb = hv.p;
+        d.gb_rs = hv.rs;
+        d.gb_cs = hv.cs;
+        d.gb_scale = 1.0;
+      }
+      sd.push_back(d);
+    }
+    pp.gemm(gp);
+    pp.sweep(UT, sc, kwU, c->ldf, c->dofs, false, k);
+    if (piv) {
+      // F += H (column by column, F may have ldf > n), then the pivoted L^T sweep in place
+      double *Fp = Fd;
+      const int64_t ldp = ld;
+      pp.ops.push_back([=](char *) {
+        for (int col = 0; col < m; ++col) {
+          int e = launch_axpy(Fp + (int64_t)col * ldp, H + (int64_t)col * n, 1.0, n, s);
+          if (e) return e;
+        }
+        return 0;
+      });
+    }
+    pp.sweep(LT, sd, k, c->ldf, c->dofs, piv, k);
+  }
+  SP_TRY(pp.run(c));
+  if (!fdev) {
+    SP_CUDA(cudaMemcpy2DAsync(F, sizeof(double) * ldf, Fd, sizeof(double) * n, sizeof(double) * n, m,
+                              cudaMemcpyDeviceToHost, s));
+    SP_CUDA(cudaStreamSynchronize(s));
+  }
+  return 0;
+}
+
+extern "C" int spike_solve(spike_handle h, double *F, int nrhs, char trans) {
+  if (!valid(h)) return SPIKE_EHANDLE;
+  return spike_solve_ex(h, F, h->pl.n, nrhs, trans);
+}
+
+extern "C" int spike_set_stream(spike_handle h, void *stream) {
+  if (!valid(h)) return SPIKE_EHANDLE;
+  h->stream = (cudaStream_t)stream;
+  return 0;
+}
+
+extern "C" int spike_get_info(spike_handle h, spike_info *out) {
+  if (!valid(h)) return SPIKE_EHANDLE;
+  if (!out) return -2;
+  fill_info(h->pl, out);
+  out->boosts = h->boosts;
+  out->zero_pivot_col = h->zero_col;
+  out->device_bytes = (int64_t)(h->mem_bytes + h->scr_bytes + h->dargs_bytes);
+  return 0;
+}
+
+extern "C" int spike_get_tips(spike_handle h, int level, double *host_dst) {
+  if (!valid(h)) return SPIKE_EHANDLE;
+  if (level < 0 || level >= std::max(h->NL, 1)) return -2;
+  if (!host_dst) return -3;
+  const int64_t kk = (int64_t)h->k * h->k;
+  // device layout [V/W][leaf][top/bot]; host layout [leaf][Vt, Vb, Wt, Wb]
+  std::vector<double> tmp((size_t)2 * h->nleaves * 2 * kk);
+  SP_CUDA(cudaMemcpyAsync(tmp.data(), TIP(h, level, 0, 0, 0), sizeof(double) * tmp.size(), cudaMemcpyDeviceToHost,
+                          h->stream));
+  SP_CUDA(cudaStreamSynchronize(h->stream));
+  for (int i = 0; i < h->nleaves; ++i)
+    for (int sp = 0; sp < 2; ++sp)
+      for (int t = 0; t < 2; ++t)
+        memcpy(host_dst + ((int64_t)i * 4 + sp * 2 + t) * kk, tmp.data() + (((int64_t)sp * h->nleaves + i) * 2 + t) * kk,
+               sizeof(double) * kk);
+  return 0;
+}
+
+extern "C" int spike_backward_error(const double *band, int64_t ldab, int64_t n, int kl, int ku, const double *X,
+                                    const double *F, int nrhs, char trans, void *stream, double *berr) {
+  if (!band) return -1;
+  if (ldab < (int64_t)kl + ku + 1) return -2;
+  if (n < 1) return -3;
+  if (kl < 0) return -4;
+  if (ku < 0) return -5;
+  if (!X) return -6;
+  if (!F) return -7;
+  if (nrhs < 1) return -8;
+  if (trans != 'N' && trans != 'n' && trans != 'T' && trans != 't') return -9;
+  if (!berr) return -11;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long *scr = nullptr;
+  const size_t bytes = sizeof(unsigned long long) * (1 + 2 * (size_t)nrhs);
+  SP_CUDA(cudaMallocAsync((void **)&scr, bytes, s));
+  SP_CUDA(cudaMemsetAsync(scr, 0, bytes, s));
+  const int e = launch_berr(band, ldab, n, kl, ku, X, F, nrhs, (trans == 'T' || trans == 't') ? 1 : 0, scr, s);
+  if (e) {
+    cudaFreeAsync(scr, s);
+    g_cuda_err = std::string("berr kernel: ") + cudaGetErrorString((cudaError_t)e);
+    return SPIKE_ECUDA;
+  }
+  std::vector<unsigned long long> h(1 + 2 * (size_t)nrhs);
+  SP_CUDA(cudaMemcpyAsync(h.data(), scr, bytes, cudaMemcpyDeviceToHost, s));
+  SP_CUDA(cudaFreeAsync(scr, s));
+  SP_CUDA(cudaStreamSynchronize(s));
+  auto as_d = [](unsigned long long b) {
+    double d;
+    memcpy(&d, &b, sizeof(d));
+    return d;
+  };
+  const double an = as_d(h[0]);
+  for (int c = 0; c < nrhs; ++c) {
+    const double r = as_d(h[1 + 2 * c]), x = as_d(h[2 + 2 * c]);
+    berr[c] = (an > 0 && x > 0) ? r / (an * x) : (r == 0 ? 0.0 : INFINITY);
+  }
+  return 0;
+}
+
+extern "C" void spike_free(spike_handle h) {
+  if (!valid(h)) return;
+  cudaStream_t s = h->stream;
+  if (h->mem) cudaFreeAsync(h->mem, s);
+  if (h->scr) cudaFreeAsync(h->scr, s);
+  if (h->dargs) cudaFreeAsync(h->dargs, s);
+  cudaStreamSynchronize(s);
+  h->magic = 0;
+  delete h;
+}
+
+extern "C" const char *spike_strerror(int code) {
+  if (code == 0) return "success";
+  if (code > 0) return "zero pivot column: the matrix is singular";
+  switch (code) {
+    case SPIKE_ENOMEM: return "device or host allocation failed";
+    case SPIKE_ECUDA: return "CUDA error (see spike_last_cuda_error)";
+    case SPIKE_EHANDLE: return "invalid handle";
+    case SPIKE_ENOTSUP: return "unsupported argument combination";
+    case SPIKE_ENOGPU: return "no CUDA device available";
+    default: return "invalid argument";
+  }
+}
+
+extern "C" const char *spike_last_cuda_error(void) { return g_cuda_err.c_str(); }

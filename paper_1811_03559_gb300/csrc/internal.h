@@ -1,0 +1,153 @@
+// Internal declarations shared by the host orchestration (api.cu, plan.cpp) and
+// the device kernels (leaf.cu, dense.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/spike.h"
+
+namespace spk {
+
+constexpr int NB = 32;        // rows per block step in the factor and sweep kernels
+constexpr int NTHREADS = 256; // threads per CTA of the leaf kernels
+constexpr int CW = 256;       // RHS columns per sweep pass
+
+// ------------------------------------------------------------------ planning
+
+// One factored diagonal block ("leaf"): a whole partition, or one half of a
+// partition run as a SPIKE 2x2 pair (Sec. 3.1/3.2).
+struct Leaf {
+  int64_t start, len;  // global rows [start, start+len)
+  int rev;             // 1: UL factorization, done as LU of the reversed block Q A_i Q (Sec. 5.2)
+  int has_prev, has_next;
+  int part;            // partition index 0..P-1
+  int half;            // 0 single, 1 top half of a 2x2 pair, 2 bottom half
+};
+
+// One pairwise merge of the recursive reduced system (Sec. 2.2, Eqs. RED_SYS_RECB/RED_SYS_W):
+// left group = leaves [a, b), right group = leaves [b, c).
+struct Merge {
+  int a, b, c;
+  int hasV;  // the merged group has a V spike (it does not contain the last leaf)
+  int hasW;  // the merged group has a W spike (it does not contain the first leaf)
+};
+
+struct Plan {
+  int64_t n = 0;
+  int kl = 0, ku = 0, k = 0;
+  int t_req = 0, t_eff = 0, m = 0, P = 0, r = 0, nleaves = 0;
+  int pivot = 0;
+  double K = 2.0, R12 = 0, R13 = 0;
+  int64_t n1 = 0, n2 = 0, n3 = 0;
+  std::vector<Leaf> leaves;
+  std::vector<std::vector<Merge>> levels;  // merge levels, applied in order
+};
+
+// Returns 0 or -(argument index) on invalid input.
+int make_plan(int64_t n, int kl, int ku, int t, double K, int nrhs_hint, Plan &out);
+
+// ------------------------------------------------------- device descriptors
+
+// Leaf geometry as the kernels see it (local frame = reversed for UL leaves).
+struct LeafDev {
+  int64_t start, len;
+  int rev;
+  int top_nbr;  // the block has a neighbour coupled through its local top rows
+  int bot_nbr;  // ... through its local bottom rows
+  int pad;
+};
+
+// Triangular sweep kinds over the per-leaf LU band (local frame):
+//   LN: unit lower L, forward         UN: upper U, backward
+//   UT: U^T (lower), forward          LT: L^T (unit upper), backward
+enum SweepKind { LN = 0, UN = 1, UT = 2, LT = 3 };
+
+// One leaf's sweep: rows [r0, r1) of X = T^{-1} G, rows of X outside [r0, r1) taken as zero.
+// G(r,c) = ga[r*ga_rs + c*ga_cs] + gb_scale * gb[r*gb_rs + c*gb_cs]  (gb may be null)
+// X(r,c) = x[r*x_rs + c*x_cs]  (X may alias ga; it is also the source of the window rows)
+struct SweepDesc {
+  const double *fb;    // leaf factor band, local column 0
+  const double *dinv;  // leaf diagonal reciprocals, local row 0
+  const int *ipiv;     // leaf pivots (pivoting mode, local indices), local row 0
+  int64_t nl;
+  int r0, r1, ncols, pad;
+  const double *ga;
+  int64_t ga_rs, ga_cs;
+  const double *gb;
+  int64_t gb_rs, gb_cs;
+  double gb_scale;
+  double *x;
+  int64_t x_rs, x_cs;
+};
+
+// Batched FP64 GEMM on strided operands: C = beta*C0 + alpha*A*B, with
+// A(i,k) = A[i*a_rs + k*a_cs] (M x K), B(k,j) = B[k*b_rs + j*b_cs] (K x N),
+// C(i,j) = C[i*c_rs + j*c_cs]; C0 likewise (not read when beta == 0).  Negative
+// strides express reversed (Q) and transposed views.  K = 0 gives a scaled copy.
+struct GemmDesc {
+  const double *A, *B, *C0;
+  double *C;
+  int64_t a_rs, a_cs, b_rs, b_cs, c0_rs, c0_cs, c_rs, c_cs;
+  int M, N, K, tiles_n;
+  double alpha, beta;
+  int tile0, pad;
+};
+
+// Batched dense LU with partial pivoting (first index of the largest |entry|).
+struct LuDesc {
+  double *a;   // row-major n x n, lda
+  int *ipiv;   // n, 0-based row swapped with row j at step j
+  int n, lda;
+  int active;  // 0: skip
+  int pad;
+};
+
+// Batched solve with an LU of LuDesc: B <- alpha * op(M)^{-1} B (B row-major n x ncols).
+struct TrsDesc {
+  const double *lu;
+  const int *ipiv;
+  double *b;
+  int64_t ldb;
+  int n, lda, ncols, trans;
+  double alpha;
+  int tile0, pad;
+};
+
+// ------------------------------------------------------------ launchers
+// Each returns cudaError_t as int (0 = success).
+int launch_repack(const double *band, int64_t ldab, int kl, int ku, int64_t n, int k, int ldf, int dofs,
+                  const LeafDev *leaves, int nleaves, double *fb, unsigned long long *amax_bits, void *stream,
+                  int64_t max_leaf_len);
+int launch_couplings(const double *band, int64_t ldab, int kl, int ku, int64_t n, int k, const LeafDev *leaves,
+                     int nleaves, double *couple, void *stream);
+int launch_zinit(const LeafDev *leaves, int nleaves, int k, const double *couple, double *zbuf,
+                 const int64_t *zoff, int pivot, void *stream);
+int launch_factor_nopiv(const LeafDev *leaves, int nleaves, int k, int ldf, double *fb, double *dinv, double *zbuf,
+                        const int64_t *zoff, const unsigned long long *amax_bits, double boost_eps,
+                        unsigned long long *status, void *stream);
+int launch_factor_piv(const LeafDev *leaves, int nleaves, int k, int ldf, double *fb, double *dinv, int *ipiv,
+                      unsigned long long *status, void *stream);
+int launch_sweep(int kind, const SweepDesc *descs, int ndesc, int kw, int ldf, int dofs, int maxcols, void *stream);
+int launch_piv_sweep(int kind, const SweepDesc *descs, int ndesc, int k, int ldf, int dofs, void *stream);
+int launch_tips0(const LeafDev *leaves, int nleaves, int k, const double *zbuf, const int64_t *zoff, double *spk,
+                 void *stream);
+int launch_gemm(const GemmDesc *d, int ndesc, int total_tiles, void *stream);
+constexpr int GEMM_TILE = 64;
+int launch_getrf(const LuDesc *d, int ndesc, int maxn, unsigned long long *status, void *stream);
+int launch_getrs(const TrsDesc *d, int ndesc, int total_tiles, int maxn, void *stream);
+int launch_noswap_flags(const double *const *w, int k, int nm, int *flags, void *stream);
+int launch_assemble_M(const double *const *v, const double *const *w, int k, int nm, const int *flags, double *mbuf,
+                      int64_t mstride, void *stream);
+int launch_axpy(double *y, const double *x, double alpha, int64_t count, void *stream);
+// Backward-error reduction: scratch receives, as bit patterns of non-negative doubles,
+// [0] ||op(A)||_inf, [1+2c] ||op(A)x_c - f_c||_inf, [2+2c] ||x_c||_inf.
+int launch_berr(const double *band, int64_t ldab, int64_t n, int kl, int ku, const double *X, const double *F,
+                int nrhs, int trans, unsigned long long *scratch, void *stream);
+
+// spk tip storage index: level lv, spike s (0 = V, 1 = W), leaf i, tip t (0 = top, 1 = bottom)
+inline int64_t tip_index(int lv, int s, int i, int t, int nleaves, int k) {
+  return ((((int64_t)lv * 2 + s) * nleaves + i) * 2 + t) * (int64_t)k * k;
+}
+
+}  // namespace spk

@@ -1,0 +1,678 @@
+// Per-block ("leaf") kernels of the recursive SPIKE factorization and solves.
+// One CTA owns one diagonal block A_i in its local frame (reversed for the UL
+// blocks: UL(A_i) = Q LU(Q A_i Q) Q, Sec. 5.2), so every kernel here is an LU
+// kernel.  All arithmetic is FP64 on the CUDA-core FMA pipe; on this part that
+// pipe, not HBM, bounds every kernel, so the designs below aim at keeping
+// four or more warps per SM issuing independent FMAs and at minimising the
+// number of CTA-wide barriers per factored column.
+//
+// Storage (device, local frame, column-major):
+//   fb   : column c of a leaf at fb + c*ldf; entry (r, c) of the combined LU
+//          (unit L strictly below, U on/above the diagonal) at [dofs + r - c],
+//          dofs = k (no pivoting) or 2k (partial pivoting: U gains kl extra
+//          superdiagonals, Sec. 5.1).
+//   dinv : 1 / U(r, r).
+//   Z    : the two spike right-hand sides of a leaf, column-major with nl rows:
+//          columns [0, k) = [R_top; 0] (coupling through the local top rows),
+//          columns [k, 2k) = [0; R_bot] (coupling through the local bottom rows).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "internal.h"
+
+namespace spk {
+
+#define FULLMASK 0xffffffffu
+
+// ------------------------------------------------------------------ repack
+// User band (LAPACK layout, global frame) -> per-leaf LU band (local frame),
+// zero outside A_i's band, plus max|a_ij| for the boosting threshold.
+__global__ void __launch_bounds__(256) k_repack(const double *__restrict__ band, int64_t ldab, int kl, int ku,
+                                                int64_t n, int k, int ldf, int dofs, const LeafDev *leaves,
+                                                double *fb, unsigned long long *amax_bits) {
+  const LeafDev L = leaves[blockIdx.y];
+  const int64_t nl = L.len;
+  const int64_t ncols_per_blk = 8;
+  const int64_t c0 = (int64_t)blockIdx.x * ncols_per_blk;
+  double lmax = 0.0;
+  for (int64_t idx = threadIdx.x; idx < ncols_per_blk * ldf; idx += blockDim.x) {
+    const int64_t c = c0 + idx / ldf;
+    const int d = (int)(idx % ldf);
+    if (c >= nl) break;
+    const int64_t r = c + d - dofs;
+    double v = 0.0;
+    if (r >= 0 && r < nl && r - c <= k && c - r <= k) {
+      const int64_t gi = L.rev ? (L.start + nl - 1 - r) : (L.start + r);
+      const int64_t gj = L.rev ? (L.start + nl - 1 - c) : (L.start + c);
+      const int64_t off = gi - gj;
+      if (off >= -ku && off <= kl) v = band[gj * ldab + ku + off];
+    }
+    fb[(L.start + c) * ldf + d] = v;
+    lmax = fmax(lmax, fabs(v));
+  }
+  for (int o = 16; o; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(FULLMASK, lmax, o));
+  if ((threadIdx.x & 31) == 0 && lmax > 0.0) atomicMax(amax_bits, (unsigned long long)__double_as_longlong(lmax));
+}
+
+int launch_repack(const double *band, int64_t ldab, int kl, int ku, int64_t n, int k, int ldf, int dofs,
+                  const LeafDev *leaves, int nleaves, double *fb, unsigned long long *amax_bits, void *stream,
+                  int64_t max_leaf_len) {
+  dim3 grid((unsigned)((max_leaf_len + 7) / 8), (unsigned)nleaves);
+  k_repack<<<grid, 256, 0, (cudaStream_t)stream>>>(band, ldab, kl, ku, n, k, ldf, dofs, leaves, fb, amax_bits);
+  return (int)cudaGetLastError();
+}
+
+// ------------------------------------------------------------- couplings
+// couple[leaf][0] = R_top (k x k, row-major, local row order): rows = local top k rows,
+//   columns = the tip unknowns of the neighbour coupled through the top (global order):
+//   forward leaf: C_i-hat (previous block's last k columns); reversed: Q_k B_i-hat (next block's first k).
+// couple[leaf][1] = R_bot: rows = local bottom k rows; forward: B_i-hat; reversed: Q_k C_i-hat.
+__global__ void k_couplings(const double *__restrict__ band, int64_t ldab, int kl, int ku, int64_t n, int k,
+                            const LeafDev *leaves, double *couple) {
+  const LeafDev L = leaves[blockIdx.x];
+  const int64_t nl = L.len;
+  const int64_t kk = (int64_t)k * k;
+  double *Rt = couple + (int64_t)blockIdx.x * 2 * kk;
+  double *Rb = Rt + kk;
+  for (int64_t idx = threadIdx.x; idx < kk; idx += blockDim.x) {
+    const int a = (int)(idx / k), b = (int)(idx % k);
+    // top: local row a
+    double vt = 0.0, vb = 0.0;
+    {
+      const int64_t gi = L.rev ? (L.start + nl - 1 - a) : (L.start + a);
+      const int64_t gj = L.rev ? (L.start + nl + b) : (L.start - k + b);
+      const int64_t off = gi - gj;
+      if (L.top_nbr && gj >= 0 && gj < n && off >= -ku && off <= kl) vt = band[gj * ldab + ku + off];
+    }
+    {
+      const int64_t r = nl - k + a;
+      const int64_t gi = L.rev ? (L.start + nl - 1 - r) : (L.start + r);
+      const int64_t gj = L.rev ? (L.start - k + b) : (L.start + nl + b);
+      const int64_t off = gi - gj;
+      if (L.bot_nbr && gj >= 0 && gj < n && off >= -ku && off <= kl) vb = band[gj * ldab + ku + off];
+    }
+    Rt[idx] = vt;
+    Rb[idx] = vb;
+  }
+}
+
+int launch_couplings(const double *band, int64_t ldab, int kl, int ku, int64_t n, int k, const LeafDev *leaves,
+                     int nleaves, double *couple, void *stream) {
+  k_couplings<<<nleaves, 256, 0, (cudaStream_t)stream>>>(band, ldab, kl, ku, n, k, leaves, couple);
+  return (int)cudaGetLastError();
+}
+
+// Z init (Z already zeroed): R_top into rows [0,k) of columns [0,k) for leaves that
+// need the top spike (both neighbours), R_bot into rows [nl-k, nl) of columns [k, 2k).
+__global__ void k_zinit(const LeafDev *leaves, int k, const double *couple, double *zbuf, const int64_t *zoff) {
+  const LeafDev L = leaves[blockIdx.x];
+  const int64_t nl = L.len;
+  const int64_t kk = (int64_t)k * k;
+  const double *Rt = couple + (int64_t)blockIdx.x * 2 * kk;
+  const double *Rb = Rt + kk;
+  double *Z = zbuf + zoff[blockIdx.x];
+  const bool mid = L.top_nbr && L.bot_nbr;
+  for (int64_t idx = threadIdx.x; idx < kk; idx += blockDim.x) {
+    const int a = (int)(idx % k), b = (int)(idx / k);  // row a fastest -> coalesced column-major writes
+    if (mid) Z[(int64_t)b * nl + a] = Rt[(int64_t)a * k + b];
+    if (L.bot_nbr) Z[(int64_t)(k + b) * nl + (nl - k + a)] = Rb[(int64_t)a * k + b];
+  }
+}
+
+int launch_zinit(const LeafDev *leaves, int nleaves, int k, const double *couple, double *zbuf, const int64_t *zoff,
+                 int pivot, void *stream) {
+  (void)pivot;
+  k_zinit<<<nleaves, 256, 0, (cudaStream_t)stream>>>(leaves, k, couple, zbuf, zoff);
+  return (int)cudaGetLastError();
+}
+
+// -------------------------------------------------- non-pivoting block LU
+// Blocked right-looking band LU (no pivoting, diagonal boosting, Sec. 2.3) of one
+// leaf, with the L-sweep of the top spike fused as extra columns: for a middle
+// leaf, Z[:, 0:k] <- L^{-1} [R_top; 0] as the factorization proceeds (the first
+// of the three factor-stage sweeps of a middle partition, Table tab:sweeps).
+// Per block of NB columns: panel LU in shared memory (NB columns x NB+k rows),
+// U12 = L11^{-1} A12 (and the fused Z rows), then A22 -= L21 U12 on the k x k
+// window (and the fused Z rows below the panel).
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_factor_nopiv(const LeafDev *leaves, int k, int ldf, double *fb_all, double *dinv_all, double *zbuf,
+                   const int64_t *zoff, const unsigned long long *amax_bits, double boost_eps,
+                   unsigned long long *status) {
+  extern __shared__ double smem[];
+  const LeafDev L = leaves[blockIdx.x];
+  const int64_t nl = L.len;
+  double *fb = fb_all + L.start * (int64_t)ldf;
+  double *dinv = dinv_all + L.start;
+  const bool fuse = L.top_nbr && L.bot_nbr;
+  double *Z = zbuf + zoff[blockIdx.x];
+  const int kz = fuse ? k : 0;
+  const int PLD = NB + k + 1;
+  const int TLD = CW + 1;
+  double *P = smem;              // NB columns x PLD rows, column-major
+  double *T = smem + NB * PLD;   // NB rows x TLD, row-major
+  __shared__ double s_rinv;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double tau = boost_eps * __longlong_as_double((long long)*amax_bits);
+  unsigned long long nboost = 0;
+
+  for (int64_t j0 = 0; j0 < nl; j0 += NB) {
+    const int jb = (int)min((int64_t)NB, nl - j0);
+    const int prow = (int)min((int64_t)(jb + k), nl - j0);
+    // (a) panel load
+    for (int idx = tid; idx < NB * PLD; idx += NTHREADS) {
+      const int c = idx / PLD, r = idx - c * PLD;
+      double v = 0.0;
+      if (c < jb && r < prow && r - c <= k && c - r <= k) v = fb[(j0 + c) * ldf + k + r - c];
+      P[idx] = v;
+    }
+    __syncthreads();
+    // (b) panel LU
+    for (int c = 0; c < jb; ++c) {
+      if (tid == 0) {
+        double piv = P[c * PLD + c];
+        if (isnan(piv)) {
+          atomicOr(&status[2], 1ull);
+        } else if (!(fabs(piv) >= tau) || piv == 0.0) {
+          piv = (piv < 0.0) ? -tau : tau;
+          ++nboost;
+          if (piv == 0.0) {
+            const int64_t gcol = L.rev ? (L.start + nl - 1 - (j0 + c)) : (L.start + j0 + c);
+            atomicMin(&status[1], (unsigned long long)(gcol + 1));
+          }
+          P[c * PLD + c] = piv;
+        }
+        const double rinv = 1.0 / piv;
+        s_rinv = rinv;
+        dinv[j0 + c] = rinv;
+      }
+      __syncthreads();
+      const double rinv = s_rinv;
+      const int rlast = min(c + k, prow - 1);
+      const int nr = rlast - c;
+      for (int r = c + 1 + tid; r <= rlast; r += NTHREADS) P[c * PLD + r] *= rinv;
+      __syncthreads();
+      const int ncl = jb - c - 1;
+      for (int idx = tid; idx < nr * ncl; idx += NTHREADS) {
+        const int r = c + 1 + idx % nr, cc = c + 1 + idx / nr;
+        P[cc * PLD + r] -= P[c * PLD + r] * P[cc * PLD + c];
+      }
+      __syncthreads();
+    }
+    // (c) panel write-back
+    for (int idx = tid; idx < NB * PLD; idx += NTHREADS) {
+      const int c = idx / PLD, r = idx - c * PLD;
+      if (c < jb && r < prow && r - c <= k && c - r <= k) fb[(j0 + c) * ldf + k + r - c] = P[idx];
+    }
+    // (d)+(e) U12 / fused Z rows, column chunks of CW
+    const int kc = (int)min((int64_t)k, nl - j0 - jb);  // U12 columns and A22 rows present
+    const int ntot = kc + kz;
+    for (int q0 = 0; q0 < ntot; q0 += CW) {
+      const int nq = min(CW, ntot - q0);
+      __syncthreads();
+      for (int idx = tid; idx < NB * nq; idx += NTHREADS) {
+        const int a = idx / nq, qq = idx - a * nq, q = q0 + qq;
+        double v = 0.0;
+        if (a < jb) {
+          if (q < kc) {
+            if (jb + q - a <= k) v = fb[(j0 + jb + q) * ldf + k + a - jb - q];
+          } else {
+            v = Z[(int64_t)(q - kc) * nl + j0 + a];
+          }
+        }
+        T[a * TLD + qq] = v;
+      }
+      __syncthreads();
+      // TRSM with the unit lower L11 = P[0:jb, 0:jb]: one column per thread
+      for (int qq = tid; qq < nq; qq += NTHREADS) {
+        double x[NB];
+#pragma unroll
+        for (int a = 0; a < NB; ++a) x[a] = T[a * TLD + qq];
+#pragma unroll
+        for (int a = 1; a < NB; ++a) {
+          double s = x[a];
+#pragma unroll
+          for (int b = 0; b < a; ++b) s = fma(-P[b * PLD + a], x[b], s);
+          x[a] = s;
+        }
+#pragma unroll
+        for (int a = 0; a < NB; ++a) T[a * TLD + qq] = x[a];
+      }
+      __syncthreads();
+      for (int idx = tid; idx < NB * nq; idx += NTHREADS) {
+        const int a = idx % NB, qq = idx / NB, q = q0 + qq;
+        if (a < jb) {
+          if (q < kc) {
+            if (jb + q - a <= k) fb[(j0 + jb + q) * ldf + k + a - jb - q] = T[a * TLD + qq];
+          } else {
+            Z[(int64_t)(q - kc) * nl + j0 + a] = T[a * TLD + qq];
+          }
+        }
+      }
+      // GEMM: window rows i in [0, kc), columns of this chunk; lanes <-> rows, 16 columns per tile
+      const int RT = (kc + 31) / 32, CT = (nq + 15) / 16;
+      for (int tile = warp; tile < RT * CT; tile += NTHREADS / 32) {
+        const int i0 = (tile % RT) * 32, qq0 = (tile / RT) * 16;
+        const int i = i0 + lane;
+        const bool vi = i < kc;
+        const int qa = q0 + qq0;                       // first absolute column of the tile
+        const bool anyz = (q0 + min(qq0 + 16, nq) - 1) >= kc;
+        int astart = anyz ? (jb + i0 - k) : (jb + max(i0, qa) - k);
+        astart = max(astart, 0);
+        double acc[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int qq = qq0 + q, qabs = q0 + qq;
+          double v = 0.0;
+          if (vi && qq < nq) {
+            if (qabs < kc) v = fb[(j0 + jb + qabs) * ldf + k + i - qabs];
+            else v = Z[(int64_t)(qabs - kc) * nl + j0 + jb + i];
+          }
+          acc[q] = v;
+        }
+        for (int a = astart; a < jb; ++a) {
+          const double l = vi ? P[a * PLD + jb + i] : 0.0;
+          const double *trow = T + a * TLD + qq0;
+#pragma unroll
+          for (int q = 0; q < 16; ++q) acc[q] = fma(-l, trow[q], acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int qq = qq0 + q, qabs = q0 + qq;
+          if (vi && qq < nq) {
+            if (qabs < kc) fb[(j0 + jb + qabs) * ldf + k + i - qabs] = acc[q];
+            else Z[(int64_t)(qabs - kc) * nl + j0 + jb + i] = acc[q];
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && nboost) atomicAdd(&status[0], nboost);
+}
+
+int launch_factor_nopiv(const LeafDev *leaves, int nleaves, int k, int ldf, double *fb, double *dinv, double *zbuf,
+                        const int64_t *zoff, const unsigned long long *amax_bits, double boost_eps,
+                        unsigned long long *status, void *stream) {
+  const size_t smem = sizeof(double) * ((size_t)NB * (NB + k + 1) + (size_t)NB * (CW + 1));
+  cudaError_t e = cudaFuncSetAttribute(k_factor_nopiv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  k_factor_nopiv<<<nleaves, NTHREADS, smem, (cudaStream_t)stream>>>(leaves, k, ldf, fb, dinv, zbuf, zoff, amax_bits,
+                                                                     boost_eps, status);
+  return (int)cudaGetLastError();
+}
+
+// ------------------------------------------------------ pivoting block LU
+// Unblocked banded GEPP of one leaf (Sec. 5.1): the pivot is the first entry of
+// largest magnitude among the k+1 band candidates; rows are swapped across the
+// columns j..j+2k (U fill up to kl+ku superdiagonals); multipliers are stored
+// unpermuted (interleaved form, swaps applied during the sweeps).  The UL of the
+// last block is this LU of Q A Q (Sec. 5.2).
+__global__ void __launch_bounds__(NTHREADS)
+    k_factor_piv(const LeafDev *leaves, int k, int ldf, double *fb_all, double *dinv_all, int *ipiv_all,
+                 unsigned long long *status) {
+  const LeafDev L = leaves[blockIdx.x];
+  const int64_t nl = L.len;
+  double *fb = fb_all + L.start * (int64_t)ldf;
+  double *dinv = dinv_all + L.start;
+  int *ipiv = ipiv_all + L.start;
+  const int dofs = 2 * k;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ int s_p, s_zero;
+  for (int64_t j = 0; j < nl; ++j) {
+    const int64_t last = min(j + k, nl - 1);
+    if (warp == 0) {
+      double best = -1.0;
+      int64_t bi = j;
+      for (int64_t r = j + lane; r <= last; r += 32) {
+        const double v = fabs(fb[j * ldf + dofs + r - j]);
+        if (v > best) {
+          best = v;
+          bi = r;
+        }
+      }
+      for (int o = 16; o; o >>= 1) {
+        const double ov = __shfl_down_sync(FULLMASK, best, o);
+        const int64_t oi = __shfl_down_sync(FULLMASK, bi, o);
+        if (ov > best || (ov == best && oi < bi)) {
+          best = ov;
+          bi = oi;
+        }
+      }
+      if (lane == 0) {
+        s_p = (int)(bi - j);
+        s_zero = !(best > 0.0);
+        if (s_zero) {
+          const int64_t gcol = L.rev ? (L.start + nl - 1 - j) : (L.start + j);
+          atomicMin(&status[1], (unsigned long long)(gcol + 1));
+          if (isnan(best)) atomicOr(&status[2], 1ull);
+        }
+      }
+    }
+    __syncthreads();
+    const int64_t p = j + s_p;
+    if (tid == 0) ipiv[j] = (int)p;
+    if (s_zero) {
+      if (tid == 0) dinv[j] = 0.0;
+      __syncthreads();
+      continue;
+    }
+    const int64_t cmax = min(j + 2 * k, nl - 1);
+    if (p != j) {
+      for (int64_t c = j + tid; c <= cmax; c += NTHREADS) {
+        double *a = &fb[c * ldf + dofs + j - c];
+        double *b = &fb[c * ldf + dofs + p - c];
+        const double t = *a;
+        *a = *b;
+        *b = t;
+      }
+    }
+    __syncthreads();
+    const double rinv = 1.0 / fb[j * ldf + dofs];
+    if (tid == 0) dinv[j] = rinv;
+    for (int64_t r = j + 1 + tid; r <= last; r += NTHREADS) fb[j * ldf + dofs + r - j] *= rinv;
+    __syncthreads();
+    const int nr = (int)(last - j);
+    const int ncl = (int)(cmax - j);
+    for (int idx = tid; idx < nr * ncl; idx += NTHREADS) {
+      const int64_t r = j + 1 + idx % nr, c = j + 1 + idx / nr;
+      fb[c * ldf + dofs + r - c] -= fb[j * ldf + dofs + r - j] * fb[c * ldf + dofs + j - c];
+    }
+    __syncthreads();
+  }
+}
+
+int launch_factor_piv(const LeafDev *leaves, int nleaves, int k, int ldf, double *fb, double *dinv, int *ipiv,
+                      unsigned long long *status, void *stream) {
+  k_factor_piv<<<nleaves, NTHREADS, 0, (cudaStream_t)stream>>>(leaves, k, ldf, fb, dinv, ipiv, status);
+  return (int)cudaGetLastError();
+}
+
+// ------------------------------------------------------ blocked sweep engine
+// X = T^{-1} G over rows [r0, r1) of one leaf, T one of LN/UN/UT/LT (see internal.h).
+// Rows are processed in blocks of NB in sweep order; per block:
+//   (1) acc = G(block) - T(block, window) X(window)   (GEMM over the kw window rows,
+//       lanes <-> block rows, warps <-> column groups, inner dimension split when
+//       there are few columns),
+//   (2) in-block triangular solve (lanes <-> columns when there are many columns,
+//       lanes <-> rows with shuffles otherwise),
+//   (3) store.
+// Coefficients: LN/UN use column c of the band, UT/LT column r (transposed access).
+constexpr int WCH = 256;  // window rows per staged chunk
+constexpr int SCW = 128;  // RHS columns per sweep pass: 8 warps x 16 accumulators
+
+template <int KIND>
+__device__ __forceinline__ double coef(const double *fb, int ldf, int dofs, int64_t r, int64_t c) {
+  if (KIND == LN || KIND == UN) return fb[c * ldf + dofs + r - c];
+  return fb[r * ldf + dofs + c - r];
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(NTHREADS, 1) k_sweep(const SweepDesc *descs, int kw, int ldf, int dofs) {
+  extern __shared__ double sm[];
+  const SweepDesc D = descs[blockIdx.x];
+  if (D.ncols <= 0 || D.r1 <= D.r0) return;
+  constexpr bool FWD = (KIND == LN || KIND == UT);
+  constexpr bool UNIT = (KIND == LN || KIND == LT);
+  const int GLD = SCW + 1;
+  double *Tw = sm;                 // WCH x NB   : Tw[j*NB + a] = T(row(a), wrow(j))
+  double *Td = Tw + WCH * NB;      // NB x NB    : Td[a'*NB + a] = T(row(a), row(a'))
+  double *dsm = Td + NB * NB;      // NB
+  double *Gs = dsm + NB;           // NB x GLD
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nwarps = NTHREADS / 32;
+
+  for (int c0 = 0; c0 < D.ncols; c0 += SCW) {
+    const int cw = min(SCW, D.ncols - c0);
+    int nsplit = (cw < nwarps) ? (nwarps / cw) : 1;
+    const int groups = nwarps / nsplit;
+    const int cpw = (cw + groups - 1) / groups;
+    const int grp = warp % groups, split = warp / groups;
+    const int col_base = c0 + grp * cpw;
+    const int nblk = (D.r1 - D.r0 + NB - 1) / NB;
+    for (int bk = 0; bk < nblk; ++bk) {
+      int64_t b0, b1;
+      int nbk;
+      if (FWD) {
+        b0 = D.r0 + (int64_t)bk * NB;
+        nbk = (int)min((int64_t)NB, D.r1 - b0);
+        b1 = 0;
+      } else {
+        b1 = D.r1 - (int64_t)bk * NB;
+        nbk = (int)min((int64_t)NB, b1 - D.r0);
+        b0 = 0;
+      }
+      auto row = [&](int a) -> int64_t { return FWD ? (b0 + a) : (b1 - 1 - a); };
+      auto wrow = [&](int j) -> int64_t { return FWD ? (b0 - kw + j) : (b1 + j); };
+      int jlo, jhi;
+      if (FWD) {
+        jlo = (int)max((int64_t)0, D.r0 - (b0 - kw));
+        jhi = kw;
+      } else {
+        jlo = 0;
+        jhi = (int)min((int64_t)kw, D.r1 - b1);
+      }
+      __syncthreads();
+      for (int idx = tid; idx < NB * NB; idx += NTHREADS) {
+        const int ap = idx / NB, a = idx - ap * NB;
+        double v = 0.0;
+        if (ap < a && a < nbk && a - ap <= kw) v = coef<KIND>(D.fb, ldf, dofs, row(a), row(ap));
+        Td[idx] = v;
+      }
+      for (int a = tid; a < NB; a += NTHREADS) dsm[a] = (a < nbk) ? (UNIT ? 1.0 : D.dinv[row(a)]) : 0.0;
+
+      double acc[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+      for (int jc0 = jlo; jc0 < jhi; jc0 += WCH) {
+        const int jce = min(jhi, jc0 + WCH);
+        __syncthreads();
+        for (int idx = tid; idx < (jce - jc0) * NB; idx += NTHREADS) {
+          const int jj = idx / NB, a = idx - jj * NB, j = jc0 + jj;
+          double v = 0.0;
+          if (a < nbk && (FWD ? (j >= a) : (j <= kw - 1 - a))) v = coef<KIND>(D.fb, ldf, dofs, row(a), wrow(j));
+          Tw[idx] = v;
+        }
+        __syncthreads();
+        const int len = jce - jc0;
+        const int per = (len + nsplit - 1) / nsplit;
+        const int js = jc0 + split * per, je = min(jce, js + per);
+        for (int j = js; j < je; ++j) {
+          const double t = Tw[(j - jc0) * NB + lane];
+          const double *xr = D.x + wrow(j) * D.x_rs;
+#pragma unroll
+          for (int q = 0; q < 16; ++q)
+            if (q < cpw && col_base + q < c0 + cw) acc[q] = fma(t, xr[(int64_t)(col_base + q) * D.x_cs], acc[q]);
+        }
+      }
+      __syncthreads();
+      for (int s = 0; s < nsplit; ++s) {
+        if (split == s) {
+          if (lane < nbk) {
+            const int64_t r = row(lane);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+              const int col = col_base + q;
+              if (q < cpw && col < c0 + cw) {
+                double g;
+                if (s == 0) {
+                  g = D.ga[r * D.ga_rs + (int64_t)col * D.ga_cs];
+                  if (D.gb) g = fma(D.gb_scale, D.gb[r * D.gb_rs + (int64_t)col * D.gb_cs], g);
+                } else {
+                  g = Gs[lane * GLD + (col - c0)];
+                }
+                Gs[lane * GLD + (col - c0)] = g - acc[q];
+              }
+            }
+          } else if (s == 0) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+              const int col = col_base + q;
+              if (q < cpw && col < c0 + cw) Gs[lane * GLD + (col - c0)] = 0.0;
+            }
+          }
+        }
+        __syncthreads();
+      }
+      // in-block triangular solve
+      if (cw >= 64) {
+        for (int cc = tid; cc < cw; cc += NTHREADS) {
+          double xv[NB];
+#pragma unroll
+          for (int a = 0; a < NB; ++a) {
+            double s = Gs[a * GLD + cc];
+#pragma unroll
+            for (int ap = 0; ap < a; ++ap) s = fma(-Td[ap * NB + a], xv[ap], s);
+            xv[a] = s * dsm[a];
+          }
+#pragma unroll
+          for (int a = 0; a < NB; ++a) Gs[a * GLD + cc] = xv[a];
+        }
+      } else {
+        for (int cc = warp; cc < cw; cc += nwarps) {
+          double s = Gs[lane * GLD + cc];
+          double xf = 0.0;
+#pragma unroll
+          for (int ap = 0; ap < NB; ++ap) {
+            const double xa = __shfl_sync(FULLMASK, s, ap) * dsm[ap];
+            if (lane == ap) xf = xa;
+            if (lane > ap) s = fma(-Td[ap * NB + lane], xa, s);
+          }
+          Gs[lane * GLD + cc] = xf;
+        }
+      }
+      __syncthreads();
+      for (int idx = tid; idx < nbk * cw; idx += NTHREADS) {
+        const int a = idx % nbk, cc = idx / nbk;
+        D.x[row(a) * D.x_rs + (int64_t)(c0 + cc) * D.x_cs] = Gs[a * GLD + cc];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+int launch_sweep(int kind, const SweepDesc *descs, int ndesc, int kw, int ldf, int dofs, int maxcols, void *stream) {
+  (void)maxcols;
+  if (ndesc <= 0) return 0;
+  const size_t smem = sizeof(double) * ((size_t)WCH * NB + NB * NB + NB + (size_t)NB * (SCW + 1));
+  cudaError_t e = cudaSuccess;
+  cudaStream_t s = (cudaStream_t)stream;
+  switch (kind) {
+    case LN:
+      e = cudaFuncSetAttribute(k_sweep<LN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) k_sweep<LN><<<ndesc, NTHREADS, smem, s>>>(descs, kw, ldf, dofs);
+      break;
+    case UN:
+      e = cudaFuncSetAttribute(k_sweep<UN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) k_sweep<UN><<<ndesc, NTHREADS, smem, s>>>(descs, kw, ldf, dofs);
+      break;
+    case UT:
+      e = cudaFuncSetAttribute(k_sweep<UT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) k_sweep<UT><<<ndesc, NTHREADS, smem, s>>>(descs, kw, ldf, dofs);
+      break;
+    default:
+      e = cudaFuncSetAttribute(k_sweep<LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) k_sweep<LT><<<ndesc, NTHREADS, smem, s>>>(descs, kw, ldf, dofs);
+      break;
+  }
+  if (e != cudaSuccess) return (int)e;
+  return (int)cudaGetLastError();
+}
+
+// ------------------------------------------------ pivoted L sweeps (Sec. 5.1)
+// In place on X, rows [r0, r1) with r1 = nl.  One warp per RHS column, lanes over rows.
+//   LN (forward):  for j: swap X_j <-> X_ipiv[j]; X_{j+1..j+k} -= l_{.,j} X_j
+//   LT (backward): for j descending: X_j -= sum_i l_{i,j} X_i; swap X_j <-> X_ipiv[j]
+template <int KIND>
+__global__ void __launch_bounds__(NTHREADS) k_piv_sweep(const SweepDesc *descs, int k, int ldf, int dofs) {
+  const SweepDesc D = descs[blockIdx.x];
+  if (D.ncols <= 0 || D.r1 <= D.r0) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int col = warp; col < D.ncols; col += NTHREADS / 32) {
+    double *x = D.x + (int64_t)col * D.x_cs;
+    const int64_t rs = D.x_rs;
+    if (KIND == LN) {
+      for (int64_t j = D.r0; j < D.r1; ++j) {
+        const int64_t p = D.ipiv[j];
+        if (lane == 0 && p != j) {
+          const double t = x[j * rs];
+          x[j * rs] = x[p * rs];
+          x[p * rs] = t;
+        }
+        __syncwarp();
+        const double xj = x[j * rs];
+        const int64_t last = min(j + (int64_t)k, (int64_t)D.r1 - 1);
+        for (int64_t i = j + 1 + lane; i <= last; i += 32) x[i * rs] = fma(-D.fb[j * ldf + dofs + i - j], xj, x[i * rs]);
+        __syncwarp();
+      }
+    } else {
+      for (int64_t j = D.r1 - 1; j >= D.r0; --j) {
+        const int64_t last = min(j + (int64_t)k, (int64_t)D.r1 - 1);
+        double s = 0.0;
+        for (int64_t i = j + 1 + lane; i <= last; i += 32) s = fma(D.fb[j * ldf + dofs + i - j], x[i * rs], s);
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(FULLMASK, s, o);
+        if (lane == 0) {
+          const double v = x[j * rs] - s;
+          const int64_t p = D.ipiv[j];
+          if (p != j) {
+            x[j * rs] = x[p * rs];
+            x[p * rs] = v;
+          } else {
+            x[j * rs] = v;
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+}
+
+int launch_piv_sweep(int kind, const SweepDesc *descs, int ndesc, int k, int ldf, int dofs, void *stream) {
+  if (ndesc <= 0) return 0;
+  if (kind == LN)
+    k_piv_sweep<LN><<<ndesc, NTHREADS, 0, (cudaStream_t)stream>>>(descs, k, ldf, dofs);
+  else
+    k_piv_sweep<LT><<<ndesc, NTHREADS, 0, (cudaStream_t)stream>>>(descs, k, ldf, dofs);
+  return (int)cudaGetLastError();
+}
+
+// ------------------------------------------------------------ tips (level 0)
+// Spike tips of each leaf in the global frame from the swept Z:
+//   forward leaf : W = Z_top, V = Z_bot;   reversed leaf: V = Q Z_top, W = Q Z_bot.
+// spk layout: [V/W][leaf][top/bottom] k x k row-major (level 0).
+__global__ void k_tips0(const LeafDev *leaves, int nleaves, int k, const double *zbuf, const int64_t *zoff,
+                        double *spk) {
+  const int i = blockIdx.x;
+  const LeafDev L = leaves[i];
+  const int64_t nl = L.len;
+  const double *Z = zbuf + zoff[i];
+  const int64_t kk = (int64_t)k * k;
+  const bool mid = L.top_nbr && L.bot_nbr;
+  for (int64_t idx = threadIdx.x; idx < kk; idx += blockDim.x) {
+    const int j = (int)(idx / k), b = (int)(idx % k);  // tip row j, column b
+    // local rows of global top/bottom tip row j
+    const int64_t lt = L.rev ? (nl - 1 - j) : j;             // global top row j
+    const int64_t lb = L.rev ? (k - 1 - j) : (nl - k + j);   // global bottom row j
+    const double *Ztop = Z, *Zbot = Z + (int64_t)k * nl;
+    // spike coupled through the local top rows is W (fwd) / V (rev); through the bottom: V (fwd) / W (rev)
+    const int s_top = L.rev ? 0 : 1, s_bot = L.rev ? 1 : 0;
+    if (mid) {
+      spk[((int64_t)(s_top * nleaves + i) * 2 + 0) * kk + idx] = Ztop[(int64_t)b * nl + lt];
+      spk[((int64_t)(s_top * nleaves + i) * 2 + 1) * kk + idx] = Ztop[(int64_t)b * nl + lb];
+      spk[((int64_t)(s_bot * nleaves + i) * 2 + 0) * kk + idx] = Zbot[(int64_t)b * nl + lt];
+      spk[((int64_t)(s_bot * nleaves + i) * 2 + 1) * kk + idx] = Zbot[(int64_t)b * nl + lb];
+    } else if (L.bot_nbr) {
+      // first-like leaf: only the tip at the local bottom of the bottom spike exists
+      if (L.rev) spk[((int64_t)(s_bot * nleaves + i) * 2 + 0) * kk + idx] = Zbot[(int64_t)b * nl + lt];
+      else spk[((int64_t)(s_bot * nleaves + i) * 2 + 1) * kk + idx] = Zbot[(int64_t)b * nl + lb];
+    }
+  }
+}
+
+int launch_tips0(const LeafDev *leaves, int nleaves, int k, const double *zbuf, const int64_t *zoff, double *spk,
+                 void *stream) {
+  k_tips0<<<nleaves, 256, 0, (cudaStream_t)stream>>>(leaves, nleaves, k, zbuf, zoff, spk);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace spk

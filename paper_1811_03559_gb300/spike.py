@@ -1,0 +1,191 @@
+"""Thin ctypes binding of libspike.so (C ABI in include/spike.h).
+
+Argument marshalling only: every step of the factorization and solves runs in
+the library's CUDA kernels.  If libspike.so is missing, or no GPU is present,
+calls raise -- there is no CPU fallback.
+
+Arrays: `band` has shape (n, kl+ku+1) (LAPACK band layout, column-major), and
+right-hand sides have shape (nrhs, n) or (n,), row-contiguous (column-major
+n x nrhs).  They may be CUDA torch tensors (used in place, on the current torch
+stream) or NumPy arrays (host memory; the library stages them through the GPU).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libspike.so")
+_lib = None
+
+SPIKE_ENOMEM, SPIKE_ECUDA, SPIKE_EHANDLE, SPIKE_ENOTSUP, SPIKE_ENOGPU = -1001, -1002, -1003, -1004, -1005
+
+
+class SpikeInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("kl", ctypes.c_int32), ("ku", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("p_requested", ctypes.c_int32), ("p_effective", ctypes.c_int32), ("m", ctypes.c_int32),
+                ("P", ctypes.c_int32), ("r", ctypes.c_int32), ("leaves", ctypes.c_int32),
+                ("levels", ctypes.c_int32), ("pivot", ctypes.c_int32), ("n1", ctypes.c_int64),
+                ("n2", ctypes.c_int64), ("n3", ctypes.c_int64), ("R12", ctypes.c_double), ("R13", ctypes.c_double),
+                ("K", ctypes.c_double), ("boosts", ctypes.c_int64), ("zero_pivot_col", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class SpikeOptions(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_double), ("nrhs_hint", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("stream", ctypes.c_void_p), ("reserved", ctypes.c_int64 * 4)]
+
+
+EXPORTS = ["spike_plan", "spike_factor", "spike_factor_ex", "spike_solve", "spike_solve_ex", "spike_set_stream",
+           "spike_get_info", "spike_get_tips", "spike_backward_error", "spike_free", "spike_strerror",
+           "spike_last_cuda_error"]
+
+
+class SpikeError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = "%s failed: %d (%s)" % (where, code, lib().spike_strerror(code).decode())
+        if code == SPIKE_ECUDA:
+            msg += ": " + lib().spike_last_cuda_error().decode()
+        super().__init__(msg)
+
+
+def lib():
+    """Load libspike.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libspike.so not found at %s: run `python -m paper_1811_03559_gb300.build`" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        i64, i32, vp, dp = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p
+        L.spike_plan.argtypes = [i64, i32, i32, i32, ctypes.POINTER(SpikeOptions), ctypes.POINTER(SpikeInfo), vp, vp]
+        L.spike_factor.argtypes = [dp, i64, i32, i32, i32, i32, ctypes.POINTER(vp)]
+        L.spike_factor_ex.argtypes = [dp, i64, i64, i32, i32, i32, i32, ctypes.POINTER(SpikeOptions),
+                                      ctypes.POINTER(vp)]
+        L.spike_solve.argtypes = [vp, dp, i32, ctypes.c_char]
+        L.spike_solve_ex.argtypes = [vp, dp, i64, i32, ctypes.c_char]
+        L.spike_set_stream.argtypes = [vp, vp]
+        L.spike_get_info.argtypes = [vp, ctypes.POINTER(SpikeInfo)]
+        L.spike_get_tips.argtypes = [vp, i32, dp]
+        L.spike_backward_error.argtypes = [dp, i64, i64, i32, i32, dp, dp, i32, ctypes.c_char, vp, dp]
+        L.spike_free.argtypes = [vp]
+        L.spike_free.restype = None
+        L.spike_strerror.argtypes = [i32]
+        L.spike_strerror.restype = ctypes.c_char_p
+        L.spike_last_cuda_error.argtypes = []
+        L.spike_last_cuda_error.restype = ctypes.c_char_p
+        for nm in EXPORTS:
+            f = getattr(L, nm)
+            if nm not in ("spike_free", "spike_strerror", "spike_last_cuda_error"):
+                f.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    if _is_torch(x):
+        assert x.is_contiguous() and str(x.dtype) == "torch.float64"
+        return ctypes.c_void_p(x.data_ptr())
+    assert isinstance(x, np.ndarray) and x.dtype == np.float64 and x.flags["C_CONTIGUOUS"]
+    return x.ctypes.data_as(ctypes.c_void_p)
+
+
+def _torch_stream(x):
+    if _is_torch(x) and x.is_cuda:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream(x.device).cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+def plan(n, kl, ku, p, K=0.0, nrhs_hint=0):
+    """Partition plan (Sec. 3.1, 3.3) without a GPU: (info dict, block offsets, block flags)."""
+    info = SpikeInfo()
+    opt = SpikeOptions(K=K, nrhs_hint=nrhs_hint)
+    offs = np.zeros(p + 2, dtype=np.int64)
+    flags = np.zeros(p + 2, dtype=np.int32)
+    rc = lib().spike_plan(n, kl, ku, p, ctypes.byref(opt), ctypes.byref(info), offs.ctypes.data_as(ctypes.c_void_p),
+                          flags.ctypes.data_as(ctypes.c_void_p))
+    if rc != 0:
+        raise SpikeError(rc, "spike_plan")
+    nb = info.leaves
+    return info.as_dict(), offs[: nb + 1].copy(), flags[:nb].copy()
+
+
+class Factorization:
+    """A SPIKE factorization handle (spike_factor_ex); free with .free() or by garbage collection."""
+
+    def __init__(self, band, kl, ku, p, pivot=0, K=0.0, nrhs_hint=0, stream=None):
+        n, ldab = band.shape
+        self.n, self.kl, self.ku = n, kl, ku
+        s = _torch_stream(band) if stream is None else ctypes.c_void_p(stream)
+        self._opt = SpikeOptions(K=K, nrhs_hint=nrhs_hint, stream=s)
+        h = ctypes.c_void_p()
+        rc = lib().spike_factor_ex(_ptr(band), ldab, n, kl, ku, p, pivot, ctypes.byref(self._opt), ctypes.byref(h))
+        self._h = h
+        self.status = rc
+        if rc < 0:
+            raise SpikeError(rc, "spike_factor_ex")
+
+    def solve(self, F, trans="N"):
+        """Overwrite F (shape (nrhs, n) or (n,)) with op(A)^{-1} F.  Returns F."""
+        nrhs = 1 if F.ndim == 1 else F.shape[0]
+        assert F.shape[-1] == self.n
+        rc = lib().spike_solve_ex(self._h, _ptr(F), self.n, nrhs, trans.encode())
+        if rc != 0:
+            raise SpikeError(rc, "spike_solve_ex")
+        return F
+
+    def set_stream(self, stream):
+        rc = lib().spike_set_stream(self._h, ctypes.c_void_p(stream))
+        if rc != 0:
+            raise SpikeError(rc, "spike_set_stream")
+
+    def info(self):
+        out = SpikeInfo()
+        rc = lib().spike_get_info(self._h, ctypes.byref(out))
+        if rc != 0:
+            raise SpikeError(rc, "spike_get_info")
+        return out.as_dict()
+
+    def tips(self, level=0):
+        """Spike tips of a merge level: array (leaves, 4, k, k) with [V_t, V_b, W_t, W_b]."""
+        inf = self.info()
+        out = np.zeros((inf["leaves"], 4, inf["k"], inf["k"]))
+        rc = lib().spike_get_tips(self._h, level, out.ctypes.data_as(ctypes.c_void_p))
+        if rc != 0:
+            raise SpikeError(rc, "spike_get_tips")
+        return out
+
+    def free(self):
+        if self._h:
+            lib().spike_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def factor(band, kl, ku, p, pivot=0, **kw):
+    return Factorization(band, kl, ku, p, pivot, **kw)
+
+
+def backward_error(band, kl, ku, X, F, trans="N"):
+    """Per-column backward error on the GPU (device torch tensors)."""
+    n, ldab = band.shape
+    nrhs = 1 if X.ndim == 1 else X.shape[0]
+    out = np.zeros(nrhs)
+    rc = lib().spike_backward_error(_ptr(band), ldab, n, kl, ku, _ptr(X), _ptr(F), nrhs, trans.encode(),
+                                    _torch_stream(X), out.ctypes.data_as(ctypes.c_void_p))
+    if rc != 0:
+        raise SpikeError(rc, "spike_backward_error")
+    return out

@@ -1,0 +1,105 @@
+"""Host-side tests: the partition planner (Sec. 3.1, 3.3) and the C ABI surface (no GPU needed)."""
+import json
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1811_03559_gb300 import spike
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def built():
+    if not os.path.exists(spike.LIB_PATH):
+        from paper_1811_03559_gb300 import build
+        build.build()
+    return spike.lib()
+
+
+def test_abi_exports_every_declared_symbol(built):
+    hdr = open(os.path.join(ROOT, "include", "spike.h")).read()
+    names = set(re.findall(r"\b(spike_[a-z_]+)\s*\(", hdr))
+    assert {"spike_factor", "spike_solve", "spike_free", "spike_plan"} <= names
+    for nm in names:
+        assert hasattr(built, nm), nm
+
+
+@pytest.mark.parametrize("case", json.load(open(os.path.join(GOLD, "thread_distribution.json")))["cases"])
+def test_thread_distribution(built, case):
+    info, offs, flags = spike.plan(1 << 20, 4, 4, case["t"])
+    assert (info["P"], info["r"], info["p_effective"]) == (case["P"], case["r"], case["t_eff"])
+    assert info["leaves"] == case["P"] + case["r"]
+    # 2x2 pairs are partitions 2..r+1: leaves 1..2r alternate top (LU) / bottom (UL)
+    for j in range(case["r"]):
+        assert flags[1 + 2 * j] == 2 and flags[2 + 2 * j] == 5
+    assert flags[0] == 0
+    if info["leaves"] > 1:
+        assert flags[-1] == 1  # last block: UL
+    assert offs[0] == 0 and offs[-1] == 1 << 20 and np.all(np.diff(offs) > 0)
+
+
+def test_ratios_match_paper_table(built):
+    g = json.load(open(os.path.join(GOLD, "partition_ratios.json")))
+    for row in g["rows"]:
+        info, _, _ = spike.plan(10**6, g["k"], g["k"], 12, K=g["K"], nrhs_hint=row["nrhs"])
+        assert abs(info["R13"] - row["R13"]) <= 0.1 + 1e-12
+        assert abs(info["R12"] - row["R12"]) <= 0.05 + 1e-12
+        assert info["R12"] == pytest.approx(info["R13"] / 2)
+    lim, _, _ = spike.plan(10**6, g["k"], g["k"], 12, K=g["K"], nrhs_hint=0)
+    assert lim["R13"] == pytest.approx(g["factor_limit"]["R13"])
+    assert lim["R12"] == pytest.approx(g["factor_limit"]["R12"])
+    big, _, _ = spike.plan(10**6, 1, 1, 12, K=g["K"], nrhs_hint=10**7)
+    assert big["R13"] == pytest.approx(g["solve_limit"]["R13"], abs=1e-5)
+
+
+@pytest.mark.parametrize("t", [4, 5, 6, 9, 14, 64, 148, 192])
+@pytest.mark.parametrize("K,rho", [(2.0, 0), (4 / 3, 0.5), (2.0, 1.0)])
+def test_partition_sizes_follow_ratios(built, t, K, rho):
+    n, k = 1_048_576, 128
+    info, offs, flags = spike.plan(n, k, k, t, K=K, nrhs_hint=int(rho * k))
+    sizes = np.diff(offs)
+    assert sizes.sum() == n
+    P, r = info["P"], info["r"]
+    n1, n2, n3 = info["n1"], info["n2"], info["n3"]
+    # constraint n = 2 n1 + r n2 + (P-2-r) n3 (before the remainder rows)
+    assert 0 <= n - (2 * n1 + r * n2 + (P - 2 - r) * n3) <= P
+    assert n1 / n3 == pytest.approx(info["R13"], rel=1e-3)
+    assert abs(n2 - 2 * n3) <= 1
+    # leaves: ends are n1, pairs split n2 floor/ceil, singles n3 (+ at most one remainder row)
+    assert sizes[0] == n1 and sizes[-1] == n1
+    for j in range(r):
+        assert sizes[1 + 2 * j] + sizes[2 + 2 * j] in (n2, n2 + 1)
+    for s in sizes[1 + 2 * r:-1]:
+        assert s in (n3, n3 + 1)
+
+
+def test_small_matrix_lowers_worker_count(built):
+    # every block needs >= 2k rows; with n = 10 k only a few blocks fit
+    info, offs, _ = spike.plan(1000, 50, 50, 64)
+    assert np.all(np.diff(offs) >= 100)
+    assert info["p_effective"] < 64
+
+
+def test_bad_arguments(built):
+    with pytest.raises(spike.SpikeError) as e:
+        spike.plan(0, 2, 2, 4)
+    assert e.value.code == -1
+    with pytest.raises(spike.SpikeError) as e:
+        spike.plan(100, 2, 2, 0)
+    assert e.value.code == -4
+    with pytest.raises(spike.SpikeError) as e:
+        spike.plan(100, -1, 2, 2)
+    assert e.value.code == -2
+    import ctypes
+    h = ctypes.c_void_p()
+    assert built.spike_factor(None, 100, 2, 2, 4, 0, ctypes.byref(h)) == -1
+    x = np.zeros((100, 5))
+    assert built.spike_factor_ex(x.ctypes.data_as(ctypes.c_void_p), 5, 0, 2, 2, 4, 0, None, ctypes.byref(h)) == -3
+    assert built.spike_factor_ex(x.ctypes.data_as(ctypes.c_void_p), 4, 100, 2, 2, 4, 0, None, ctypes.byref(h)) == -2
+    assert built.spike_factor_ex(x.ctypes.data_as(ctypes.c_void_p), 5, 100, 2, 2, 4, 3, None, ctypes.byref(h)) == -7
+    assert built.spike_solve(None, None, 1, b"N") == spike.SPIKE_EHANDLE
+    assert built.spike_strerror(-1002).decode().startswith("CUDA")
