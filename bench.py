@@ -1,0 +1,356 @@
+#!/usr/bin/env python3
+"""Benchmark of the recursive SPIKE hot path on GB300.
+
+One step = spike_factor + spike_solve('N') + spike_solve('T') + spike_free on the
+workload n = 1,048,576, kl = ku = 128, p = 148 workers (128 partitions, 20 of
+them run as SPIKE 2x2 pairs: 148 blocks), nrhs = 64, dominance factor 1.01,
+synthetic inputs from paper_1811_03559_gb300.inputs (seed 1).
+
+Printed JSON line (rank 0):
+  value   whole-job GB/s of algorithmic bytes: 16n(2k+1) for the factorization
+          (band in, factors out) + per solve 8n(2k+1) (factors read) + 16 n nrhs
+          (F in, X out), with inputs resident in HBM, timed with CUDA events;
+  e2e     the same metric through the C ABI with pinned HOST buffers (host<->device
+          copies inside the timed calls);
+  roofline  the dominant kernel (block LU + fused spike sweep): method FP64 flops
+          per launch / its mean duration from events recorded on the library's
+          stream, against the FP64 FMA peak;
+  cpu_baseline  the CPU oracle (banded GEPP + N and T solves) on a bounded sample.
+Multi-GPU: replicas only (each rank solves its own copy; the method has no
+data-parallel exchange within one system on one GPU), value = sum over ranks.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "n=1M k=128 factor+solve GB/s & % roofline vs FP64; serving p50/p99, solves/s"
+# FP64 FMA peak derived from unit counts and clock: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP64_PEAK_NOTE = "derived: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (the recipe's 1.25 TFLOP/s nominal); " \
+                 "a DFMA throughput probe measured 1.199 TFLOP/s"
+
+
+def alg_bytes(n, k, m, nsolves=2):
+    return 16.0 * n * (2 * k + 1) + nsolves * (8.0 * n * (2 * k + 1) + 16.0 * n * m)
+
+
+def plan_groups(offs, flags):
+    """Merge levels as lists of (a, b, c) leaf ranges (mirrors the planner, Sec. 2.2 / 3.1)."""
+    nb = len(offs) - 1
+    groups = [(i, i + 1) for i in range(nb)]
+    levels = []
+    if any(f & 2 for f in flags):
+        lv, merged, i = [], [], 0
+        while i < nb:
+            if flags[i] & 2:
+                lv.append((i, i + 1, i + 2))
+                merged.append((i, i + 2))
+                i += 2
+            else:
+                merged.append((i, i + 1))
+                i += 1
+        levels.append(lv)
+        groups = merged
+    while len(groups) > 1:
+        lv, nxt = [], []
+        for j in range(0, len(groups), 2):
+            lv.append((groups[j][0], groups[j][1], groups[j + 1][1]))
+            nxt.append((groups[j][0], groups[j + 1][1]))
+        levels.append(lv)
+        groups = nxt
+    return levels
+
+
+def method_flops(offs, flags, k, m):
+    """FP64 flops the method performs (Sec. 2.3 sweep counts, Sec. 2.2 reduced system)."""
+    nb = len(offs) - 1
+    sizes = np.diff(offs).astype(np.float64)
+    f = {"block_lu": 0.0, "factor_spikes": 0.0, "factor_reduced": 0.0, "solve_n": 0.0, "solve_t": 0.0}
+    k = float(k)
+    for i, nl in enumerate(sizes):
+        mid = 0 < i < nb - 1
+        lu = nl * (2 * k * k + k)                  # band LU: k multipliers + k x k update per column
+        f["block_lu"] += lu + (2 * nl * k * k if mid else 0.0)   # + fused L-sweep of the top spike
+        if nb > 1:  # the other spike sweeps run in the same launch as the block LU
+            f["block_lu"] += (nl * (4 * k * k + 2 * k)) if mid else 2 * k ** 3  # U sweep of both spikes
+            f["block_lu"] += k ** 3  # truncated L sweep of the bottom spike
+        sweeps = 4 if mid else (2 if nb > 1 else 2)
+        f["solve_n"] += sweeps * 2 * nl * k * m
+        f["solve_t"] += sweeps * 2 * nl * k * m
+        f["solve_n"] += (2 if mid else 1) * 2 * k * k * m * (nb > 1)
+        f["solve_t"] += (2 if mid else 1) * 2 * k * k * m * (nb > 1)
+    for lv in plan_groups(offs, flags):
+        for (a, b, c) in lv:
+            nL, nR = b - a, c - b
+            hasV, hasW = c != nb, a != 0
+            fr = 2 * k ** 3 + 2 * k ** 3 / 3            # S = I - W V, LU(S)
+            fr += (2 * k ** 3 + 2 * k ** 3) * hasV + (4 * k ** 3 + 2 * k ** 3) * hasW
+            fr += (2 * k ** 3) * (2 * nL + 2 * nR - 1) * (hasV + hasW)
+            f["factor_reduced"] += fr
+            f["solve_n"] += 2 * k * k * m * (3 + (2 * nL - 1) + (2 * nR - 1))
+            f["solve_t"] += 2 * k * k * m * (2 * nL + 2 * nR + 3 + 2)
+    f["factor"] = f["block_lu"] + f["factor_spikes"] + f["factor_reduced"]
+    f["step"] = f["factor"] + f["solve_n"] + f["solve_t"]
+    return f
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = sorted(r[0] for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": rows[0][1], "samples": len(rows),
+                "power_w_max": max(r[2] for r in rows), "reasons": reasons}
+
+
+def cpu_oracle_sample(k, m, dd, n_sample, seed):
+    """Time the CPU oracle (banded GEPP + N and T solves) on the first rows of the workload's generator."""
+    import oracle
+    from paper_1811_03559_gb300 import inputs
+    pr = inputs.make_problem(n_sample, k, k, m, seed=seed, dd=dd)
+    oracle.build_oracle()
+    t0 = time.perf_counter()
+    lu = oracle.BandLU(pr["band"], k, k)
+    lu.solve(pr["F"], "N")
+    lu.solve(pr["F"], "T")
+    dt = time.perf_counter() - t0
+    return {"value": alg_bytes(n_sample, k, m) / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": "n=%d kl=ku=%d nrhs=%d DD=%g: banded GEPP factor + N solve + T solve, single thread, "
+                      "%.2f s" % (n_sample, k, m, dd, dt), "seconds": dt}
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in ("leaf.cu", "internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1811_03559_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic():
+    path = os.path.join(ROOT, "profiles", "block_lu_k128_traffic.json")
+    if not os.path.exists(path):
+        return None, None
+    d = json.load(open(path))
+    if d.get("source_hash") != source_hash():
+        return None, d
+    return d.get("dram_bytes_per_launch_full"), d
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="spike", choices=["spike", "reference"])
+    ap.add_argument("--n", type=int, default=1_048_576)
+    ap.add_argument("--k", type=int, default=128)
+    ap.add_argument("--p", type=int, default=148)
+    ap.add_argument("--nrhs", type=int, default=64)
+    ap.add_argument("--dd", type=float, default=1.01)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-sample", type=int, default=65536)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    n, k, p, m, dd, seed = args.n, args.k, args.p, args.nrhs, args.dd, 1
+    workload = "n=%d kl=ku=%d p=%d nrhs=%d DD=%g: spike_factor + spike_solve N + spike_solve T" % (n, k, p, m, dd)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        # The reference arm is the CPU oracle, timed on this host; only rank 0 runs it.
+        if rank != 0:
+            return
+        steps = []
+        for _ in range(max(args.warmup, 0)):
+            cpu_oracle_sample(k, m, dd, max(4096, args.cpu_sample // 4), seed)
+        for _ in range(args.steps):
+            steps.append(cpu_oracle_sample(k, m, dd, max(4096, args.cpu_sample // 4), seed))
+        v = float(np.mean([s["value"] for s in steps]))
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": 0,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean([s["seconds"] for s in steps])),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": workload, "sample_rows": max(4096, args.cpu_sample // 4)},
+                "cpu_baseline": {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": steps[0]["sample"]},
+                "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_1811_03559_gb300 import inputs, spike
+    spike.lib()
+    pr = inputs.make_problem(n, k, k, m, seed=seed, dd=dd)
+    F2h = inputs.band_matvec(pr["band"], k, k, pr["xstar"], "T")
+    band = torch.from_numpy(pr["band"]).to(dev)
+    F1src = torch.from_numpy(pr["F"]).to(dev)
+    F2src = torch.from_numpy(F2h).to(dev)
+    F1, F2 = torch.empty_like(F1src), torch.empty_like(F2src)
+    info, offs, flags = spike.plan(n, k, k, p, nrhs_hint=m, stage_balance=True)
+    fl = method_flops(offs, flags, k, m)
+
+    stage_acc = {}
+
+    def step(record):
+        F1.copy_(F1src)
+        F2.copy_(F2src)
+        fac = spike.Factorization(band, k, k, p, nrhs_hint=m, timing=record, stage_balance=True)
+        fac.solve(F1, "N")
+        fac.solve(F2, "T")
+        if record:
+            for key, val in fac.timings().items():
+                stage_acc.setdefault(key, []).append(val)
+        fac.free()
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    launches0 = spike.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        step(True)
+    e1.record()
+    torch.cuda.synchronize()
+    launches = spike.kernel_launches() - launches0
+    ms = e0.elapsed_time(e1)
+    clocks = sampler.stop() if sampler else None
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+
+    # accuracy of the last timed step (GPU residual from the original band)
+    be_n = float(spike.backward_error(band, k, k, F1, F1src, "N").max())
+    be_t = float(spike.backward_error(band, k, k, F2, F2src, "T").max())
+
+    # e2e: same metric through the C ABI with pinned host buffers
+    band_h = torch.from_numpy(pr["band"]).pin_memory()
+    F1h = torch.empty((m, n), dtype=torch.float64).pin_memory()
+    F2hp = torch.empty((m, n), dtype=torch.float64).pin_memory()
+    e2e_s = 0.0
+    for it in range(args.e2e_steps + 1):
+        F1h.copy_(torch.from_numpy(pr["F"]))
+        F2hp.copy_(torch.from_numpy(F2h))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fac = spike.Factorization(band_h.numpy(), k, k, p, nrhs_hint=m, stream=0, stage_balance=True)
+        fac.solve(F1h.numpy(), "N")
+        fac.solve(F2hp.numpy(), "T")
+        fac.free()
+        dt = time.perf_counter() - t0
+        if it > 0:
+            e2e_s += dt
+    e2e_step_s = e2e_s / args.e2e_steps if args.e2e_steps > 0 else float("nan")
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    bytes_step = alg_bytes(n, k, m)
+    value = world * bytes_step * args.steps / (ms * 1e-3) / 1e9
+    st = {key: float(np.mean(v)) for key, v in stage_acc.items()}
+    lu_ms = st.get("block_lu", float("nan"))
+    achieved = fl["block_lu"] / (lu_ms * 1e-3) / 1e12
+    traffic, tinfo = load_traffic()
+    step_tflops = fl["step"] / (ms / args.steps * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload, "n": n, "kl": k, "ku": k, "p": p, "nrhs": m, "dd": dd,
+                   "blocks": info["leaves"], "partitions": info["P"], "pairs_2x2": info["r"],
+                   "l2": "inputs larger than L2 (band %.2f GB per step)" % (8.0 * n * (2 * k + 1) / 1e9),
+                   "planner": "stage-balanced sizing (SPIKE_FLAG_STAGE_BALANCE: R13 = %.3g)" % info["R13"],
+                   "parallelism": "replicas x%d" % world},
+        "roofline": {"bound": "alu", "kernel": "k_factor_nopiv (block LU + all spike sweeps of the block)",
+                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "peak_note": FP64_PEAK_NOTE,
+                     "flops_per_launch": fl["block_lu"], "mean_launch_ms": lu_ms},
+        "step_roofline": {"method_tflop_per_step": fl["step"] / 1e12, "achieved_tflops": step_tflops,
+                          "frac_fp64": step_tflops / FP64_PEAK_TFLOPS,
+                          "lu_equivalent_tflop_per_step": (2.0 * n * k * k + 3 * 4.0 * n * k * m) / 1e12},
+        "stages_ms": st,
+        "accuracy": {"backward_error_N": be_n, "backward_error_T": be_t},
+        "e2e": {"value": world * bytes_step / e2e_step_s / 1e9, "unit": "GB/s",
+                "h2d_bytes_per_step": int(8 * n * (2 * k + 1) + 2 * 8 * n * m),
+                "d2h_bytes_per_step": int(2 * 8 * n * m), "steps": args.e2e_steps,
+                "ms_per_step": e2e_step_s * 1e3},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if not args.no_cpu and rank == 0:
+        line["cpu_baseline"] = cpu_oracle_sample(k, m, dd, args.cpu_sample, seed)
+        line["cpu_baseline"].pop("seconds", None)
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -43,6 +43,36 @@ extern "C" {
 #define SPIKE_ENOTSUP (-1004)  /* unsupported combination (e.g. bandwidth above the library limit) */
 #define SPIKE_ENOGPU (-1005)   /* no CUDA device available */
 
+#define SPIKE_FLAG_TIMING 1
+/* Size partitions for stage-synchronised execution.  The reduced system puts a
+ * device-wide synchronisation between the factorization and the solves, so each
+ * stage costs the maximum over blocks of that stage alone.  The paper's combined
+ * balance (Eq. R13_calculation: equal factor + solve work per partition) then
+ * leaves the two end blocks idle in one stage and the inner ones in the other.
+ * With this flag R13 is the paper's solve-stage limit 2 (Eq. ratios) when
+ * nrhs_hint > 0, and its factorization limit 1 + 1.5K (Eq. ratiof) otherwise:
+ * with few end blocks the inner blocks bound the factorization either way, and
+ * R13 = 2 balances the solve stages exactly. */
+#define SPIKE_FLAG_STAGE_BALANCE 2
+
+/* Stage indices of spike_get_timings (milliseconds between CUDA events recorded
+ * on the handle's stream; the last factorization and the last N / T solve). */
+#define SPIKE_T_FACTOR 0         /* whole spike_factor GPU work */
+#define SPIKE_T_SETUP 1          /* band repack, couplings, spike right-hand sides */
+#define SPIKE_T_BLOCK_LU 2       /* block factorization kernel; without pivoting it also runs every
+                                    spike sweep of the block in the same launch */
+#define SPIKE_T_SPIKES 3         /* tip extraction (and, when pivoting, the spike sweeps) */
+#define SPIKE_T_REDUCED 4        /* recursive reduced-system factorization */
+#define SPIKE_T_SOLVE_N 5        /* whole N solve */
+#define SPIKE_T_SOLVE_N_D 6      /*   D stage (L sweep, tip sweeps) */
+#define SPIKE_T_SOLVE_N_RED 7    /*   reduced system */
+#define SPIKE_T_SOLVE_N_RET 8    /*   retrieval */
+#define SPIKE_T_SOLVE_T 9        /* whole T solve */
+#define SPIKE_T_SOLVE_T_S 10     /*   S^T stage (sweeps, modified RHS) */
+#define SPIKE_T_SOLVE_T_RED 11   /*   transposed reduced system */
+#define SPIKE_T_SOLVE_T_D 12     /*   D^T stage */
+#define SPIKE_T_COUNT 13
+
 /* Largest half-bandwidth max(kl, ku) the kernels accept. */
 #define SPIKE_MAX_K 512
 
@@ -59,7 +89,9 @@ typedef struct {
   /* Expected nrhs used to size partitions (n_rhs/k in Eqs. R13/R12_calculation).
    * 0 selects the factorization-dominated limit n_rhs/k -> 0 (Eq. ratiof). */
   int32_t nrhs_hint;
-  int32_t reserved0;
+  /* Bit flags: SPIKE_FLAG_TIMING records CUDA events around the pipeline stages
+   * (read them with spike_get_timings). */
+  int32_t flags;
   /* cudaStream_t for all work of the handle; NULL = the legacy default stream. */
   void *stream;
   int64_t reserved[4];
@@ -137,6 +169,14 @@ int spike_get_tips(spike_handle h, int level, double *host_dst);
  * synchronises it before returning.  Allocates a small device scratch buffer. */
 int spike_backward_error(const double *band, int64_t ldab, int64_t n, int kl, int ku, const double *X,
                          const double *F, int nrhs, char trans, void *stream, double *berr);
+
+/* Stage times of the last factorization and the last N and T solves of a handle
+ * created with SPIKE_FLAG_TIMING (indices SPIKE_T_*; -1 for stages not run).
+ * Synchronises the handle's stream.  ms must hold `count` doubles. */
+int spike_get_timings(spike_handle h, double *ms, int count);
+
+/* Number of CUDA kernels this library has launched in the process so far. */
+int64_t spike_kernel_launches(void);
 
 /* Release a handle and all its device memory.  NULL is ignored. */
 void spike_free(spike_handle h);

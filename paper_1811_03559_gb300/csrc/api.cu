@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cstring>
 #include <functional>
@@ -17,6 +18,11 @@
 #include "internal.h"
 
 using namespace spk;
+
+namespace spk {
+static std::atomic<long long> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace spk
 
 namespace {
 
@@ -139,6 +145,10 @@ struct spike_ctx {
   size_t scr_bytes = 0;
   char *dargs = nullptr;
   size_t dargs_bytes = 0;
+  // stage timing (SPIKE_FLAG_TIMING): boundary events of the last factor / N solve / T solve
+  bool timing = false;
+  cudaEvent_t fev[5] = {}, nev[4] = {}, tev[4] = {};
+  bool fdone = false, ndone = false, tdone = false;
 };
 
 static bool valid(spike_handle h) { return h && h->magic == kMagic; }
@@ -210,7 +220,7 @@ extern "C" int spike_plan(int64_t n, int kl, int ku, int p, const spike_options 
                           int64_t *leaf_offsets, int32_t *leaf_flags) {
   if (!out) return -6;
   Plan pl;
-  const int rc = make_plan(n, kl, ku, p, opt ? opt->K : 0.0, opt ? opt->nrhs_hint : 0, pl);
+  const int rc = make_plan(n, kl, ku, p, opt ? opt->K : 0.0, opt ? opt->nrhs_hint : 0, opt ? opt->flags : 0, pl);
   if (rc != 0) return rc;  // -1 n, -2 kl, -3 ku, -4 p, or SPIKE_ENOTSUP
   fill_info(pl, out);
   for (int i = 0; i < pl.nleaves; ++i) {
@@ -222,18 +232,14 @@ extern "C" int spike_plan(int64_t n, int kl, int ku, int p, const spike_options 
   return 0;
 }
 
-// view of leaf i's rows of a global-frame column-major array (local row 0 first)
+// a strided view: element (local row r, column c) at p[r*rs + c*cs]
 struct View {
   double *p;
   int64_t rs, cs;
 };
-static View leaf_view(const LeafDev &L, double *base, int64_t ld) {
-  if (L.rev) return View{base + L.start + L.len - 1, -1, ld};
-  return View{base + L.start, 1, ld};
-}
 
-static SweepDesc sdesc(spike_ctx *c, int i, int r0, int r1, int ncols, View g, const double *gb, View gbv,
-                       double gbs, View x) {
+static SweepDesc sdesc(spike_ctx *c, int i, int kind, int r0, int r1, int ncols, View g, const double *gb,
+                       View gbv, double gbs, View x) {
   const LeafDev &L = c->hl[i];
   SweepDesc d;
   memset(&d, 0, sizeof(d));
@@ -244,6 +250,8 @@ static SweepDesc sdesc(spike_ctx *c, int i, int r0, int r1, int ncols, View g, c
   d.r0 = r0;
   d.r1 = r1;
   d.ncols = ncols;
+  d.kind = kind;
+  d.kw = (kind == UN || kind == UT) ? c->dofs : c->k;  // U has 2k superdiagonals when pivoting
   d.ga = g.p;
   d.ga_rs = g.rs;
   d.ga_cs = g.cs;
@@ -254,6 +262,12 @@ static SweepDesc sdesc(spike_ctx *c, int i, int r0, int r1, int ncols, View g, c
   d.x = x.p;
   d.x_rs = x.rs;
   d.x_cs = x.cs;
+  return d;
+}
+
+static SweepDesc empty_sweep() {
+  SweepDesc d;
+  memset(&d, 0, sizeof(d));
   return d;
 }
 
@@ -283,15 +297,40 @@ struct Pipeline {
     cudaStream_t s = st;
     ops.push_back([=](char *base) { return launch_gemm((GemmDesc *)(base + off), nd, tiles, s); });
   }
-  void sweep(int kind, std::vector<SweepDesc> &v, int kw, int ldf, int dofs, bool piv, int kpiv) {
-    if (v.empty()) return;
-    const size_t off = ar.put(v);
-    const int nd = (int)v.size();
+  // One stage = per leaf a first and a second sweep (a[i], b[i]; empty slots have
+  // ncols == 0), run by the leaf's CTA back to back in a single launch.  Pivoted
+  // L / L^T sweeps (interleaved row swaps, a_piv / b_piv = LN or LT, -1 = none) use
+  // their own kernel and launch.
+  void stage(std::vector<SweepDesc> &a, std::vector<SweepDesc> &b, int a_piv, int b_piv, int ldf, int dofs,
+             int k) {
     cudaStream_t s = st;
-    ops.push_back([=](char *base) {
-      if (piv) return launch_piv_sweep(kind, (SweepDesc *)(base + off), nd, kpiv, ldf, dofs, s);
-      return launch_sweep(kind, (SweepDesc *)(base + off), nd, kw, ldf, dofs, 0, s);
-    });
+    const int nl = (int)a.size();
+    auto used = [](const std::vector<SweepDesc> &v) {
+      for (auto &d : v)
+        if (d.ncols > 0) return true;
+      return false;
+    };
+    const bool ua = used(a), ub = used(b);
+    if (a_piv < 0 && b_piv < 0 && ua && ub) {
+      std::vector<SweepDesc> ab;
+      for (int i = 0; i < nl; ++i) {
+        ab.push_back(a[i]);
+        ab.push_back(b[i]);
+      }
+      const size_t off = ar.put(ab);
+      ops.push_back([=](char *base) { return launch_sweeps((SweepDesc *)(base + off), nl, 2, ldf, dofs, s); });
+      return;
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+      std::vector<SweepDesc> &v = pass ? b : a;
+      const int pk = pass ? b_piv : a_piv;
+      if (!(pass ? ub : ua)) continue;
+      const size_t off = ar.put(v);
+      ops.push_back([=](char *base) {
+        return pk >= 0 ? launch_piv_sweep(pk, (SweepDesc *)(base + off), nl, k, ldf, dofs, s)
+                       : launch_sweeps((SweepDesc *)(base + off), nl, 1, ldf, dofs, s);
+      });
+    }
   }
   void trs(TrsBatch &b) {
     if (b.d.empty()) return;
@@ -322,7 +361,7 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
     return SPIKE_ENOGPU;
   }
   Plan pl;
-  int rc = make_plan(n, kl, ku, p, opt ? opt->K : 0.0, opt ? opt->nrhs_hint : 0, pl);
+  int rc = make_plan(n, kl, ku, p, opt ? opt->K : 0.0, opt ? opt->nrhs_hint : 0, opt ? opt->flags : 0, pl);
   if (rc != 0) return map_plan_rc(rc);
   pl.pivot = pivot;
 
@@ -335,6 +374,12 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
   c->ldf = (c->dofs + pl.k + 1 + 1) & ~1;
   c->nleaves = pl.nleaves;
   c->NL = (int)pl.levels.size();
+  c->timing = opt && (opt->flags & SPIKE_FLAG_TIMING);
+  if (c->timing) {
+    for (auto &e : c->fev) cudaEventCreate(&e);
+    for (auto &e : c->nev) cudaEventCreate(&e);
+    for (auto &e : c->tev) cudaEventCreate(&e);
+  }
   const int k = c->k, nlv = c->nleaves;
   const int64_t kk = (int64_t)k * k;
   cudaStream_t s = c->stream;
@@ -465,6 +510,7 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
       return fail2(SPIKE_ECUDA);
     }
   }
+  if (c->timing) cudaEventRecord(c->fev[0], s);
   // 1. repack the band into per-leaf LU storage; couplings; Z right-hand sides
   if ((rc = launch_repack(dband, ldab, kl, ku, n, k, c->ldf, c->dofs, dleaf, nlv, c->fb, &c->status[3], s,
                           maxlen)) != 0 ||
@@ -473,42 +519,70 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
     g_cuda_err = std::string("setup kernels: ") + cudaGetErrorString((cudaError_t)rc);
     return fail2(SPIKE_ECUDA);
   }
-  // 2. block factorizations (+ fused L-sweep of the top spike when not pivoting)
-  rc = pivot ? launch_factor_piv(dleaf, nlv, k, c->ldf, c->fb, c->dinv, c->ipiv, c->status, s)
-             : launch_factor_nopiv(dleaf, nlv, k, c->ldf, c->fb, c->dinv, zbuf, dzoff, &c->status[3], kBoostEps,
-                                   c->status, s);
-  if (rc != 0) {
-    g_cuda_err = std::string("factor kernel: ") + cudaGetErrorString((cudaError_t)rc);
-    return fail2(SPIKE_ECUDA);
-  }
-  // 3. spike sweeps (Sec. 2.3: truncated for the first/last blocks, three full sweeps for middle ones)
+  if (c->timing) cudaEventRecord(c->fev[1], s);
+  // 2. block factorizations and spike sweeps (Sec. 2.3): truncated sweeps for the
+  // first/last blocks, three full sweeps for middle ones (the L-sweep of the top spike
+  // is fused into the non-pivoting LU; the others run in the same CTA after it).
   {
-    Pipeline pp;
-    pp.st = s;
-    std::vector<SweepDesc> ltop, lbot, ub;
+    std::vector<SweepDesc> ltop(nlv, empty_sweep()), lbot(nlv, empty_sweep()), ub(nlv, empty_sweep());
+    View none{nullptr, 0, 0};
     for (int i = 0; i < nlv; ++i) {
       const LeafDev &L = c->hl[i];
       const int nl = (int)L.len;
       const bool mid = L.top_nbr && L.bot_nbr;
       View zt{zbuf + zoff[i], 1, L.len}, zb{zbuf + zoff[i] + (int64_t)k * L.len, 1, L.len};
-      View none{nullptr, 0, 0};
-      if (pivot && mid) ltop.push_back(sdesc(c, i, 0, nl, k, zt, nullptr, none, 0.0, zt));
-      if (L.bot_nbr) lbot.push_back(sdesc(c, i, pivot ? nl - 2 * k : nl - k, nl, k, zb, nullptr, none, 0.0, zb));
-      if (mid) ub.push_back(sdesc(c, i, 0, nl, 2 * k, zt, nullptr, none, 0.0, zt));
-      else if (L.bot_nbr) ub.push_back(sdesc(c, i, nl - k, nl, k, zb, nullptr, none, 0.0, zb));
+      if (pivot && mid) ltop[i] = sdesc(c, i, LN, 0, nl, k, zt, nullptr, none, 0.0, zt);
+      if (L.bot_nbr) lbot[i] = sdesc(c, i, LN, pivot ? nl - 2 * k : nl - k, nl, k, zb, nullptr, none, 0.0, zb);
+      if (mid) ub[i] = sdesc(c, i, UN, 0, nl, 2 * k, zt, nullptr, none, 0.0, zt);
+      else if (L.bot_nbr) ub[i] = sdesc(c, i, UN, nl - k, nl, k, zb, nullptr, none, 0.0, zb);
     }
-    pp.sweep(LN, ltop, k, c->ldf, c->dofs, true, k);
-    pp.sweep(LN, lbot, k, c->ldf, c->dofs, pivot != 0, k);
-    pp.sweep(UN, ub, pivot ? 2 * k : k, c->ldf, c->dofs, false, k);
-    if ((rc = pp.run(c)) != 0) return fail2(rc);
+    if (!pivot) {
+      std::vector<SweepDesc> pairs;
+      for (int i = 0; i < nlv; ++i) {
+        pairs.push_back(lbot[i]);
+        pairs.push_back(ub[i]);
+      }
+      Arena ar;
+      const size_t off = ar.put(pairs);
+      if ((rc = ensure(&c->dargs, &c->dargs_bytes, ar.h.size(), s)) != 0) return fail2(rc);
+      if (cudaMemcpyAsync(c->dargs, ar.h.data(), ar.h.size(), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        g_cuda_err = "sweep descriptors";
+        return fail2(SPIKE_ECUDA);
+      }
+      rc = launch_factor_nopiv(dleaf, nlv, k, c->ldf, c->fb, c->dinv, zbuf, dzoff, &c->status[3], kBoostEps,
+                               c->status, (const SweepDesc *)(c->dargs + off), s);
+      if (rc != 0) {
+        g_cuda_err = std::string("factor kernel: ") + cudaGetErrorString((cudaError_t)rc);
+        return fail2(SPIKE_ECUDA);
+      }
+      if (c->timing) cudaEventRecord(c->fev[2], s);
+    } else {
+      rc = launch_factor_piv(dleaf, nlv, k, c->ldf, c->fb, c->dinv, c->ipiv, c->status, s);
+      if (rc != 0) {
+        g_cuda_err = std::string("factor kernel: ") + cudaGetErrorString((cudaError_t)rc);
+        return fail2(SPIKE_ECUDA);
+      }
+      if (c->timing) cudaEventRecord(c->fev[2], s);
+      Pipeline pp;
+      pp.st = s;
+      std::vector<SweepDesc> none_v(nlv, empty_sweep());
+      pp.stage(ltop, lbot, LN, LN, c->ldf, c->dofs, k);
+      pp.stage(ub, none_v, -1, -1, c->ldf, c->dofs, k);
+      if ((rc = pp.run(c)) != 0) return fail2(rc);
+    }
   }
   if ((rc = launch_tips0(dleaf, nlv, k, zbuf, dzoff, c->spk, s)) != 0) {
     g_cuda_err = std::string("tips kernel: ") + cudaGetErrorString((cudaError_t)rc);
     return fail2(SPIKE_ECUDA);
   }
+  if (c->timing) cudaEventRecord(c->fev[3], s);
   // 4. recursive reduced system factorization
   for (int lv = 0; lv < c->NL; ++lv) {
     if ((rc = factor_reduced_level(c, lv, tmp, tmp_bytes)) != 0) return fail2(rc);
+  }
+  if (c->timing) {
+    cudaEventRecord(c->fev[4], s);
+    c->fdone = true;
   }
   // 5. status
   unsigned long long st[8];
@@ -681,7 +755,9 @@ extern "C" int spike_solve_ex(spike_handle h, double *F, int64_t ldf, int nrhs, 
   const int64_t kk = (int64_t)k * k, km = (int64_t)k * m;
   cudaStream_t s = c->stream;
 
-  // scratch: [staged F][H][Y][merge temps]
+  // Work layout: the sweeps run on a ROW-major copy W of F (row r holds the m
+  // right-hand-side entries contiguously), so a block row and its window rows
+  // touch a few contiguous lines instead of m lines n*8 bytes apart.
   const bool fdev = is_device_ptr(F);
   size_t off = 0;
   auto carve = [&](size_t bytes) {
@@ -690,11 +766,13 @@ extern "C" int spike_solve_ex(spike_handle h, double *F, int64_t ldf, int nrhs, 
     return o;
   };
   const size_t o_f = fdev ? 0 : carve(sizeof(double) * (size_t)n * m);
+  const size_t o_w = (m > 1) ? carve(sizeof(double) * (size_t)n * m) : 0;
   const size_t o_h = carve(sizeof(double) * (size_t)n * m);
   const size_t o_y = carve(sizeof(double) * (size_t)nlv * 2 * km);
   size_t maxm = 1;
   for (auto &lvv : c->pl.levels) maxm = std::max(maxm, lvv.size());
   const size_t o_t = carve(sizeof(double) * maxm * 2 * km);
+  const size_t o_p = carve(sizeof(double) * (size_t)nlv * km);
   SP_TRY(ensure(&c->scr, &c->scr_bytes, off, s));
   double *Fd = F;
   int64_t ld = ldf;
@@ -704,46 +782,65 @@ extern "C" int spike_solve_ex(spike_handle h, double *F, int64_t ldf, int nrhs, 
     SP_CUDA(cudaMemcpy2DAsync(Fd, sizeof(double) * n, F, sizeof(double) * ldf, sizeof(double) * n, m,
                               cudaMemcpyHostToDevice, s));
   }
+  double *W = (m > 1) ? (double *)(c->scr + o_w) : Fd;  // m == 1: column-major == row-major
   double *H = (double *)(c->scr + o_h);
   double *Y = (double *)(c->scr + o_y);
   double *TM = (double *)(c->scr + o_t);
+  double *PP = (double *)(c->scr + o_p);
   auto YB = [&](int i, int t) { return Y + ((int64_t)i * 2 + t) * km; };  // k x m row-major block
+  // leaf view of a row-major n x m array (local row 0 first)
+  auto rview = [&](const LeafDev &L, double *base) {
+    if (L.rev) return View{base + (L.start + L.len - 1) * (int64_t)m, -(int64_t)m, 1};
+    return View{base + L.start * (int64_t)m, (int64_t)m, 1};
+  };
+  auto rows = [&](double *base, int64_t row0) { return base + row0 * (int64_t)m; };  // rows of a row-major array
 
   Pipeline pp;
   pp.st = s;
   View none{nullptr, 0, 0};
   const bool piv = c->pivot != 0;
-  const int kwU = piv ? 2 * k : k;
   auto memset_op = [&](void *p, size_t bytes) {
     pp.ops.push_back([=](char *) { return (int)cudaMemsetAsync(p, 0, bytes, s); });
   };
+  cudaEvent_t *evs = tr ? c->tev : c->nev;
+  const bool timing = c->timing;
+  auto mark = [&](int i) {
+    if (!timing) return;
+    cudaEvent_t e = evs[i];
+    pp.ops.push_back([=](char *) { return (int)cudaEventRecord(e, s); });
+  };
+  mark(0);
+  if (m > 1) {
+    double *src = Fd;
+    const int64_t ldx = ld;
+    pp.ops.push_back([=](char *) { return launch_transpose(src, W, n, m, ldx, 1, s); });
+  }
   memset_op(H, sizeof(double) * (size_t)n * m);
   memset_op(Y, sizeof(double) * (size_t)nlv * 2 * km);
-  // tip rows of a global-frame column-major array as a k x m matrix view
-  auto rows_view = [&](double *base, int64_t ldx, int64_t row0) { return View{base + row0, 1, ldx}; };
 
   if (tr == 0) {
     // ---------------- D stage (Eq. Dstage) with the sweep savings of Sec. 2.3
-    std::vector<SweepDesc> sa, sb;
+    std::vector<SweepDesc> sa(nlv, empty_sweep()), sb(nlv, empty_sweep());
     for (int i = 0; i < nlv; ++i) {
       const LeafDev &L = c->hl[i];
       const int nl = (int)L.len;
-      const View fv = leaf_view(L, Fd, ld), hv = leaf_view(L, H, n);
-      sa.push_back(sdesc(c, i, 0, nl, m, fv, nullptr, none, 0, fv));  // F <- L^{-1} F
-      if (L.top_nbr && L.bot_nbr) sb.push_back(sdesc(c, i, 0, nl, m, fv, nullptr, none, 0, hv));
-      else if (L.bot_nbr) sb.push_back(sdesc(c, i, nl - k, nl, m, fv, nullptr, none, 0, hv));
+      const View fv = rview(L, W), hv = rview(L, H);
+      sa[i] = sdesc(c, i, LN, 0, nl, m, fv, nullptr, none, 0, fv);  // W <- L^{-1} W
+      if (L.top_nbr && L.bot_nbr) sb[i] = sdesc(c, i, UN, 0, nl, m, fv, nullptr, none, 0, hv);
+      else if (L.bot_nbr) sb[i] = sdesc(c, i, UN, nl - k, nl, m, fv, nullptr, none, 0, hv);
     }
-    pp.sweep(LN, sa, k, c->ldf, c->dofs, piv, k);
-    pp.sweep(UN, sb, kwU, c->ldf, c->dofs, false, k);
+    pp.stage(sa, sb, piv ? LN : -1, -1, c->ldf, c->dofs, k);
     // gather Y tips (global rows) from H
     GemmBatch g0;
     for (int i = 0; i < nlv; ++i) {
       const LeafDev &L = c->hl[i];
-      if (i > 0) g0.add(gd(nullptr, 0, 0, nullptr, 0, 0, H + L.start, 1, n, YB(i, 0), m, 1, k, m, 0, 0.0, 1.0));
+      if (i > 0) g0.add(gd(nullptr, 0, 0, nullptr, 0, 0, rows(H, L.start), m, 1, YB(i, 0), m, 1, k, m, 0, 0.0, 1.0));
       if (i + 1 < nlv)
-        g0.add(gd(nullptr, 0, 0, nullptr, 0, 0, H + L.start + L.len - k, 1, n, YB(i, 1), m, 1, k, m, 0, 0.0, 1.0));
+        g0.add(gd(nullptr, 0, 0, nullptr, 0, 0, rows(H, L.start + L.len - k), m, 1, YB(i, 1), m, 1, k, m, 0, 0.0,
+                  1.0));
     }
     pp.gemm(g0);
+    mark(1);
     // ---------------- reduced system, levels ascending: D^[1]^-1 ... (Eqs. D1Inverse, S2Inverse)
     for (int lv = 0; lv < c->NL; ++lv) {
       const auto &ms = c->pl.levels[lv];
@@ -778,14 +875,15 @@ extern "C" int spike_solve_ex(spike_handle h, double *F, int64_t ldf, int nrhs, 
       pp.gemm(g2);
       pp.gemm(g3);
     }
+    mark(2);
     // ---------------- retrieval (Eqs. one/two/three): X_i = U^{-1}(L^{-1}F - L^{-1}[R_top x_top; 0; R_bot x_bot])
     memset_op(H, sizeof(double) * (size_t)n * m);
     GemmBatch gc;
-    std::vector<SweepDesc> sc, sd;
+    std::vector<SweepDesc> sc(nlv, empty_sweep()), sd(nlv, empty_sweep());
     for (int i = 0; i < nlv; ++i) {
       const LeafDev &L = c->hl[i];
       const int nl = (int)L.len;
-      const View fv = leaf_view(L, Fd, ld), hv = leaf_view(L, H, n);
+      const View fv = rview(L, W), hv = rview(L, H);
       const double *Rt = c->couple + (int64_t)i * 2 * kk, *Rb = Rt + kk;
       if (L.top_nbr) {
         const double *xn = L.rev ? YB(i + 1, 0) : YB(i - 1, 1);
@@ -796,57 +894,54 @@ extern "C" int spike_solve_ex(spike_handle h, double *F, int64_t ldf, int nrhs, 
         gc.add(gd(Rb, k, 1, xn, m, 1, nullptr, 0, 0, hv.p + (int64_t)(nl - k) * hv.rs, hv.rs, hv.cs, k, m, k, 1.0,
                   0.0));
       }
-      if (L.top_nbr && L.bot_nbr) sc.push_back(sdesc(c, i, 0, nl, m, hv, nullptr, none, 0, hv));
-      else if (L.bot_nbr) sc.push_back(sdesc(c, i, piv ? nl - 2 * k : nl - k, nl, m, hv, nullptr, none, 0, hv));
-      sd.push_back(sdesc(c, i, 0, nl, m, fv, hv.p, hv, -1.0, fv));
+      if (L.top_nbr && L.bot_nbr) sc[i] = sdesc(c, i, LN, 0, nl, m, hv, nullptr, none, 0, hv);
+      else if (L.bot_nbr) sc[i] = sdesc(c, i, LN, piv ? nl - 2 * k : nl - k, nl, m, hv, nullptr, none, 0, hv);
+      sd[i] = sdesc(c, i, UN, 0, nl, m, fv, hv.p, hv, -1.0, fv);
     }
     pp.gemm(gc);
-    pp.sweep(LN, sc, k, c->ldf, c->dofs, piv, k);
-    pp.sweep(UN, sd, kwU, c->ldf, c->dofs, false, k);
+    pp.stage(sc, sd, piv ? LN : -1, -1, c->ldf, c->dofs, k);
   } else {
     // ---------------- transpose: S^T Y = F then D^T X = Y (Sec. 4.1, 4.2)
     GemmBatch g0, gz;
     for (int i = 0; i < nlv; ++i) {
       const LeafDev &L = c->hl[i];
       if (i > 0) {
-        const View v = rows_view(Fd, ld, L.start);
-        g0.add(gd(nullptr, 0, 0, nullptr, 0, 0, v.p, v.rs, v.cs, YB(i, 0), m, 1, k, m, 0, 0.0, 1.0));
-        gz.add(gd(nullptr, 0, 0, nullptr, 0, 0, nullptr, 0, 0, v.p, v.rs, v.cs, k, m, 0, 0.0, 0.0));
+        double *v = rows(W, L.start);
+        g0.add(gd(nullptr, 0, 0, nullptr, 0, 0, v, m, 1, YB(i, 0), m, 1, k, m, 0, 0.0, 1.0));
+        gz.add(gd(nullptr, 0, 0, nullptr, 0, 0, nullptr, 0, 0, v, m, 1, k, m, 0, 0.0, 0.0));
       }
       if (i + 1 < nlv) {
-        const View v = rows_view(Fd, ld, L.start + L.len - k);
-        g0.add(gd(nullptr, 0, 0, nullptr, 0, 0, v.p, v.rs, v.cs, YB(i, 1), m, 1, k, m, 0, 0.0, 1.0));
-        gz.add(gd(nullptr, 0, 0, nullptr, 0, 0, nullptr, 0, 0, v.p, v.rs, v.cs, k, m, 0, 0.0, 0.0));
+        double *v = rows(W, L.start + L.len - k);
+        g0.add(gd(nullptr, 0, 0, nullptr, 0, 0, v, m, 1, YB(i, 1), m, 1, k, m, 0, 0.0, 1.0));
+        gz.add(gd(nullptr, 0, 0, nullptr, 0, 0, nullptr, 0, 0, v, m, 1, k, m, 0, 0.0, 0.0));
       }
     }
     pp.gemm(g0);
     pp.gemm(gz);
-    std::vector<SweepDesc> sa, sb;
+    std::vector<SweepDesc> sa(nlv, empty_sweep()), sb(nlv, empty_sweep()), e0(nlv, empty_sweep());
     for (int i = 0; i < nlv; ++i) {
       const LeafDev &L = c->hl[i];
       const int nl = (int)L.len;
-      const View fv = leaf_view(L, Fd, ld), hv = leaf_view(L, H, n);
-      sa.push_back(sdesc(c, i, 0, nl, m, fv, nullptr, none, 0, fv));  // w = U^{-T} [0; F~; 0]
+      const View fv = rview(L, W), hv = rview(L, H);
+      sa[i] = sdesc(c, i, UT, 0, nl, m, fv, nullptr, none, 0, fv);  // w = U^{-T} [0; F~; 0]
       const int r0 = (L.top_nbr && L.bot_nbr) ? 0 : (piv ? nl - 2 * k : nl - k);
-      if (L.bot_nbr) sb.push_back(sdesc(c, i, r0, nl, m, piv ? hv : fv, nullptr, none, 0, hv));
+      if (L.bot_nbr) sb[i] = sdesc(c, i, LT, r0, nl, m, piv ? hv : fv, nullptr, none, 0, hv);
     }
-    pp.sweep(UT, sa, kwU, c->ldf, c->dofs, false, k);
     if (piv) {
       // the pivoted L^T sweep runs in place: copy w into H first
-      double *Fp = Fd;
-      const int64_t ldp = ld;
-      pp.ops.push_back([=](char *) {
-        return (int)cudaMemcpy2DAsync(H, sizeof(double) * n, Fp, sizeof(double) * ldp, sizeof(double) * n, m,
-                                      cudaMemcpyDeviceToDevice, s);
-      });
+      pp.stage(sa, e0, -1, -1, c->ldf, c->dofs, k);
+      const size_t bytes = sizeof(double) * (size_t)n * m;
+      pp.ops.push_back([=](char *) { return (int)cudaMemcpyAsync(H, W, bytes, cudaMemcpyDeviceToDevice, s); });
+      pp.stage(sb, e0, LT, -1, c->ldf, c->dofs, k);
+    } else {
+      pp.stage(sa, sb, -1, -1, c->ldf, c->dofs, k);
     }
-    pp.sweep(LT, sb, k, c->ldf, c->dofs, piv, k);
     // G tips: y_{j+1,top} -= Bhat_j^T z_{j,bot}, y_{j-1,bot} -= Chat_j^T z_{j,top} (Eqs. G_in_transpose_1/2)
     GemmBatch gg;
     for (int j = 0; j < nlv; ++j) {
       const LeafDev &L = c->hl[j];
       const int nl = (int)L.len;
-      const View hv = leaf_view(L, H, n);
+      const View hv = rview(L, H);
       const double *Rt = c->couple + (int64_t)j * 2 * kk, *Rb = Rt + kk;
       if (L.top_nbr) {
         double *tgt = L.rev ? YB(j + 1, 0) : YB(j - 1, 1);
@@ -858,11 +953,14 @@ extern "C" int spike_solve_ex(spike_handle h, double *F, int64_t ldf, int nrhs, 
       }
     }
     pp.gemm(gg);
+    mark(1);
     // ---------------- transposed reduced system, levels descending (Sec. 4.3)
     for (int lv = c->NL - 1; lv >= 0; --lv) {
       const auto &ms = c->pl.levels[lv];
-      GemmBatch g1, g2, g3, g4;
+      GemmBatch gpart, g2, g3, g4;
+      std::vector<SumDesc> sums;
       TrsBatch ts;
+      int64_t maxe = 0;
       for (int mi = 0; mi < (int)ms.size(); ++mi) {
         const Merge &mg = ms[mi];
         const int64_t gm = c->merge_off[lv] + mi;
@@ -870,10 +968,18 @@ extern "C" int spike_solve_ex(spike_handle h, double *F, int64_t ldf, int nrhs, 
         const int *pv = c->mpiv + gm * 2 * k;
         double *s2 = TM + (int64_t)mi * 2 * km, *s1 = s2 + km;  // [g2; g1] -> [s2; s1]
         const double *Vlb = TIP(c, lv, 0, mg.b - 1, 1), *Wrt = TIP(c, lv, 1, mg.b, 0);
-        const int KL = 2 * (mg.b - mg.a) * k, KR = 2 * (mg.c - mg.b) * k;
-        // g1 = V_L^T y_L, g2 = W_R^T y_R (stacked tips)
-        g1.add(gd(TIP(c, lv, 0, mg.a, 0), 1, k, YB(mg.a, 0), m, 1, nullptr, 0, 0, s1, m, 1, k, m, KL, 1.0, 0.0));
-        g1.add(gd(TIP(c, lv, 1, mg.b, 0), 1, k, YB(mg.b, 0), m, 1, nullptr, 0, 0, s2, m, 1, k, m, KR, 1.0, 0.0));
+        // g1 = V_L^T y_L, g2 = W_R^T y_R: one partial product per leaf (both tips), then a
+        // fixed-order sum over the group's leaves
+        for (int i = mg.a; i < mg.c; ++i) {
+          const int sp = (i < mg.b) ? 0 : 1;
+          gpart.add(gd(TIP(c, lv, sp, i, 0), 1, k, YB(i, 0), m, 1, nullptr, 0, 0, PP + (int64_t)i * km, m, 1, k, m,
+                       2 * k, 1.0, 0.0));
+        }
+        SumDesc d1{PP + (int64_t)mg.a * km, s1, km, km, mg.b - mg.a, 0};
+        SumDesc d2{PP + (int64_t)mg.b * km, s2, km, km, mg.c - mg.b, 0};
+        sums.push_back(d1);
+        sums.push_back(d2);
+        maxe = std::max<int64_t>(maxe, km);
         if (c->schur[lv][mi]) {
           // s1 = S^{-T} (g1 - V^T g2);  s2 = g2 - W^T s1
           g2.add(gd(Vlb, 1, k, s2, m, 1, s1, m, 1, s1, m, 1, k, m, k, -1.0, 1.0));
@@ -886,51 +992,60 @@ extern "C" int spike_solve_ex(spike_handle h, double *F, int64_t ldf, int nrhs, 
         g4.add(gd(c->ident, k, 1, s1, m, 1, YB(mg.b, 0), m, 1, YB(mg.b, 0), m, 1, k, m, k, -1.0, 1.0));
         g4.add(gd(c->ident, k, 1, s2, m, 1, YB(mg.b - 1, 1), m, 1, YB(mg.b - 1, 1), m, 1, k, m, k, -1.0, 1.0));
       }
-      pp.gemm(g1);
+      pp.gemm(gpart);
+      {
+        const size_t so = pp.ar.put(sums);
+        const int nd = (int)sums.size();
+        pp.ops.push_back([=](char *base) { return launch_sum_blocks((SumDesc *)(base + so), nd, maxe, s); });
+      }
       pp.gemm(g2);
       pp.trs(ts);
       pp.gemm(g3);
       pp.gemm(g4);
     }
+    mark(2);
     // ---------------- D^T stage (Eq. sweeps_in_D): X_i = L^{-T}(w + U^{-T}[y_top; 0; y_bot])
     memset_op(H, sizeof(double) * (size_t)n * m);
     GemmBatch gp;
-    std::vector<SweepDesc> sc, sd;
+    std::vector<SweepDesc> sc(nlv, empty_sweep()), sd(nlv, empty_sweep());
     for (int i = 0; i < nlv; ++i) {
       const LeafDev &L = c->hl[i];
       const int nl = (int)L.len;
-      const View fv = leaf_view(L, Fd, ld), hv = leaf_view(L, H, n);
-      if (i > 0) gp.add(gd(nullptr, 0, 0, nullptr, 0, 0, YB(i, 0), m, 1, H + L.start, 1, n, k, m, 0, 0.0, 1.0));
+      const View fv = rview(L, W), hv = rview(L, H);
+      if (i > 0) gp.add(gd(nullptr, 0, 0, nullptr, 0, 0, YB(i, 0), m, 1, rows(H, L.start), m, 1, k, m, 0, 0.0, 1.0));
       if (i + 1 < nlv)
-        gp.add(gd(nullptr, 0, 0, nullptr, 0, 0, YB(i, 1), m, 1, H + L.start + L.len - k, 1, n, k, m, 0, 0.0, 1.0));
-      if (L.top_nbr && L.bot_nbr) sc.push_back(sdesc(c, i, 0, nl, m, hv, nullptr, none, 0, hv));
-      else if (L.bot_nbr) sc.push_back(sdesc(c, i, nl - k, nl, m, hv, nullptr, none, 0, hv));
-      SweepDesc d = sdesc(c, i, 0, nl, m, fv, nullptr, none, 0, fv);
+        gp.add(gd(nullptr, 0, 0, nullptr, 0, 0, YB(i, 1), m, 1, rows(H, L.start + L.len - k), m, 1, k, m, 0, 0.0,
+                  1.0));
+      if (L.top_nbr && L.bot_nbr) sc[i] = sdesc(c, i, UT, 0, nl, m, hv, nullptr, none, 0, hv);
+      else if (L.bot_nbr) sc[i] = sdesc(c, i, UT, nl - k, nl, m, hv, nullptr, none, 0, hv);
+      SweepDesc d = sdesc(c, i, LT, 0, nl, m, fv, nullptr, none, 0, fv);
       if (!piv) {
         d.gb = hv.p;
         d.gb_rs = hv.rs;
         d.gb_cs = hv.cs;
         d.gb_scale = 1.0;
       }
-      sd.push_back(d);
+      sd[i] = d;
     }
     pp.gemm(gp);
-    pp.sweep(UT, sc, kwU, c->ldf, c->dofs, false, k);
     if (piv) {
-      // F += H (column by column, F may have ldf > n), then the pivoted L^T sweep in place
-      double *Fp = Fd;
-      const int64_t ldp = ld;
-      pp.ops.push_back([=](char *) {
-        for (int col = 0; col < m; ++col) {
-          int e = launch_axpy(Fp + (int64_t)col * ldp, H + (int64_t)col * n, 1.0, n, s);
-          if (e) return e;
-        }
-        return 0;
-      });
+      // W += H, then the pivoted L^T sweep in place
+      pp.stage(sc, e0, -1, -1, c->ldf, c->dofs, k);
+      const int64_t cnt = n * (int64_t)m;
+      pp.ops.push_back([=](char *) { return launch_axpy(W, H, 1.0, cnt, s); });
+      pp.stage(sd, e0, LT, -1, c->ldf, c->dofs, k);
+    } else {
+      pp.stage(sc, sd, -1, -1, c->ldf, c->dofs, k);
     }
-    pp.sweep(LT, sd, k, c->ldf, c->dofs, piv, k);
   }
+  if (m > 1) {
+    double *dst = Fd;
+    const int64_t ldx = ld;
+    pp.ops.push_back([=](char *) { return launch_transpose(W, dst, n, m, ldx, 0, s); });
+  }
+  mark(3);
   SP_TRY(pp.run(c));
+  if (timing) (tr ? c->tdone : c->ndone) = true;
   if (!fdev) {
     SP_CUDA(cudaMemcpy2DAsync(F, sizeof(double) * ldf, Fd, sizeof(double) * n, sizeof(double) * n, m,
                               cudaMemcpyDeviceToHost, s));
@@ -1018,6 +1133,47 @@ extern "C" int spike_backward_error(const double *band, int64_t ldab, int64_t n,
   return 0;
 }
 
+extern "C" int spike_get_timings(spike_handle h, double *ms, int count) {
+  if (!valid(h)) return SPIKE_EHANDLE;
+  if (!ms || count < 0) return -2;
+  double t[SPIKE_T_COUNT];
+  for (double &v : t) v = -1.0;
+  if (h->timing) {
+    SP_CUDA(cudaStreamSynchronize(h->stream));
+    auto el = [](cudaEvent_t a, cudaEvent_t b) {
+      float f = -1.0f;
+      if (cudaEventElapsedTime(&f, a, b) != cudaSuccess) {
+        cudaGetLastError();
+        return -1.0;
+      }
+      return (double)f;
+    };
+    if (h->fdone) {
+      t[SPIKE_T_FACTOR] = el(h->fev[0], h->fev[4]);
+      t[SPIKE_T_SETUP] = el(h->fev[0], h->fev[1]);
+      t[SPIKE_T_BLOCK_LU] = el(h->fev[1], h->fev[2]);
+      t[SPIKE_T_SPIKES] = el(h->fev[2], h->fev[3]);
+      t[SPIKE_T_REDUCED] = el(h->fev[3], h->fev[4]);
+    }
+    if (h->ndone) {
+      t[SPIKE_T_SOLVE_N] = el(h->nev[0], h->nev[3]);
+      t[SPIKE_T_SOLVE_N_D] = el(h->nev[0], h->nev[1]);
+      t[SPIKE_T_SOLVE_N_RED] = el(h->nev[1], h->nev[2]);
+      t[SPIKE_T_SOLVE_N_RET] = el(h->nev[2], h->nev[3]);
+    }
+    if (h->tdone) {
+      t[SPIKE_T_SOLVE_T] = el(h->tev[0], h->tev[3]);
+      t[SPIKE_T_SOLVE_T_S] = el(h->tev[0], h->tev[1]);
+      t[SPIKE_T_SOLVE_T_RED] = el(h->tev[1], h->tev[2]);
+      t[SPIKE_T_SOLVE_T_D] = el(h->tev[2], h->tev[3]);
+    }
+  }
+  for (int i = 0; i < count; ++i) ms[i] = (i < SPIKE_T_COUNT) ? t[i] : -1.0;
+  return 0;
+}
+
+extern "C" int64_t spike_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
 extern "C" void spike_free(spike_handle h) {
   if (!valid(h)) return;
   cudaStream_t s = h->stream;
@@ -1025,6 +1181,11 @@ extern "C" void spike_free(spike_handle h) {
   if (h->scr) cudaFreeAsync(h->scr, s);
   if (h->dargs) cudaFreeAsync(h->dargs, s);
   cudaStreamSynchronize(s);
+  if (h->timing) {
+    for (auto &e : h->fev) cudaEventDestroy(e);
+    for (auto &e : h->nev) cudaEventDestroy(e);
+    for (auto &e : h->tev) cudaEventDestroy(e);
+  }
   h->magic = 0;
   delete h;
 }

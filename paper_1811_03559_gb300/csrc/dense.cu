@@ -5,6 +5,7 @@
 // report backward errors.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "internal.h"
@@ -97,6 +98,7 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmDesc *descs, int ndesc) 
 int launch_gemm(const GemmDesc *d, int ndesc, int total_tiles, void *stream) {
   if (ndesc <= 0 || total_tiles <= 0) return 0;
   k_gemm<<<total_tiles, 256, 0, (cudaStream_t)stream>>>(d, ndesc);
+  count_launch();
   return (int)cudaGetLastError();
 }
 
@@ -197,6 +199,7 @@ int launch_getrf(const LuDesc *d, int ndesc, int maxn, unsigned long long *statu
     if (e != cudaSuccess) return (int)e;
   }
   k_getrf<<<ndesc, 256, smem, (cudaStream_t)stream>>>(d, status);
+  count_launch();
   return (int)cudaGetLastError();
 }
 
@@ -294,6 +297,7 @@ int launch_getrs(const TrsDesc *d, int ndesc, int total_tiles, int maxn, void *s
     if (e != cudaSuccess) return (int)e;
   }
   k_getrs<<<total_tiles, 256, smem, (cudaStream_t)stream>>>(d, ndesc);
+  count_launch();
   return (int)cudaGetLastError();
 }
 
@@ -314,12 +318,74 @@ __global__ void k_noswap(const double *const *w, int k, int *flags) {
 int launch_noswap_flags(const double *const *w, int k, int nm, int *flags, void *stream) {
   if (nm <= 0) return 0;
   k_noswap<<<nm, 256, 0, (cudaStream_t)stream>>>(w, k, flags);
+  count_launch();
   return (int)cudaGetLastError();
 }
 
 int launch_assemble_M(const double *const *, const double *const *, int, int, const int *, double *, int64_t,
                       void *) {
   return 0;  // assembly is expressed as GEMM copies (K = 0)
+}
+
+// ------------------------------------------------------------- transpose
+// Column-major (rows x cols, ld) <-> row-major (rows x cols, row stride cols), 32 x 32 tiles.
+__global__ void k_transpose(const double *__restrict__ in, double *__restrict__ out, int64_t rows, int cols,
+                            int64_t ld, int to_row_major) {
+  __shared__ double t[32][33];
+  const int64_t r0 = (int64_t)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  for (int q = ty; q < 32; q += 8) {
+    if (to_row_major) {  // read column-major: rows contiguous
+      const int64_t r = r0 + tx;
+      const int c = c0 + q;
+      t[q][tx] = (r < rows && c < cols) ? in[(int64_t)c * ld + r] : 0.0;
+    } else {             // read row-major: columns contiguous
+      const int64_t r = r0 + q;
+      const int c = c0 + tx;
+      t[tx][q] = (r < rows && c < cols) ? in[r * cols + c] : 0.0;
+    }
+  }
+  __syncthreads();
+  for (int q = ty; q < 32; q += 8) {
+    if (to_row_major) {
+      const int64_t r = r0 + q;
+      const int c = c0 + tx;
+      if (r < rows && c < cols) out[r * cols + c] = t[tx][q];
+    } else {
+      const int64_t r = r0 + tx;
+      const int c = c0 + q;
+      if (r < rows && c < cols) out[(int64_t)c * ld + r] = t[q][tx];
+    }
+  }
+}
+
+int launch_transpose(const double *in, double *out, int64_t rows, int cols, int64_t ld, int to_row_major,
+                     void *stream) {
+  if (rows <= 0 || cols <= 0) return 0;
+  dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((cols + 31) / 32));
+  k_transpose<<<grid, 256, 0, (cudaStream_t)stream>>>(in, out, rows, cols, ld, to_row_major);
+  count_launch();
+  return (int)cudaGetLastError();
+}
+
+// -------------------------------------------------------- block sums
+// out[e] = sum_{i < count} in[i*stride + e], summed in index order (deterministic).
+__global__ void k_sum_blocks(const SumDesc *d) {
+  const SumDesc D = d[blockIdx.y];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < D.elems; e += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int i = 0; i < D.count; ++i) s += D.in[(int64_t)i * D.stride + e];
+    D.out[e] = s;
+  }
+}
+
+int launch_sum_blocks(const SumDesc *d, int ndesc, int64_t max_elems, void *stream) {
+  if (ndesc <= 0) return 0;
+  dim3 grid((unsigned)std::min<int64_t>((max_elems + 255) / 256, 64), (unsigned)ndesc);
+  k_sum_blocks<<<grid, 256, 0, (cudaStream_t)stream>>>(d);
+  count_launch();
+  return (int)cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ axpy
@@ -333,6 +399,7 @@ int launch_axpy(double *y, const double *x, double alpha, int64_t count, void *s
   int blocks = (int)((count + 255) / 256);
   if (blocks > 152 * 16) blocks = 152 * 16;
   k_axpy<<<blocks, 256, 0, (cudaStream_t)stream>>>(y, x, alpha, count);
+  count_launch();
   return (int)cudaGetLastError();
 }
 
@@ -385,6 +452,7 @@ int launch_berr(const double *band, int64_t ldab, int64_t n, int kl, int ku, con
   if (bx > 152 * 8) bx = 152 * 8;
   dim3 grid(bx, nrhs);
   k_berr<<<grid, 256, 0, (cudaStream_t)stream>>>(band, ldab, n, kl, ku, X, F, trans, scratch);
+  count_launch();
   return (int)cudaGetLastError();
 }
 

@@ -45,7 +45,7 @@ struct Plan {
 };
 
 // Returns 0 or -(argument index) on invalid input.
-int make_plan(int64_t n, int kl, int ku, int t, double K, int nrhs_hint, Plan &out);
+int make_plan(int64_t n, int kl, int ku, int t, double K, int nrhs_hint, int flags, Plan &out);
 
 // ------------------------------------------------------- device descriptors
 
@@ -71,7 +71,10 @@ struct SweepDesc {
   const double *dinv;  // leaf diagonal reciprocals, local row 0
   const int *ipiv;     // leaf pivots (pivoting mode, local indices), local row 0
   int64_t nl;
-  int r0, r1, ncols, pad;
+  int r0, r1, ncols;   // ncols == 0: empty slot
+  int kind;            // SweepKind
+  int kw;              // off-diagonal width of the triangle (k, or 2k for U in pivoting mode)
+  int pad;
   const double *ga;
   int64_t ga_rs, ga_cs;
   const double *gb;
@@ -114,8 +117,17 @@ struct TrsDesc {
   int tile0, pad;
 };
 
+// Fixed-order sum of `count` equally strided blocks: out[e] = sum_i in[i*stride + e].
+struct SumDesc {
+  const double *in;
+  double *out;
+  int64_t stride, elems;
+  int count, pad;
+};
+
 // ------------------------------------------------------------ launchers
-// Each returns cudaError_t as int (0 = success).
+// Each returns cudaError_t as int (0 = success) and counts its kernel launches.
+void count_launch(int n = 1);
 int launch_repack(const double *band, int64_t ldab, int kl, int ku, int64_t n, int k, int ldf, int dofs,
                   const LeafDev *leaves, int nleaves, double *fb, unsigned long long *amax_bits, void *stream,
                   int64_t max_leaf_len);
@@ -123,12 +135,15 @@ int launch_couplings(const double *band, int64_t ldab, int kl, int ku, int64_t n
                      int nleaves, double *couple, void *stream);
 int launch_zinit(const LeafDev *leaves, int nleaves, int k, const double *couple, double *zbuf,
                  const int64_t *zoff, int pivot, void *stream);
+// Block LU of every leaf followed, in the same CTA, by the leaf's spike sweeps
+// (sweeps[2*leaf], sweeps[2*leaf+1]; empty slots have ncols == 0).
 int launch_factor_nopiv(const LeafDev *leaves, int nleaves, int k, int ldf, double *fb, double *dinv, double *zbuf,
                         const int64_t *zoff, const unsigned long long *amax_bits, double boost_eps,
-                        unsigned long long *status, void *stream);
+                        unsigned long long *status, const SweepDesc *sweeps, void *stream);
 int launch_factor_piv(const LeafDev *leaves, int nleaves, int k, int ldf, double *fb, double *dinv, int *ipiv,
                       unsigned long long *status, void *stream);
-int launch_sweep(int kind, const SweepDesc *descs, int ndesc, int kw, int ldf, int dofs, int maxcols, void *stream);
+// Runs per_cta consecutive descriptors per CTA (a leaf's sweep sequence), ncta CTAs.
+int launch_sweeps(const SweepDesc *descs, int ncta, int per_cta, int ldf, int dofs, void *stream);
 int launch_piv_sweep(int kind, const SweepDesc *descs, int ndesc, int k, int ldf, int dofs, void *stream);
 int launch_tips0(const LeafDev *leaves, int nleaves, int k, const double *zbuf, const int64_t *zoff, double *spk,
                  void *stream);
@@ -140,6 +155,9 @@ int launch_noswap_flags(const double *const *w, int k, int nm, int *flags, void 
 int launch_assemble_M(const double *const *v, const double *const *w, int k, int nm, const int *flags, double *mbuf,
                       int64_t mstride, void *stream);
 int launch_axpy(double *y, const double *x, double alpha, int64_t count, void *stream);
+int launch_transpose(const double *in, double *out, int64_t rows, int cols, int64_t ld, int to_row_major,
+                     void *stream);
+int launch_sum_blocks(const SumDesc *d, int ndesc, int64_t max_elems, void *stream);
 // Backward-error reduction: scratch receives, as bit patterns of non-negative doubles,
 // [0] ||op(A)||_inf, [1+2c] ||op(A)x_c - f_c||_inf, [2+2c] ||x_c||_inf.
 int launch_berr(const double *band, int64_t ldab, int64_t n, int kl, int ku, const double *X, const double *F,

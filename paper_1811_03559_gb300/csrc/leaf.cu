@@ -25,6 +25,10 @@ namespace spk {
 
 #define FULLMASK 0xffffffffu
 
+constexpr int WCH = 256;  // sweep window rows per staged chunk
+constexpr int SCW = 128;  // RHS columns per sweep pass: 8 warps x 16 accumulators
+constexpr size_t SWEEP_SMEM = sizeof(double) * ((size_t)WCH * NB + NB * NB + NB + (size_t)NB * (SCW + 1));
+
 // ------------------------------------------------------------------ repack
 // User band (LAPACK layout, global frame) -> per-leaf LU band (local frame),
 // zero outside A_i's band, plus max|a_ij| for the boosting threshold.
@@ -60,6 +64,7 @@ int launch_repack(const double *band, int64_t ldab, int kl, int ku, int64_t n, i
                   int64_t max_leaf_len) {
   dim3 grid((unsigned)((max_leaf_len + 7) / 8), (unsigned)nleaves);
   k_repack<<<grid, 256, 0, (cudaStream_t)stream>>>(band, ldab, kl, ku, n, k, ldf, dofs, leaves, fb, amax_bits);
+  count_launch();
   return (int)cudaGetLastError();
 }
 
@@ -100,6 +105,7 @@ __global__ void k_couplings(const double *__restrict__ band, int64_t ldab, int k
 int launch_couplings(const double *band, int64_t ldab, int kl, int ku, int64_t n, int k, const LeafDev *leaves,
                      int nleaves, double *couple, void *stream) {
   k_couplings<<<nleaves, 256, 0, (cudaStream_t)stream>>>(band, ldab, kl, ku, n, k, leaves, couple);
+  count_launch();
   return (int)cudaGetLastError();
 }
 
@@ -124,8 +130,11 @@ int launch_zinit(const LeafDev *leaves, int nleaves, int k, const double *couple
                  int pivot, void *stream) {
   (void)pivot;
   k_zinit<<<nleaves, 256, 0, (cudaStream_t)stream>>>(leaves, k, couple, zbuf, zoff);
+  count_launch();
   return (int)cudaGetLastError();
 }
+
+__device__ void sweep_run(const SweepDesc &D, int ldf, int dofs, double *sm);
 
 // -------------------------------------------------- non-pivoting block LU
 // Blocked right-looking band LU (no pivoting, diagonal boosting, Sec. 2.3) of one
@@ -138,7 +147,7 @@ int launch_zinit(const LeafDev *leaves, int nleaves, int k, const double *couple
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_factor_nopiv(const LeafDev *leaves, int k, int ldf, double *fb_all, double *dinv_all, double *zbuf,
                    const int64_t *zoff, const unsigned long long *amax_bits, double boost_eps,
-                   unsigned long long *status) {
+                   unsigned long long *status, const SweepDesc *sweeps) {
   extern __shared__ double smem[];
   const LeafDev L = leaves[blockIdx.x];
   const int64_t nl = L.len;
@@ -160,11 +169,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int jb = (int)min((int64_t)NB, nl - j0);
     const int prow = (int)min((int64_t)(jb + k), nl - j0);
     // (a) panel load
-    for (int idx = tid; idx < NB * PLD; idx += NTHREADS) {
-      const int c = idx / PLD, r = idx - c * PLD;
-      double v = 0.0;
-      if (c < jb && r < prow && r - c <= k && c - r <= k) v = fb[(j0 + c) * ldf + k + r - c];
-      P[idx] = v;
+    for (int base = tid; base < NB * PLD; base += NTHREADS * 8) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int idx = base + u * NTHREADS;
+        const int c = idx / PLD, r = idx - c * PLD;
+        v[u] = (idx < NB * PLD && c < jb && r < prow && r - c <= k && c - r <= k) ? fb[(j0 + c) * ldf + k + r - c]
+                                                                                   : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (base + u * NTHREADS < NB * PLD) P[base + u * NTHREADS] = v[u];
     }
     __syncthreads();
     // (b) panel LU
@@ -210,17 +226,27 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int q0 = 0; q0 < ntot; q0 += CW) {
       const int nq = min(CW, ntot - q0);
       __syncthreads();
-      for (int idx = tid; idx < NB * nq; idx += NTHREADS) {
-        const int a = idx / nq, qq = idx - a * nq, q = q0 + qq;
-        double v = 0.0;
-        if (a < jb) {
-          if (q < kc) {
-            if (jb + q - a <= k) v = fb[(j0 + jb + q) * ldf + k + a - jb - q];
-          } else {
-            v = Z[(int64_t)(q - kc) * nl + j0 + a];
+      for (int base = tid; base < NB * nq; base += NTHREADS * 8) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int idx = base + u * NTHREADS;
+          const int a = idx % NB, qq = idx / NB, q = q0 + qq;
+          double w = 0.0;
+          if (idx < NB * nq && a < jb) {
+            if (q < kc) {
+              if (jb + q - a <= k) w = fb[(j0 + jb + q) * ldf + k + a - jb - q];
+            } else {
+              w = Z[(int64_t)(q - kc) * nl + j0 + a];
+            }
           }
+          v[u] = w;
         }
-        T[a * TLD + qq] = v;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int idx = base + u * NTHREADS;
+          if (idx < NB * nq) T[(idx % NB) * TLD + idx / NB] = v[u];
+        }
       }
       __syncthreads();
       // TRSM with the unit lower L11 = P[0:jb, 0:jb]: one column per thread
@@ -289,16 +315,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     __syncthreads();
   }
   if (tid == 0 && nboost) atomicAdd(&status[0], nboost);
+  // the leaf's spike sweeps, in the same CTA (shared memory reused)
+  __syncthreads();
+  sweep_run(sweeps[2 * blockIdx.x], ldf, k, smem);
+  __syncthreads();
+  sweep_run(sweeps[2 * blockIdx.x + 1], ldf, k, smem);
 }
 
 int launch_factor_nopiv(const LeafDev *leaves, int nleaves, int k, int ldf, double *fb, double *dinv, double *zbuf,
                         const int64_t *zoff, const unsigned long long *amax_bits, double boost_eps,
-                        unsigned long long *status, void *stream) {
-  const size_t smem = sizeof(double) * ((size_t)NB * (NB + k + 1) + (size_t)NB * (CW + 1));
+                        unsigned long long *status, const SweepDesc *sweeps, void *stream) {
+  size_t smem = sizeof(double) * ((size_t)NB * (NB + k + 1) + (size_t)NB * (CW + 1));
+  if (smem < SWEEP_SMEM) smem = SWEEP_SMEM;
   cudaError_t e = cudaFuncSetAttribute(k_factor_nopiv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
   k_factor_nopiv<<<nleaves, NTHREADS, smem, (cudaStream_t)stream>>>(leaves, k, ldf, fb, dinv, zbuf, zoff, amax_bits,
-                                                                     boost_eps, status);
+                                                                     boost_eps, status, sweeps);
+  count_launch();
   return (int)cudaGetLastError();
 }
 
@@ -385,6 +418,7 @@ __global__ void __launch_bounds__(NTHREADS)
 int launch_factor_piv(const LeafDev *leaves, int nleaves, int k, int ldf, double *fb, double *dinv, int *ipiv,
                       unsigned long long *status, void *stream) {
   k_factor_piv<<<nleaves, NTHREADS, 0, (cudaStream_t)stream>>>(leaves, k, ldf, fb, dinv, ipiv, status);
+  count_launch();
   return (int)cudaGetLastError();
 }
 
@@ -398,22 +432,32 @@ int launch_factor_piv(const LeafDev *leaves, int nleaves, int k, int ldf, double
 //       lanes <-> rows with shuffles otherwise),
 //   (3) store.
 // Coefficients: LN/UN use column c of the band, UT/LT column r (transposed access).
-constexpr int WCH = 256;  // window rows per staged chunk
-constexpr int SCW = 128;  // RHS columns per sweep pass: 8 warps x 16 accumulators
-
-template <int KIND>
-__device__ __forceinline__ double coef(const double *fb, int ldf, int dofs, int64_t r, int64_t c) {
-  if (KIND == LN || KIND == UN) return fb[c * ldf + dofs + r - c];
+__device__ __forceinline__ double coef(int kind, const double *fb, int ldf, int dofs, int64_t r, int64_t c) {
+  if (kind == LN || kind == UN) return fb[c * ldf + dofs + r - c];
   return fb[r * ldf + dofs + c - r];
 }
 
-template <int KIND>
-__global__ void __launch_bounds__(NTHREADS, 1) k_sweep(const SweepDesc *descs, int kw, int ldf, int dofs) {
-  extern __shared__ double sm[];
-  const SweepDesc D = descs[blockIdx.x];
+// acc[q] += sum_j Tw[j*NB] * X(row_j, col_base + q), rows row_j = row_0 + j (stride xstep),
+// for q < C.  Columns past `lastc` are clamped (their accumulators are never stored).
+template <int C>
+__device__ __forceinline__ void window_fma(double *acc, const double *tw, const double *xrow, int64_t xstep,
+                                           int64_t xcs, int col_base, int lastc, int count) {
+  int64_t coff[C];
+#pragma unroll
+  for (int q = 0; q < C; ++q) coff[q] = (int64_t)min(col_base + q, lastc) * xcs;
+  for (int j = 0; j < count; ++j) {
+    const double t = tw[j * NB];
+#pragma unroll
+    for (int q = 0; q < C; ++q) acc[q] = fma(t, xrow[coff[q]], acc[q]);
+    xrow += xstep;
+  }
+}
+
+__device__ void sweep_run(const SweepDesc &D, int ldf, int dofs, double *sm) {
   if (D.ncols <= 0 || D.r1 <= D.r0) return;
-  constexpr bool FWD = (KIND == LN || KIND == UT);
-  constexpr bool UNIT = (KIND == LN || KIND == LT);
+  const int kind = D.kind, kw = D.kw;
+  const bool FWD = (kind == LN || kind == UT);
+  const bool UNIT = (kind == LN || kind == LT);
   const int GLD = SCW + 1;
   double *Tw = sm;                 // WCH x NB   : Tw[j*NB + a] = T(row(a), wrow(j))
   double *Td = Tw + WCH * NB;      // NB x NB    : Td[a'*NB + a] = T(row(a), row(a'))
@@ -453,11 +497,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sweep(const SweepDesc *descs, i
         jhi = (int)min((int64_t)kw, D.r1 - b1);
       }
       __syncthreads();
-      for (int idx = tid; idx < NB * NB; idx += NTHREADS) {
-        const int ap = idx / NB, a = idx - ap * NB;
-        double v = 0.0;
-        if (ap < a && a < nbk && a - ap <= kw) v = coef<KIND>(D.fb, ldf, dofs, row(a), row(ap));
-        Td[idx] = v;
+      {
+        double v[NB * NB / NTHREADS];
+#pragma unroll
+        for (int u = 0; u < NB * NB / NTHREADS; ++u) {
+          const int idx = tid + u * NTHREADS;
+          const int ap = idx / NB, a = idx - ap * NB;
+          v[u] = (ap < a && a < nbk && a - ap <= kw) ? coef(kind, D.fb, ldf, dofs, row(a), row(ap)) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < NB * NB / NTHREADS; ++u) Td[tid + u * NTHREADS] = v[u];
       }
       for (int a = tid; a < NB; a += NTHREADS) dsm[a] = (a < nbk) ? (UNIT ? 1.0 : D.dinv[row(a)]) : 0.0;
 
@@ -467,23 +516,34 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sweep(const SweepDesc *descs, i
       for (int jc0 = jlo; jc0 < jhi; jc0 += WCH) {
         const int jce = min(jhi, jc0 + WCH);
         __syncthreads();
-        for (int idx = tid; idx < (jce - jc0) * NB; idx += NTHREADS) {
-          const int jj = idx / NB, a = idx - jj * NB, j = jc0 + jj;
-          double v = 0.0;
-          if (a < nbk && (FWD ? (j >= a) : (j <= kw - 1 - a))) v = coef<KIND>(D.fb, ldf, dofs, row(a), wrow(j));
-          Tw[idx] = v;
+        const int tot = (jce - jc0) * NB;
+        for (int base = tid; base < tot; base += NTHREADS * 8) {
+          double v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int idx = base + u * NTHREADS;
+            const int jj = idx / NB, a = idx - jj * NB, j = jc0 + jj;
+            v[u] = (idx < tot && a < nbk && (FWD ? (j >= a) : (j <= kw - 1 - a)))
+                       ? coef(kind, D.fb, ldf, dofs, row(a), wrow(j)) : 0.0;
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (base + u * NTHREADS < tot) Tw[base + u * NTHREADS] = v[u];
         }
         __syncthreads();
         const int len = jce - jc0;
         const int per = (len + nsplit - 1) / nsplit;
         const int js = jc0 + split * per, je = min(jce, js + per);
-        for (int j = js; j < je; ++j) {
-          const double t = Tw[(j - jc0) * NB + lane];
-          const double *xr = D.x + wrow(j) * D.x_rs;
-#pragma unroll
-          for (int q = 0; q < 16; ++q)
-            if (q < cpw && col_base + q < c0 + cw) acc[q] = fma(t, xr[(int64_t)(col_base + q) * D.x_cs], acc[q]);
-        }
+        // A predicated-off DFMA still occupies the FP64 pipe, so the accumulation loop is
+        // instantiated for the exact column count; edge columns are clamped, not predicated.
+        const double *xw = D.x + wrow(js) * D.x_rs;
+        const int64_t step = D.x_rs;  // wrow(j+1) = wrow(j) + 1 in both sweep directions
+        const int lastc = c0 + cw - 1;
+        if (cpw <= 1) window_fma<1>(acc, Tw + (js - jc0) * NB + lane, xw, step, D.x_cs, col_base, lastc, je - js);
+        else if (cpw <= 2) window_fma<2>(acc, Tw + (js - jc0) * NB + lane, xw, step, D.x_cs, col_base, lastc, je - js);
+        else if (cpw <= 4) window_fma<4>(acc, Tw + (js - jc0) * NB + lane, xw, step, D.x_cs, col_base, lastc, je - js);
+        else if (cpw <= 8) window_fma<8>(acc, Tw + (js - jc0) * NB + lane, xw, step, D.x_cs, col_base, lastc, je - js);
+        else window_fma<16>(acc, Tw + (js - jc0) * NB + lane, xw, step, D.x_cs, col_base, lastc, je - js);
       }
       __syncthreads();
       for (int s = 0; s < nsplit; ++s) {
@@ -542,40 +602,36 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sweep(const SweepDesc *descs, i
         }
       }
       __syncthreads();
-      for (int idx = tid; idx < nbk * cw; idx += NTHREADS) {
-        const int a = idx % nbk, cc = idx / nbk;
-        D.x[row(a) * D.x_rs + (int64_t)(c0 + cc) * D.x_cs] = Gs[a * GLD + cc];
+      if (D.x_cs == 1) {  // row-major X: columns contiguous
+        for (int idx = tid; idx < nbk * cw; idx += NTHREADS) {
+          const int cc = idx % cw, a = idx / cw;
+          D.x[row(a) * D.x_rs + (c0 + cc)] = Gs[a * GLD + cc];
+        }
+      } else {
+        for (int idx = tid; idx < nbk * cw; idx += NTHREADS) {
+          const int a = idx % nbk, cc = idx / nbk;
+          D.x[row(a) * D.x_rs + (int64_t)(c0 + cc) * D.x_cs] = Gs[a * GLD + cc];
+        }
       }
     }
     __syncthreads();
   }
 }
 
-int launch_sweep(int kind, const SweepDesc *descs, int ndesc, int kw, int ldf, int dofs, int maxcols, void *stream) {
-  (void)maxcols;
-  if (ndesc <= 0) return 0;
-  const size_t smem = sizeof(double) * ((size_t)WCH * NB + NB * NB + NB + (size_t)NB * (SCW + 1));
-  cudaError_t e = cudaSuccess;
-  cudaStream_t s = (cudaStream_t)stream;
-  switch (kind) {
-    case LN:
-      e = cudaFuncSetAttribute(k_sweep<LN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) k_sweep<LN><<<ndesc, NTHREADS, smem, s>>>(descs, kw, ldf, dofs);
-      break;
-    case UN:
-      e = cudaFuncSetAttribute(k_sweep<UN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) k_sweep<UN><<<ndesc, NTHREADS, smem, s>>>(descs, kw, ldf, dofs);
-      break;
-    case UT:
-      e = cudaFuncSetAttribute(k_sweep<UT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) k_sweep<UT><<<ndesc, NTHREADS, smem, s>>>(descs, kw, ldf, dofs);
-      break;
-    default:
-      e = cudaFuncSetAttribute(k_sweep<LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) k_sweep<LT><<<ndesc, NTHREADS, smem, s>>>(descs, kw, ldf, dofs);
-      break;
+__global__ void __launch_bounds__(NTHREADS, 1) k_sweeps(const SweepDesc *descs, int per_cta, int ldf, int dofs) {
+  extern __shared__ double sm[];
+  for (int s = 0; s < per_cta; ++s) {
+    sweep_run(descs[(int64_t)blockIdx.x * per_cta + s], ldf, dofs, sm);
+    __syncthreads();
   }
+}
+
+int launch_sweeps(const SweepDesc *descs, int ncta, int per_cta, int ldf, int dofs, void *stream) {
+  if (ncta <= 0 || per_cta <= 0) return 0;
+  cudaError_t e = cudaFuncSetAttribute(k_sweeps, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_SMEM);
   if (e != cudaSuccess) return (int)e;
+  k_sweeps<<<ncta, NTHREADS, SWEEP_SMEM, (cudaStream_t)stream>>>(descs, per_cta, ldf, dofs);
+  count_launch();
   return (int)cudaGetLastError();
 }
 
@@ -633,6 +689,7 @@ int launch_piv_sweep(int kind, const SweepDesc *descs, int ndesc, int k, int ldf
     k_piv_sweep<LN><<<ndesc, NTHREADS, 0, (cudaStream_t)stream>>>(descs, k, ldf, dofs);
   else
     k_piv_sweep<LT><<<ndesc, NTHREADS, 0, (cudaStream_t)stream>>>(descs, k, ldf, dofs);
+  count_launch();
   return (int)cudaGetLastError();
 }
 
@@ -672,6 +729,7 @@ __global__ void k_tips0(const LeafDev *leaves, int nleaves, int k, const double 
 int launch_tips0(const LeafDev *leaves, int nleaves, int k, const double *zbuf, const int64_t *zoff, double *spk,
                  void *stream) {
   k_tips0<<<nleaves, 256, 0, (cudaStream_t)stream>>>(leaves, nleaves, k, zbuf, zoff, spk);
+  count_launch();
   return (int)cudaGetLastError();
 }
 

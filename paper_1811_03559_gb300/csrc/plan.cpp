@@ -16,6 +16,10 @@
 // rho -> infinity), and n = 2 n1 + x n2 + y n3 with x = r pairs and y = P-2-r
 // single inner partitions, solved for n1, n2, n3.
 //
+// With SPIKE_FLAG_STAGE_BALANCE the ratio is instead the paper's solve-stage limit
+// R13 = 2 (or its factorization limit when no solve is expected), which balances
+// each stage separately (see spike.h).
+//
 // Readings where the paper is silent: sizes are floored, the remainder rows go
 // one at a time to the inner partitions starting at the second one; a 2x2
 // partition is split floor/ceil; every factored block must have at least 2k
@@ -60,7 +64,7 @@ static void build_levels(Plan &pl, const std::vector<int> &part_first_leaf) {
     }
 }
 
-int make_plan(int64_t n, int kl, int ku, int t, double K, int nrhs_hint, Plan &pl) {
+int make_plan(int64_t n, int kl, int ku, int t, double K, int nrhs_hint, int flags, Plan &pl) {
   if (n < 1) return -1;
   if (kl < 0) return -2;
   if (ku < 0) return -3;
@@ -77,6 +81,7 @@ int make_plan(int64_t n, int kl, int ku, int t, double K, int nrhs_hint, Plan &p
   pl.K = (K > 0) ? K : 2.0;
   const double rho = (nrhs_hint > 0) ? (double)nrhs_hint / pl.k : 0.0;
   pl.R13 = (1.0 + 1.5 * pl.K + 2.0 * pl.K * rho) / (1.0 + pl.K * rho);
+  if (flags & SPIKE_FLAG_STAGE_BALANCE) pl.R13 = (rho > 0.0) ? 2.0 : 1.0 + 1.5 * pl.K;
   pl.R12 = pl.R13 / 2.0;
   const int64_t k = pl.k;
 

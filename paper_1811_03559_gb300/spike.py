@@ -35,13 +35,18 @@ class SpikeInfo(ctypes.Structure):
 
 
 class SpikeOptions(ctypes.Structure):
-    _fields_ = [("K", ctypes.c_double), ("nrhs_hint", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+    _fields_ = [("K", ctypes.c_double), ("nrhs_hint", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("reserved", ctypes.c_int64 * 4)]
 
 
 EXPORTS = ["spike_plan", "spike_factor", "spike_factor_ex", "spike_solve", "spike_solve_ex", "spike_set_stream",
-           "spike_get_info", "spike_get_tips", "spike_backward_error", "spike_free", "spike_strerror",
-           "spike_last_cuda_error"]
+           "spike_get_info", "spike_get_tips", "spike_backward_error", "spike_get_timings", "spike_kernel_launches",
+           "spike_free", "spike_strerror", "spike_last_cuda_error"]
+
+FLAG_TIMING = 1
+FLAG_STAGE_BALANCE = 2
+STAGES = ["factor", "setup", "block_lu", "spikes", "reduced", "solve_n", "solve_n_d", "solve_n_reduced",
+          "solve_n_retrieval", "solve_t", "solve_t_s", "solve_t_reduced", "solve_t_d"]
 
 
 class SpikeError(RuntimeError):
@@ -71,6 +76,9 @@ def lib():
         L.spike_get_info.argtypes = [vp, ctypes.POINTER(SpikeInfo)]
         L.spike_get_tips.argtypes = [vp, i32, dp]
         L.spike_backward_error.argtypes = [dp, i64, i64, i32, i32, dp, dp, i32, ctypes.c_char, vp, dp]
+        L.spike_get_timings.argtypes = [vp, dp, i32]
+        L.spike_kernel_launches.argtypes = []
+        L.spike_kernel_launches.restype = ctypes.c_int64
         L.spike_free.argtypes = [vp]
         L.spike_free.restype = None
         L.spike_strerror.argtypes = [i32]
@@ -79,7 +87,7 @@ def lib():
         L.spike_last_cuda_error.restype = ctypes.c_char_p
         for nm in EXPORTS:
             f = getattr(L, nm)
-            if nm not in ("spike_free", "spike_strerror", "spike_last_cuda_error"):
+            if nm not in ("spike_free", "spike_strerror", "spike_last_cuda_error", "spike_kernel_launches"):
                 f.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -104,10 +112,10 @@ def _torch_stream(x):
     return ctypes.c_void_p(0)
 
 
-def plan(n, kl, ku, p, K=0.0, nrhs_hint=0):
+def plan(n, kl, ku, p, K=0.0, nrhs_hint=0, stage_balance=False):
     """Partition plan (Sec. 3.1, 3.3) without a GPU: (info dict, block offsets, block flags)."""
     info = SpikeInfo()
-    opt = SpikeOptions(K=K, nrhs_hint=nrhs_hint)
+    opt = SpikeOptions(K=K, nrhs_hint=nrhs_hint, flags=FLAG_STAGE_BALANCE if stage_balance else 0)
     offs = np.zeros(p + 2, dtype=np.int64)
     flags = np.zeros(p + 2, dtype=np.int32)
     rc = lib().spike_plan(n, kl, ku, p, ctypes.byref(opt), ctypes.byref(info), offs.ctypes.data_as(ctypes.c_void_p),
@@ -121,11 +129,14 @@ def plan(n, kl, ku, p, K=0.0, nrhs_hint=0):
 class Factorization:
     """A SPIKE factorization handle (spike_factor_ex); free with .free() or by garbage collection."""
 
-    def __init__(self, band, kl, ku, p, pivot=0, K=0.0, nrhs_hint=0, stream=None):
-        n, ldab = band.shape
-        self.n, self.kl, self.ku = n, kl, ku
+    def __init__(self, band, kl, ku, p, pivot=0, K=0.0, nrhs_hint=0, stream=None, timing=False, n=None,
+                 stage_balance=False):
+        rows, ldab = band.shape
+        self.n, self.kl, self.ku = (rows if n is None else n), kl, ku
+        n = self.n
         s = _torch_stream(band) if stream is None else ctypes.c_void_p(stream)
-        self._opt = SpikeOptions(K=K, nrhs_hint=nrhs_hint, stream=s)
+        flags = (FLAG_TIMING if timing else 0) | (FLAG_STAGE_BALANCE if stage_balance else 0)
+        self._opt = SpikeOptions(K=K, nrhs_hint=nrhs_hint, flags=flags, stream=s)
         h = ctypes.c_void_p()
         rc = lib().spike_factor_ex(_ptr(band), ldab, n, kl, ku, p, pivot, ctypes.byref(self._opt), ctypes.byref(h))
         self._h = h
@@ -154,6 +165,14 @@ class Factorization:
             raise SpikeError(rc, "spike_get_info")
         return out.as_dict()
 
+    def timings(self):
+        """Stage times (ms) of the last factor / N solve / T solve (handle created with timing=True)."""
+        out = np.zeros(len(STAGES))
+        rc = lib().spike_get_timings(self._h, out.ctypes.data_as(ctypes.c_void_p), len(STAGES))
+        if rc != 0:
+            raise SpikeError(rc, "spike_get_timings")
+        return dict(zip(STAGES, out.tolist()))
+
     def tips(self, level=0):
         """Spike tips of a merge level: array (leaves, 4, k, k) with [V_t, V_b, W_t, W_b]."""
         inf = self.info()
@@ -173,6 +192,11 @@ class Factorization:
             self.free()
         except Exception:
             pass
+
+
+def kernel_launches():
+    """Kernels launched by libspike.so in this process so far."""
+    return int(lib().spike_kernel_launches())
 
 
 def factor(band, kl, ku, p, pivot=0, **kw):

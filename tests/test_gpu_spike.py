@@ -91,10 +91,11 @@ def test_many_rhs(nrhs, trans):
 
 @pytest.mark.parametrize("p", [64, 148, 192])
 @pytest.mark.parametrize("trans", ["N", "T"])
-def test_large_p(p, trans):
+@pytest.mark.parametrize("stage_balance", [False, True])
+def test_large_p(p, trans, stage_balance):
     n, k = 200_000, 16
     pr = inputs.make_problem(n, k, k, 2, seed=p, dd=1.01, trans=trans)
-    X, fac = gpu_solve(pr["band"], k, k, pr["F"], p, trans)
+    X, fac = gpu_solve(pr["band"], k, k, pr["F"], p, trans, nrhs_hint=2, stage_balance=stage_balance)
     check(pr["band"], k, k, pr["F"], X, trans)
     assert fac.info()["p_effective"] == p
 

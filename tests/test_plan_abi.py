@@ -103,3 +103,13 @@ def test_bad_arguments(built):
     assert built.spike_factor_ex(x.ctypes.data_as(ctypes.c_void_p), 5, 100, 2, 2, 4, 3, None, ctypes.byref(h)) == -7
     assert built.spike_solve(None, None, 1, b"N") == spike.SPIKE_EHANDLE
     assert built.spike_strerror(-1002).decode().startswith("CUDA")
+
+
+def test_stage_balance_uses_paper_limits(built):
+    """SPIKE_FLAG_STAGE_BALANCE: R13 = 2 (Eq. ratios) when a solve is expected, else 1 + 1.5 K (Eq. ratiof)."""
+    info, offs, _ = spike.plan(1_048_576, 128, 128, 148, K=2.0, nrhs_hint=64, stage_balance=True)
+    assert info["R13"] == 2.0 and info["R12"] == 1.0
+    sizes = np.diff(offs)
+    assert abs(sizes[0] - 2 * info["n3"]) <= 1 and abs(sizes[1] + sizes[2] - 2 * info["n3"]) <= 2
+    f, _, _ = spike.plan(1_048_576, 128, 128, 148, K=4 / 3, nrhs_hint=0, stage_balance=True)
+    assert f["R13"] == pytest.approx(3.0)
