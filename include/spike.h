@@ -42,6 +42,7 @@ extern "C" {
 #define SPIKE_EHANDLE (-1003)  /* NULL or freed handle */
 #define SPIKE_ENOTSUP (-1004)  /* unsupported combination (e.g. bandwidth above the library limit) */
 #define SPIKE_ENOGPU (-1005)   /* no CUDA device available */
+#define SPIKE_ELIMIT (-1006)   /* size above the fixed limit of an entry point that allocates nothing */
 
 #define SPIKE_FLAG_TIMING 1
 /* Size partitions for stage-synchronised execution.  The reduced system puts a
@@ -177,6 +178,33 @@ int spike_get_timings(spike_handle h, double *ms, int count);
 
 /* Number of CUDA kernels this library has launched in the process so far. */
 int64_t spike_kernel_launches(void);
+
+/* Largest nrhs accepted by spike_backward_error_noalloc. */
+#define SPIKE_NOALLOC_MAX_NRHS 1024
+
+/* spike_backward_error for callers that cannot allocate memory.  (The paper has no
+ * counterpart: this is a library-usage entry point.)  Some callers must not
+ * allocate during the call: processes whose device memory is entirely held by
+ * their own pool or caching allocator (a cudaMalloc would fail or fragment it),
+ * and latency-bound loops that cannot absorb cudaFree, which synchronises the
+ * whole device.  This entry point performs the same computation on the same
+ * kernel as spike_backward_error and returns the same values, but calls no
+ * cudaMalloc, cudaFree or other allocating routine, on the device or the host.
+ * Its reduction scratch is a fixed array of (1 + 3*SPIKE_NOALLOC_MAX_NRHS)
+ * 8-byte words (about 24 KB) in the library's device memory, held by every GPU
+ * that loads the library until the process exits.
+ *   - nrhs above SPIKE_NOALLOC_MAX_NRHS returns SPIKE_ELIMIT (nothing runs).
+ *   - The first call on a device looks up that array's device address (once
+ *     per device, with the device current); make that first call before any
+ *     stream capture.
+ *   - Every call shares the one array: calls whose GPU work overlaps (other
+ *     streams, other host threads) race on it and must be serialised by the
+ *     caller.  Each call clears the part it uses before using it.
+ *   - On a CUDA failure it returns SPIKE_ECUDA without updating the text of
+ *     spike_last_cuda_error (that text lives in a heap-allocated string).
+ * Arguments, layout and synchronisation are those of spike_backward_error. */
+int spike_backward_error_noalloc(const double *band, int64_t ldab, int64_t n, int kl, int ku, const double *X,
+                                 const double *F, int nrhs, char trans, void *stream, double *berr);
 
 /* Release a handle and all its device memory.  NULL is ignored. */
 void spike_free(spike_handle h);

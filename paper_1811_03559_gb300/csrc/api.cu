@@ -1199,6 +1199,7 @@ extern "C" const char *spike_strerror(int code) {
     case SPIKE_EHANDLE: return "invalid handle";
     case SPIKE_ENOTSUP: return "unsupported argument combination";
     case SPIKE_ENOGPU: return "no CUDA device available";
+    case SPIKE_ELIMIT: return "size above the fixed limit of an entry point that allocates nothing";
     default: return "invalid argument";
   }
 }

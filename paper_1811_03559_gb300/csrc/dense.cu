@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 
 #include "internal.h"
@@ -456,4 +457,75 @@ int launch_berr(const double *band, int64_t ldab, int64_t n, int kl, int ku, con
   return (int)cudaGetLastError();
 }
 
+// -------------------------------------------- backward error without allocation
+// Fixed reduction scratch for spike_backward_error_noalloc:
+//   [0]                         ||op(A)||_inf      (bit pattern, atomicMax)
+//   [1 + 2c], [2 + 2c]          residual and ||x_c|| of column c
+//   [1 + 2*MAX + c]             the finished berr[c] (as a double)
+constexpr int NOALLOC_WORDS = 1 + 3 * SPIKE_NOALLOC_MAX_NRHS;
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[NOALLOC_WORDS];
+
+// Host code must not pass g_noalloc_scratch itself to a kernel: on the host that name
+// is a stand-in, not a device address.  The address is looked up once per device.
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static std::atomic<unsigned long long *> g_noalloc_addr[NOALLOC_MAX_DEVICES];
+
+static int noalloc_scratch(unsigned long long **out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SPIKE_ECUDA;
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return SPIKE_ELIMIT;
+  unsigned long long *p = g_noalloc_addr[dev].load(std::memory_order_acquire);
+  if (!p) {
+    void *addr = nullptr;
+    if (cudaGetSymbolAddress(&addr, g_noalloc_scratch) != cudaSuccess || addr == nullptr) return SPIKE_ECUDA;
+    p = (unsigned long long *)addr;
+    g_noalloc_addr[dev].store(p, std::memory_order_release);
+  }
+  *out = p;
+  return 0;
+}
+
+__global__ void k_berr_finish(unsigned long long *scr, int nrhs) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nrhs) return;
+  const double an = __longlong_as_double((long long)scr[0]);
+  const double r = __longlong_as_double((long long)scr[1 + 2 * c]);
+  const double x = __longlong_as_double((long long)scr[2 + 2 * c]);
+  const double b = (an > 0 && x > 0) ? r / (an * x) : (r == 0 ? 0.0 : INFINITY);
+  scr[1 + 2 * SPIKE_NOALLOC_MAX_NRHS + c] = (unsigned long long)__double_as_longlong(b);
+}
+
 }  // namespace spk
+
+extern "C" int spike_backward_error_noalloc(const double *band, int64_t ldab, int64_t n, int kl, int ku,
+                                            const double *X, const double *F, int nrhs, char trans, void *stream,
+                                            double *berr) {
+  if (!band) return -1;
+  if (ldab < (int64_t)kl + ku + 1) return -2;
+  if (n < 1) return -3;
+  if (kl < 0) return -4;
+  if (ku < 0) return -5;
+  if (!X) return -6;
+  if (!F) return -7;
+  if (nrhs < 1) return -8;
+  if (nrhs > SPIKE_NOALLOC_MAX_NRHS) return SPIKE_ELIMIT;
+  if (trans != 'N' && trans != 'n' && trans != 'T' && trans != 't') return -9;
+  if (!berr) return -11;
+  unsigned long long *scr = nullptr;
+  const int rc = spk::noalloc_scratch(&scr);
+  if (rc != 0) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the norms are max-reductions from zero: clear the words this call uses
+  if (cudaMemsetAsync(scr, 0, sizeof(unsigned long long) * (1 + 2 * (size_t)nrhs), s) != cudaSuccess)
+    return SPIKE_ECUDA;
+  if (spk::launch_berr(band, ldab, n, kl, ku, X, F, nrhs, (trans == 'T' || trans == 't') ? 1 : 0, scr, s) != 0)
+    return SPIKE_ECUDA;
+  spk::k_berr_finish<<<(nrhs + 127) / 128, 128, 0, s>>>(scr, nrhs);
+  spk::count_launch();
+  if (cudaGetLastError() != cudaSuccess) return SPIKE_ECUDA;
+  if (cudaMemcpyAsync(berr, scr + 1 + 2 * SPIKE_NOALLOC_MAX_NRHS, sizeof(double) * (size_t)nrhs,
+                      cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return SPIKE_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return SPIKE_ECUDA;
+  return 0;
+}

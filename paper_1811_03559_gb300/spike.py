@@ -41,7 +41,9 @@ class SpikeOptions(ctypes.Structure):
 
 EXPORTS = ["spike_plan", "spike_factor", "spike_factor_ex", "spike_solve", "spike_solve_ex", "spike_set_stream",
            "spike_get_info", "spike_get_tips", "spike_backward_error", "spike_get_timings", "spike_kernel_launches",
-           "spike_free", "spike_strerror", "spike_last_cuda_error"]
+           "spike_free", "spike_strerror", "spike_last_cuda_error", "spike_backward_error_noalloc"]
+SPIKE_ELIMIT = -1006
+NOALLOC_MAX_NRHS = 1024
 
 FLAG_TIMING = 1
 FLAG_STAGE_BALANCE = 2
@@ -76,6 +78,7 @@ def lib():
         L.spike_get_info.argtypes = [vp, ctypes.POINTER(SpikeInfo)]
         L.spike_get_tips.argtypes = [vp, i32, dp]
         L.spike_backward_error.argtypes = [dp, i64, i64, i32, i32, dp, dp, i32, ctypes.c_char, vp, dp]
+        L.spike_backward_error_noalloc.argtypes = [dp, i64, i64, i32, i32, dp, dp, i32, ctypes.c_char, vp, dp]
         L.spike_get_timings.argtypes = [vp, dp, i32]
         L.spike_kernel_launches.argtypes = []
         L.spike_kernel_launches.restype = ctypes.c_int64
@@ -212,4 +215,17 @@ def backward_error(band, kl, ku, X, F, trans="N"):
                                     _torch_stream(X), out.ctypes.data_as(ctypes.c_void_p))
     if rc != 0:
         raise SpikeError(rc, "spike_backward_error")
+    return out
+
+
+def backward_error_noalloc(band, kl, ku, X, F, trans="N"):
+    """As backward_error, through the entry point that allocates nothing (fixed device scratch,
+    nrhs <= NOALLOC_MAX_NRHS; calls whose GPU work overlaps must not share it)."""
+    n, ldab = band.shape
+    nrhs = 1 if X.ndim == 1 else X.shape[0]
+    out = np.zeros(nrhs)
+    rc = lib().spike_backward_error_noalloc(_ptr(band), ldab, n, kl, ku, _ptr(X), _ptr(F), nrhs, trans.encode(),
+                                            _torch_stream(X), out.ctypes.data_as(ctypes.c_void_p))
+    if rc != 0:
+        raise SpikeError(rc, "spike_backward_error_noalloc")
     return out
