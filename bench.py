@@ -198,6 +198,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-sample", type=int, default=65536)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer (e2e) leg, e.g. under a profiler")
     args = ap.parse_args()
     n, k, p, m, dd, seed = args.n, args.k, args.p, args.nrhs, args.dd, 1
     workload = "n=%d kl=ku=%d p=%d nrhs=%d DD=%g: spike_factor + spike_solve N + spike_solve T" % (n, k, p, m, dd)
@@ -293,7 +294,9 @@ def main():
     F1h = torch.empty((m, n), dtype=torch.float64).pin_memory()
     F2hp = torch.empty((m, n), dtype=torch.float64).pin_memory()
     e2e_s = 0.0
-    for it in range(args.e2e_steps + 1):
+    if args.no_e2e:
+        args.e2e_steps = 0
+    for it in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         F1h.copy_(torch.from_numpy(pr["F"]))
         F2hp.copy_(torch.from_numpy(F2h))
         torch.cuda.synchronize()
