@@ -37,7 +37,25 @@ METRIC = "n=1M k=128 factor+solve GB/s & % roofline vs FP64; serving p50/p99, so
 # FP64 FMA peak derived from unit counts and clock: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP64_PEAK_NOTE = "derived: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (the recipe's 1.25 TFLOP/s nominal); " \
-                 "a DFMA throughput probe measured 1.199 TFLOP/s"
+                 "peak_measured is the library's DFMA probe (spike_measure_fp64_peak) run in this process"
+
+
+def aggregate_over_ranks(ms_local, bytes_per_step_local, steps, dist=None, device=None):
+    """Max of the timed region over ranks and the whole-job throughput (GB/s) of N replicas."""
+    ms = float(ms_local)
+    world = 1
+    if dist is not None:
+        import torch
+        world = dist.get_world_size()
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        tb = torch.tensor([float(bytes_per_step_local)], dtype=torch.float64, device=device)
+        dist.all_reduce(tb, op=dist.ReduceOp.SUM)
+        total_bytes = float(tb.item())
+    else:
+        total_bytes = float(bytes_per_step_local)
+    return ms, total_bytes * steps / (ms * 1e-3) / 1e9, world
 
 
 def alg_bytes(n, k, m, nsolves=2):
@@ -279,11 +297,11 @@ def main():
     launches = spike.kernel_launches() - launches0
     ms = e0.elapsed_time(e1)
     clocks = sampler.stop() if sampler else None
+    bytes_step = alg_bytes(n, k, m)
+    ms, value, _ = aggregate_over_ranks(ms, bytes_step, args.steps, dist, dev)
     if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
+    peak_meas = spike.measure_fp64_peak(torch.cuda.current_stream().cuda_stream) if rank == 0 else None
 
     # accuracy of the last timed step (GPU residual from the original band)
     be_n = float(spike.backward_error(band, k, k, F1, F1src, "N").max())
@@ -315,8 +333,6 @@ def main():
             dist.destroy_process_group()
         return
 
-    bytes_step = alg_bytes(n, k, m)
-    value = world * bytes_step * args.steps / (ms * 1e-3) / 1e9
     st = {key: float(np.mean(v)) for key, v in stage_acc.items()}
     lu_ms = st.get("block_lu", float("nan"))
     achieved = fl["block_lu"] / (lu_ms * 1e-3) / 1e12
@@ -334,6 +350,7 @@ def main():
         "roofline": {"bound": "alu", "kernel": "k_factor_nopiv (block LU + all spike sweeps of the block)",
                      "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "peak_note": FP64_PEAK_NOTE,
+                     "peak_measured": peak_meas, "frac_of_measured": achieved / peak_meas if peak_meas else None,
                      "flops_per_launch": fl["block_lu"], "mean_launch_ms": lu_ms},
         "step_roofline": {"method_tflop_per_step": fl["step"] / 1e12, "achieved_tflops": step_tflops,
                           "frac_fp64": step_tflops / FP64_PEAK_TFLOPS,

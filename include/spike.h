@@ -176,6 +176,12 @@ int spike_backward_error(const double *band, int64_t ldab, int64_t n, int kl, in
  * Synchronises the handle's stream.  ms must hold `count` doubles. */
 int spike_get_timings(spike_handle h, double *ms, int count);
 
+/* Measure the FP64 FMA throughput of the current device with a dependent-chain
+ * DFMA loop on every SM (8 independent chains per thread, 2 CTAs of 512 threads
+ * per SM), in TFLOP/s (2 flop per FMA).  The roofline denominator of the FP64
+ * kernels.  Synchronises `stream`. */
+int spike_measure_fp64_peak(void *stream, double *tflops);
+
 /* Number of CUDA kernels this library has launched in the process so far. */
 int64_t spike_kernel_launches(void);
 

@@ -457,6 +457,21 @@ int launch_berr(const double *band, int64_t ldab, int64_t n, int kl, int ku, con
   return (int)cudaGetLastError();
 }
 
+// -------------------------------------------------------- FP64 FMA probe
+__global__ void __launch_bounds__(512) k_dfma_probe(double *out, int iters, double b, double c) {
+  double a[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) a[i] = threadIdx.x * 1e-3 + i;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = fma(a[i], b, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s += a[i];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 // -------------------------------------------- backward error without allocation
 // Fixed reduction scratch for spike_backward_error_noalloc:
 //   [0]                         ||op(A)||_inf      (bit pattern, atomicMax)
@@ -527,5 +542,32 @@ extern "C" int spike_backward_error_noalloc(const double *band, int64_t ldab, in
                       cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return SPIKE_ECUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return SPIKE_ECUDA;
+  return 0;
+}
+
+extern "C" int spike_measure_fp64_peak(void *stream, double *tflops) {
+  if (!tflops) return -2;
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return SPIKE_ECUDA;
+  const int blocks = 2 * sms, threads = 512, iters = 8192;
+  double *out = nullptr;
+  if (cudaMallocAsync((void **)&out, sizeof(double) * blocks * threads, s) != cudaSuccess) return SPIKE_ENOMEM;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  spk::k_dfma_probe<<<blocks, threads, 0, s>>>(out, iters / 8, 1.0000001, 1e-9);  // warm-up
+  cudaEventRecord(e0, s);
+  spk::k_dfma_probe<<<blocks, threads, 0, s>>>(out, iters, 1.0000001, 1e-9);
+  cudaEventRecord(e1, s);
+  spk::count_launch(2);
+  float ms = 0.0f;
+  const bool ok = cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(out, s);
+  if (!ok || ms <= 0.0f) return SPIKE_ECUDA;
+  *tflops = 2.0 * 8.0 * (double)iters * blocks * threads / (ms * 1e-3) / 1e12;
   return 0;
 }

@@ -41,7 +41,8 @@ class SpikeOptions(ctypes.Structure):
 
 EXPORTS = ["spike_plan", "spike_factor", "spike_factor_ex", "spike_solve", "spike_solve_ex", "spike_set_stream",
            "spike_get_info", "spike_get_tips", "spike_backward_error", "spike_get_timings", "spike_kernel_launches",
-           "spike_free", "spike_strerror", "spike_last_cuda_error", "spike_backward_error_noalloc"]
+           "spike_free", "spike_strerror", "spike_last_cuda_error", "spike_backward_error_noalloc",
+           "spike_measure_fp64_peak"]
 SPIKE_ELIMIT = -1006
 NOALLOC_MAX_NRHS = 1024
 
@@ -80,6 +81,7 @@ def lib():
         L.spike_backward_error.argtypes = [dp, i64, i64, i32, i32, dp, dp, i32, ctypes.c_char, vp, dp]
         L.spike_backward_error_noalloc.argtypes = [dp, i64, i64, i32, i32, dp, dp, i32, ctypes.c_char, vp, dp]
         L.spike_get_timings.argtypes = [vp, dp, i32]
+        L.spike_measure_fp64_peak.argtypes = [vp, dp]
         L.spike_kernel_launches.argtypes = []
         L.spike_kernel_launches.restype = ctypes.c_int64
         L.spike_free.argtypes = [vp]
@@ -195,6 +197,15 @@ class Factorization:
             self.free()
         except Exception:
             pass
+
+
+def measure_fp64_peak(stream=None):
+    """Measured FP64 FMA throughput of the current GPU in TFLOP/s (library probe kernel)."""
+    out = ctypes.c_double(0.0)
+    rc = lib().spike_measure_fp64_peak(ctypes.c_void_p(stream or 0), ctypes.byref(out))
+    if rc != 0:
+        raise SpikeError(rc, "spike_measure_fp64_peak")
+    return out.value
 
 
 def kernel_launches():
