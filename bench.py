@@ -217,6 +217,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=65536)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer (e2e) leg, e.g. under a profiler")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision variant")
     args = ap.parse_args()
     n, k, p, m, dd, seed = args.n, args.k, args.p, args.nrhs, args.dd, 1
     workload = "n=%d kl=ku=%d p=%d nrhs=%d DD=%g: spike_factor + spike_solve N + spike_solve T" % (n, k, p, m, dd)
@@ -307,6 +308,57 @@ def main():
     be_n = float(spike.backward_error(band, k, k, F1, F1src, "N").max())
     be_t = float(spike.backward_error(band, k, k, F2, F2src, "T").max())
 
+    # mixed-precision variant (SPIKE_FLAG_MIXED: FP32 blocks + FP64 refinement) against plain FP64,
+    # on this step (nrhs = m) and with nrhs = 1, where the factorization dominates.
+    mixed = None
+    if not args.no_mixed:
+        def variant(nr, use_mixed):
+            A1, A2 = F1src[:nr], F2src[:nr]
+            B1, B2 = torch.empty_like(A1), torch.empty_like(A2)
+            stg, refs = {}, []
+
+            def one(record):
+                B1.copy_(A1)
+                B2.copy_(A2)
+                fac = spike.Factorization(band, k, k, p, nrhs_hint=nr, timing=record, stage_balance=True,
+                                          mixed=use_mixed)
+                fac.solve(B1, "N")
+                r1 = fac.info()["refine_steps"]
+                fac.solve(B2, "T")
+                r2 = fac.info()["refine_steps"]
+                if record:
+                    for key, val in fac.timings().items():
+                        stg.setdefault(key, []).append(val)
+                    refs.append((r1, r2))
+                fac.free()
+
+            for _ in range(max(1, args.warmup)):
+                one(False)
+            torch.cuda.synchronize()
+            v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            v0.record()
+            for _ in range(args.steps):
+                one(True)
+            v1.record()
+            torch.cuda.synchronize()
+            vms = v0.elapsed_time(v1) / args.steps
+            out = {"ms_per_step": vms, "value": alg_bytes(n, k, nr) / (vms * 1e-3) / 1e9,
+                   "backward_error_N": float(spike.backward_error(band, k, k, B1, A1, "N").max()),
+                   "backward_error_T": float(spike.backward_error(band, k, k, B2, A2, "T").max()),
+                   "stages_ms": {key: round(float(np.mean(v)), 3) for key, v in stg.items()}}
+            if use_mixed:
+                out["refine_steps_N_T"] = refs[-1]
+            return out
+
+        mx = variant(m, True)
+        f1 = variant(1, False)
+        m1 = variant(1, True)
+        mixed = {"method": "FP32 block factorizations and sweeps, FP64 spike tips and reduced system, FP64 "
+                           "iterative refinement to backward error <= 1e-14 (SPIKE_FLAG_MIXED)",
+                 "unit": "GB/s",
+                 "nrhs_%d" % m: dict(mx, speedup_vs_fp64=(ms / args.steps) / mx["ms_per_step"]),
+                 "nrhs_1": {"fp64": f1, "mixed": m1, "speedup_vs_fp64": f1["ms_per_step"] / m1["ms_per_step"]}}
+
     # e2e: same metric through the C ABI with pinned host buffers
     band_h = torch.from_numpy(pr["band"]).pin_memory()
     F1h = torch.empty((m, n), dtype=torch.float64).pin_memory()
@@ -361,6 +413,7 @@ def main():
                 "h2d_bytes_per_step": int(8 * n * (2 * k + 1) + 2 * 8 * n * m),
                 "d2h_bytes_per_step": int(2 * 8 * n * m), "steps": args.e2e_steps,
                 "ms_per_step": e2e_step_s * 1e3},
+        "variants": {"mixed_fp32_fp64_refinement": mixed},
         "gpu_launches": int(launches),
         "clocks": clocks,
     }

@@ -55,6 +55,17 @@ extern "C" {
  * with few end blocks the inner blocks bound the factorization either way, and
  * R13 = 2 balances the solve stages exactly. */
 #define SPIKE_FLAG_STAGE_BALANCE 2
+/* Mixed precision: the block factorizations, spike sweeps and solve sweeps run in
+ * FP32 (the FP32 FMA pipe is ~60x the FP64 one on GB300); the spike tips and the
+ * whole reduced system stay FP64; spike_solve then refines in FP64: each step
+ * forms r = F - op(A) x from an FP64 copy of the band kept by the handle, solves
+ * with the FP32 factorization and adds the correction, until the backward error
+ * of every column is <= SPIKE_MIXED_TOL (at most SPIKE_MIXED_MAX_STEPS steps;
+ * spike_get_info reports the steps and the final backward error).  Non-pivoting
+ * only (SPIKE_ENOTSUP with pivot = 1). */
+#define SPIKE_FLAG_MIXED 4
+#define SPIKE_MIXED_TOL 1e-14
+#define SPIKE_MIXED_MAX_STEPS 10
 
 /* Stage indices of spike_get_timings (milliseconds between CUDA events recorded
  * on the handle's stream; the last factorization and the last N / T solve). */
@@ -117,6 +128,9 @@ typedef struct {
   int64_t boosts;           /* non-pivoting mode: number of boosted (near-zero) pivots (Sec. 2.3) */
   int64_t zero_pivot_col;   /* pivoting mode: 1-based global column of the first all-zero pivot column, 0 if none */
   int64_t device_bytes;     /* device memory held by the handle */
+  int32_t mixed;            /* 1: SPIKE_FLAG_MIXED handle */
+  int32_t refine_steps;     /* mixed: FP64 refinement steps of the last solve */
+  double refine_berr;       /* mixed: max backward error over columns after the last solve */
 } spike_info;
 
 /* Compute the partition plan for (n, kl, ku, p) without touching a GPU (Sec. 3.1, 3.3).

@@ -131,7 +131,14 @@ struct spike_ctx {
   // persistent device memory (one allocation, carved)
   char *mem = nullptr;
   size_t mem_bytes = 0;
-  double *fb = nullptr, *dinv = nullptr, *couple = nullptr, *spk = nullptr, *mlu = nullptr, *ident = nullptr;
+  char *fbc = nullptr, *dinvc = nullptr;  // leaf factors / reciprocals, element size es
+  double *couple = nullptr, *spk = nullptr, *mlu = nullptr, *ident = nullptr;
+  int f32 = 0;                             // SPIKE_FLAG_MIXED: FP32 leaf factors and sweeps
+  size_t es = sizeof(double);
+  double *band64 = nullptr;                // mixed: FP64 copy of the band for the refinement residuals
+  int64_t ldab64 = 0;
+  int last_iters = 0;                      // mixed: refinement steps of the last solve
+  double last_berr = 0.0;                  //        and its final backward error
   int *ipiv = nullptr, *mpiv = nullptr;
   unsigned long long *status = nullptr;
   std::vector<LeafDev> hl;
@@ -243,8 +250,8 @@ static SweepDesc sdesc(spike_ctx *c, int i, int kind, int r0, int r1, int ncols,
   const LeafDev &L = c->hl[i];
   SweepDesc d;
   memset(&d, 0, sizeof(d));
-  d.fb = c->fb + L.start * (int64_t)c->ldf;
-  d.dinv = c->dinv + L.start;
+  d.fb = (const double *)(c->fbc + L.start * (int64_t)c->ldf * c->es);
+  d.dinv = (const double *)(c->dinvc + L.start * (int64_t)c->es);
   d.ipiv = c->ipiv ? c->ipiv + L.start : nullptr;
   d.nl = L.len;
   d.r0 = r0;
@@ -271,9 +278,12 @@ static SweepDesc empty_sweep() {
   return d;
 }
 
+static std::vector<SweepDesc> e0_dummy(int n) { return std::vector<SweepDesc>(n, empty_sweep()); }
+
 // Upload an arena and run the recorded launches.
 struct Pipeline {
   cudaStream_t st = nullptr;
+  int f32 = 0;  // sweep storage precision
   Arena ar;
   std::vector<std::function<int(char *)>> ops;
   int run(spike_ctx *c) {
@@ -311,6 +321,7 @@ struct Pipeline {
       return false;
     };
     const bool ua = used(a), ub = used(b);
+    const int fp = f32;
     if (a_piv < 0 && b_piv < 0 && ua && ub) {
       std::vector<SweepDesc> ab;
       for (int i = 0; i < nl; ++i) {
@@ -318,7 +329,7 @@ struct Pipeline {
         ab.push_back(b[i]);
       }
       const size_t off = ar.put(ab);
-      ops.push_back([=](char *base) { return launch_sweeps((SweepDesc *)(base + off), nl, 2, ldf, dofs, s); });
+      ops.push_back([=](char *base) { return launch_sweeps((SweepDesc *)(base + off), nl, 2, ldf, dofs, s, fp); });
       return;
     }
     for (int pass = 0; pass < 2; ++pass) {
@@ -328,7 +339,7 @@ struct Pipeline {
       const size_t off = ar.put(v);
       ops.push_back([=](char *base) {
         return pk >= 0 ? launch_piv_sweep(pk, (SweepDesc *)(base + off), nl, k, ldf, dofs, s)
-                       : launch_sweeps((SweepDesc *)(base + off), nl, 1, ldf, dofs, s);
+                       : launch_sweeps((SweepDesc *)(base + off), nl, 1, ldf, dofs, s, fp);
       });
     }
   }
@@ -375,6 +386,12 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
   c->nleaves = pl.nleaves;
   c->NL = (int)pl.levels.size();
   c->timing = opt && (opt->flags & SPIKE_FLAG_TIMING);
+  c->f32 = (opt && (opt->flags & SPIKE_FLAG_MIXED)) ? 1 : 0;
+  c->es = c->f32 ? sizeof(float) : sizeof(double);
+  if (c->f32 && pivot) {
+    delete c;
+    return SPIKE_ENOTSUP;
+  }
   if (c->timing) {
     for (auto &e : c->fev) cudaEventCreate(&e);
     for (auto &e : c->nev) cudaEventCreate(&e);
@@ -425,8 +442,9 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
     off = (off + bytes + 255) & ~size_t(255);
     return o;
   };
-  const size_t o_fb = carve(sizeof(double) * (size_t)n * c->ldf);
-  const size_t o_dinv = carve(sizeof(double) * (size_t)n);
+  const size_t o_fb = carve(c->es * (size_t)n * c->ldf);
+  const size_t o_dinv = carve(c->es * (size_t)n);
+  const size_t o_b64 = c->f32 ? carve(sizeof(double) * (size_t)n * ldab) : 0;
   const size_t o_ipiv = pivot ? carve(sizeof(int) * (size_t)n) : 0;
   const size_t o_cpl = carve(sizeof(double) * (size_t)nlv * 2 * kk);
   const size_t o_spk = carve(sizeof(double) * (size_t)nspk * 2 * nlv * 2 * kk);
@@ -443,8 +461,12 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
       return fail(SPIKE_ENOMEM);
     }
   }
-  c->fb = (double *)(c->mem + o_fb);
-  c->dinv = (double *)(c->mem + o_dinv);
+  c->fbc = c->mem + o_fb;
+  c->dinvc = c->mem + o_dinv;
+  if (c->f32) {
+    c->band64 = (double *)(c->mem + o_b64);
+    c->ldab64 = ldab;
+  }
   c->ipiv = pivot ? (int *)(c->mem + o_ipiv) : nullptr;
   c->couple = (double *)(c->mem + o_cpl);
   c->spk = (double *)(c->mem + o_spk);
@@ -462,7 +484,7 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
     return o;
   };
   const size_t s_band = band_dev ? 0 : scarve(sizeof(double) * (size_t)n * ldab);
-  const size_t s_z = scarve(sizeof(double) * (size_t)zacc);
+  const size_t s_z = scarve(c->es * (size_t)zacc);
   const size_t s_zoff = scarve(sizeof(int64_t) * (size_t)nlv);
   const size_t s_leaf = scarve(sizeof(LeafDev) * (size_t)nlv);
   size_t maxm = 1;
@@ -490,7 +512,7 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
     }
     dband = b;
   }
-  double *zbuf = (double *)(fscr + s_z);
+  char *zbuf = fscr + s_z;  // element size es
   int64_t *dzoff = (int64_t *)(fscr + s_zoff);
   LeafDev *dleaf = (LeafDev *)(fscr + s_leaf);
   char *tmp = fscr + s_tmp;
@@ -504,7 +526,7 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
         cudaMemcpyAsync(c->status, st, sizeof(st), cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(dzoff, zoff.data(), sizeof(int64_t) * nlv, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(dleaf, c->hl.data(), sizeof(LeafDev) * nlv, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemsetAsync(zbuf, 0, sizeof(double) * (size_t)zacc, s) != cudaSuccess ||
+        cudaMemsetAsync(zbuf, 0, c->es * (size_t)zacc, s) != cudaSuccess ||
         cudaMemsetAsync(c->spk, 0, sizeof(double) * (size_t)nspk * 2 * nlv * 2 * kk, s) != cudaSuccess) {
       g_cuda_err = "initialisation copies";
       return fail2(SPIKE_ECUDA);
@@ -512,10 +534,15 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
   }
   if (c->timing) cudaEventRecord(c->fev[0], s);
   // 1. repack the band into per-leaf LU storage; couplings; Z right-hand sides
-  if ((rc = launch_repack(dband, ldab, kl, ku, n, k, c->ldf, c->dofs, dleaf, nlv, c->fb, &c->status[3], s,
-                          maxlen)) != 0 ||
+  if (c->f32 && cudaMemcpyAsync(c->band64, dband, sizeof(double) * (size_t)n * ldab, cudaMemcpyDeviceToDevice, s) !=
+                    cudaSuccess) {
+    g_cuda_err = "band copy";
+    return fail2(SPIKE_ECUDA);
+  }
+  if ((rc = launch_repack(dband, ldab, kl, ku, n, k, c->ldf, c->dofs, dleaf, nlv, c->fbc, &c->status[3], s, maxlen,
+                          c->f32)) != 0 ||
       (rc = launch_couplings(dband, ldab, kl, ku, n, k, dleaf, nlv, c->couple, s)) != 0 ||
-      (rc = launch_zinit(dleaf, nlv, k, c->couple, zbuf, dzoff, pivot, s)) != 0) {
+      (rc = launch_zinit(dleaf, nlv, k, c->couple, zbuf, dzoff, c->f32, s)) != 0) {
     g_cuda_err = std::string("setup kernels: ") + cudaGetErrorString((cudaError_t)rc);
     return fail2(SPIKE_ECUDA);
   }
@@ -530,7 +557,8 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
       const LeafDev &L = c->hl[i];
       const int nl = (int)L.len;
       const bool mid = L.top_nbr && L.bot_nbr;
-      View zt{zbuf + zoff[i], 1, L.len}, zb{zbuf + zoff[i] + (int64_t)k * L.len, 1, L.len};
+      View zt{(double *)(zbuf + zoff[i] * (int64_t)c->es), 1, L.len},
+          zb{(double *)(zbuf + (zoff[i] + (int64_t)k * L.len) * (int64_t)c->es), 1, L.len};
       if (pivot && mid) ltop[i] = sdesc(c, i, LN, 0, nl, k, zt, nullptr, none, 0.0, zt);
       if (L.bot_nbr) lbot[i] = sdesc(c, i, LN, pivot ? nl - 2 * k : nl - k, nl, k, zb, nullptr, none, 0.0, zb);
       if (mid) ub[i] = sdesc(c, i, UN, 0, nl, 2 * k, zt, nullptr, none, 0.0, zt);
@@ -549,15 +577,15 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
         g_cuda_err = "sweep descriptors";
         return fail2(SPIKE_ECUDA);
       }
-      rc = launch_factor_nopiv(dleaf, nlv, k, c->ldf, c->fb, c->dinv, zbuf, dzoff, &c->status[3], kBoostEps,
-                               c->status, (const SweepDesc *)(c->dargs + off), s);
+      rc = launch_factor_nopiv(dleaf, nlv, k, c->ldf, c->fbc, c->dinvc, zbuf, dzoff, &c->status[3], kBoostEps,
+                               c->status, (const SweepDesc *)(c->dargs + off), s, c->f32);
       if (rc != 0) {
         g_cuda_err = std::string("factor kernel: ") + cudaGetErrorString((cudaError_t)rc);
         return fail2(SPIKE_ECUDA);
       }
       if (c->timing) cudaEventRecord(c->fev[2], s);
     } else {
-      rc = launch_factor_piv(dleaf, nlv, k, c->ldf, c->fb, c->dinv, c->ipiv, c->status, s);
+      rc = launch_factor_piv(dleaf, nlv, k, c->ldf, (double *)c->fbc, (double *)c->dinvc, c->ipiv, c->status, s);
       if (rc != 0) {
         g_cuda_err = std::string("factor kernel: ") + cudaGetErrorString((cudaError_t)rc);
         return fail2(SPIKE_ECUDA);
@@ -571,7 +599,7 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
       if ((rc = pp.run(c)) != 0) return fail2(rc);
     }
   }
-  if ((rc = launch_tips0(dleaf, nlv, k, zbuf, dzoff, c->spk, s)) != 0) {
+  if ((rc = launch_tips0(dleaf, nlv, k, zbuf, dzoff, c->spk, s, c->f32)) != 0) {
     g_cuda_err = std::string("tips kernel: ") + cudaGetErrorString((cudaError_t)rc);
     return fail2(SPIKE_ECUDA);
   }
@@ -740,82 +768,53 @@ static int factor_reduced_level(spike_ctx *c, int lv, char *tmp, size_t tmp_byte
 }
 
 // ================================================================ solve
-extern "C" int spike_solve_ex(spike_handle h, double *F, int64_t ldf, int nrhs, char trans) {
-  if (!valid(h)) return SPIKE_EHANDLE;
-  if (!F) return -2;
-  spike_ctx *c = h;
+// Scratch of one solve pipeline (element size es for the work arrays W and H).
+struct SolveBufs {
+  void *W;     // row-major n x m work array (RHS in, solution out), element size es
+  void *H;     // row-major n x m scratch, element size es
+  double *Y;   // reduced unknowns: leaves x {top, bottom} x k x m, row-major blocks
+  double *TM;  // per-merge temporaries, 2 k x m each
+  double *PP;  // per-leaf partial products (transposed reduced system), k x m each
+};
+
+// Record the SPIKE solve of op(A) X = W (Sec. 2.1-2.3 for N, Sec. 4 for T) on the
+// row-major work array W, in place.  f32: W and H are FP32 and the leaf sweeps run
+// in FP32 (mixed-precision handles); the reduced system is always FP64.
+static void build_solve(spike_ctx *c, Pipeline &pp, const SolveBufs &B, int m, int tr, bool marks) {
   const int64_t n = c->pl.n;
-  if (ldf < n) return -3;
-  if (nrhs < 0) return -4;
-  const int tr = (trans == 'N' || trans == 'n') ? 0 : ((trans == 'T' || trans == 't' || trans == 'C' || trans == 'c') ? 1 : -1);
-  if (tr < 0) return -5;
-  if (c->pivot && c->zero_col) return (int)std::min<int64_t>(c->zero_col, INT_MAX);
-  if (nrhs == 0) return 0;
-  const int k = c->k, nlv = c->nleaves, m = nrhs;
+  const int k = c->k, nlv = c->nleaves;
   const int64_t kk = (int64_t)k * k, km = (int64_t)k * m;
-  cudaStream_t s = c->stream;
-
-  // Work layout: the sweeps run on a ROW-major copy W of F (row r holds the m
-  // right-hand-side entries contiguously), so a block row and its window rows
-  // touch a few contiguous lines instead of m lines n*8 bytes apart.
-  const bool fdev = is_device_ptr(F);
-  size_t off = 0;
-  auto carve = [&](size_t bytes) {
-    size_t o = off;
-    off = (off + bytes + 255) & ~size_t(255);
-    return o;
+  const size_t es = c->es;
+  const int f32 = c->f32;
+  cudaStream_t s = pp.st;
+  double *Y = B.Y, *TM = B.TM, *PP = B.PP;
+  auto eptr = [es](void *base, int64_t idx) { return (double *)((char *)base + idx * (int64_t)es); };
+  auto YB = [&](int i, int t) { return Y + ((int64_t)i * 2 + t) * km; };
+  auto rview = [&](const LeafDev &L, void *base) {
+    if (L.rev) return View{eptr(base, (L.start + L.len - 1) * (int64_t)m), -(int64_t)m, 1};
+    return View{eptr(base, L.start * (int64_t)m), (int64_t)m, 1};
   };
-  const size_t o_f = fdev ? 0 : carve(sizeof(double) * (size_t)n * m);
-  const size_t o_w = (m > 1) ? carve(sizeof(double) * (size_t)n * m) : 0;
-  const size_t o_h = carve(sizeof(double) * (size_t)n * m);
-  const size_t o_y = carve(sizeof(double) * (size_t)nlv * 2 * km);
-  size_t maxm = 1;
-  for (auto &lvv : c->pl.levels) maxm = std::max(maxm, lvv.size());
-  const size_t o_t = carve(sizeof(double) * maxm * 2 * km);
-  const size_t o_p = carve(sizeof(double) * (size_t)nlv * km);
-  SP_TRY(ensure(&c->scr, &c->scr_bytes, off, s));
-  double *Fd = F;
-  int64_t ld = ldf;
-  if (!fdev) {
-    Fd = (double *)(c->scr + o_f);
-    ld = n;
-    SP_CUDA(cudaMemcpy2DAsync(Fd, sizeof(double) * n, F, sizeof(double) * ldf, sizeof(double) * n, m,
-                              cudaMemcpyHostToDevice, s));
-  }
-  double *W = (m > 1) ? (double *)(c->scr + o_w) : Fd;  // m == 1: column-major == row-major
-  double *H = (double *)(c->scr + o_h);
-  double *Y = (double *)(c->scr + o_y);
-  double *TM = (double *)(c->scr + o_t);
-  double *PP = (double *)(c->scr + o_p);
-  auto YB = [&](int i, int t) { return Y + ((int64_t)i * 2 + t) * km; };  // k x m row-major block
-  // leaf view of a row-major n x m array (local row 0 first)
-  auto rview = [&](const LeafDev &L, double *base) {
-    if (L.rev) return View{base + (L.start + L.len - 1) * (int64_t)m, -(int64_t)m, 1};
-    return View{base + L.start * (int64_t)m, (int64_t)m, 1};
+  auto rows = [&](void *base, int64_t row0) { return eptr(base, row0 * (int64_t)m); };
+  // GEMM operand type flags for the work arrays
+  const int tA = f32 ? G_A32 : 0, tB = f32 ? G_B32 : 0, tC0 = f32 ? G_C032 : 0, tC = f32 ? G_C32 : 0;
+  auto typed = [](GemmDesc g, int t) {
+    g.types = t;
+    return g;
   };
-  auto rows = [&](double *base, int64_t row0) { return base + row0 * (int64_t)m; };  // rows of a row-major array
-
-  Pipeline pp;
-  pp.st = s;
+  (void)tA;
+  void *W = B.W, *H = B.H;
   View none{nullptr, 0, 0};
   const bool piv = c->pivot != 0;
   auto memset_op = [&](void *p, size_t bytes) {
     pp.ops.push_back([=](char *) { return (int)cudaMemsetAsync(p, 0, bytes, s); });
   };
   cudaEvent_t *evs = tr ? c->tev : c->nev;
-  const bool timing = c->timing;
   auto mark = [&](int i) {
-    if (!timing) return;
+    if (!marks || !c->timing) return;
     cudaEvent_t e = evs[i];
     pp.ops.push_back([=](char *) { return (int)cudaEventRecord(e, s); });
   };
-  mark(0);
-  if (m > 1) {
-    double *src = Fd;
-    const int64_t ldx = ld;
-    pp.ops.push_back([=](char *) { return launch_transpose(src, W, n, m, ldx, 1, s); });
-  }
-  memset_op(H, sizeof(double) * (size_t)n * m);
+  memset_op(H, es * (size_t)n * m);
   memset_op(Y, sizeof(double) * (size_t)nlv * 2 * km);
 
   if (tr == 0) {
@@ -834,10 +833,12 @@ extern "C" int spike_solve_ex(spike_handle h, double *F, int64_t ldf, int nrhs, 
     GemmBatch g0;
     for (int i = 0; i < nlv; ++i) {
       const LeafDev &L = c->hl[i];
-      if (i > 0) g0.add(gd(nullptr, 0, 0, nullptr, 0, 0, rows(H, L.start), m, 1, YB(i, 0), m, 1, k, m, 0, 0.0, 1.0));
+      if (i > 0)
+        g0.add(typed(gd(nullptr, 0, 0, nullptr, 0, 0, rows(H, L.start), m, 1, YB(i, 0), m, 1, k, m, 0, 0.0, 1.0), tC0));
       if (i + 1 < nlv)
-        g0.add(gd(nullptr, 0, 0, nullptr, 0, 0, rows(H, L.start + L.len - k), m, 1, YB(i, 1), m, 1, k, m, 0, 0.0,
-                  1.0));
+        g0.add(typed(gd(nullptr, 0, 0, nullptr, 0, 0, rows(H, L.start + L.len - k), m, 1, YB(i, 1), m, 1, k, m, 0,
+                        0.0, 1.0),
+                     tC0));
     }
     pp.gemm(g0);
     mark(1);
@@ -877,7 +878,7 @@ extern "C" int spike_solve_ex(spike_handle h, double *F, int64_t ldf, int nrhs, 
     }
     mark(2);
     // ---------------- retrieval (Eqs. one/two/three): X_i = U^{-1}(L^{-1}F - L^{-1}[R_top x_top; 0; R_bot x_bot])
-    memset_op(H, sizeof(double) * (size_t)n * m);
+    memset_op(H, es * (size_t)n * m);
     GemmBatch gc;
     std::vector<SweepDesc> sc(nlv, empty_sweep()), sd(nlv, empty_sweep());
     for (int i = 0; i < nlv; ++i) {
@@ -887,12 +888,13 @@ extern "C" int spike_solve_ex(spike_handle h, double *F, int64_t ldf, int nrhs, 
       const double *Rt = c->couple + (int64_t)i * 2 * kk, *Rb = Rt + kk;
       if (L.top_nbr) {
         const double *xn = L.rev ? YB(i + 1, 0) : YB(i - 1, 1);
-        gc.add(gd(Rt, k, 1, xn, m, 1, nullptr, 0, 0, hv.p, hv.rs, hv.cs, k, m, k, 1.0, 0.0));
+        gc.add(typed(gd(Rt, k, 1, xn, m, 1, nullptr, 0, 0, hv.p, hv.rs, hv.cs, k, m, k, 1.0, 0.0), tC));
       }
       if (L.bot_nbr) {
         const double *xn = L.rev ? YB(i - 1, 1) : YB(i + 1, 0);
-        gc.add(gd(Rb, k, 1, xn, m, 1, nullptr, 0, 0, hv.p + (int64_t)(nl - k) * hv.rs, hv.rs, hv.cs, k, m, k, 1.0,
-                  0.0));
+        gc.add(typed(gd(Rb, k, 1, xn, m, 1, nullptr, 0, 0, (double *)((char *)hv.p + (int64_t)(nl - k) * hv.rs * (int64_t)es),
+                        hv.rs, hv.cs, k, m, k, 1.0, 0.0),
+                     tC));
       }
       if (L.top_nbr && L.bot_nbr) sc[i] = sdesc(c, i, LN, 0, nl, m, hv, nullptr, none, 0, hv);
       else if (L.bot_nbr) sc[i] = sdesc(c, i, LN, piv ? nl - 2 * k : nl - k, nl, m, hv, nullptr, none, 0, hv);
@@ -907,13 +909,13 @@ extern "C" int spike_solve_ex(spike_handle h, double *F, int64_t ldf, int nrhs, 
       const LeafDev &L = c->hl[i];
       if (i > 0) {
         double *v = rows(W, L.start);
-        g0.add(gd(nullptr, 0, 0, nullptr, 0, 0, v, m, 1, YB(i, 0), m, 1, k, m, 0, 0.0, 1.0));
-        gz.add(gd(nullptr, 0, 0, nullptr, 0, 0, nullptr, 0, 0, v, m, 1, k, m, 0, 0.0, 0.0));
+        g0.add(typed(gd(nullptr, 0, 0, nullptr, 0, 0, v, m, 1, YB(i, 0), m, 1, k, m, 0, 0.0, 1.0), tC0));
+        gz.add(typed(gd(nullptr, 0, 0, nullptr, 0, 0, nullptr, 0, 0, v, m, 1, k, m, 0, 0.0, 0.0), tC));
       }
       if (i + 1 < nlv) {
         double *v = rows(W, L.start + L.len - k);
-        g0.add(gd(nullptr, 0, 0, nullptr, 0, 0, v, m, 1, YB(i, 1), m, 1, k, m, 0, 0.0, 1.0));
-        gz.add(gd(nullptr, 0, 0, nullptr, 0, 0, nullptr, 0, 0, v, m, 1, k, m, 0, 0.0, 0.0));
+        g0.add(typed(gd(nullptr, 0, 0, nullptr, 0, 0, v, m, 1, YB(i, 1), m, 1, k, m, 0, 0.0, 1.0), tC0));
+        gz.add(typed(gd(nullptr, 0, 0, nullptr, 0, 0, nullptr, 0, 0, v, m, 1, k, m, 0, 0.0, 0.0), tC));
       }
     }
     pp.gemm(g0);
@@ -930,7 +932,7 @@ extern "C" int spike_solve_ex(spike_handle h, double *F, int64_t ldf, int nrhs, 
     if (piv) {
       // the pivoted L^T sweep runs in place: copy w into H first
       pp.stage(sa, e0, -1, -1, c->ldf, c->dofs, k);
-      const size_t bytes = sizeof(double) * (size_t)n * m;
+      const size_t bytes = es * (size_t)n * m;
       pp.ops.push_back([=](char *) { return (int)cudaMemcpyAsync(H, W, bytes, cudaMemcpyDeviceToDevice, s); });
       pp.stage(sb, e0, LT, -1, c->ldf, c->dofs, k);
     } else {
@@ -945,11 +947,13 @@ extern "C" int spike_solve_ex(spike_handle h, double *F, int64_t ldf, int nrhs, 
       const double *Rt = c->couple + (int64_t)j * 2 * kk, *Rb = Rt + kk;
       if (L.top_nbr) {
         double *tgt = L.rev ? YB(j + 1, 0) : YB(j - 1, 1);
-        gg.add(gd(Rt, 1, k, hv.p, hv.rs, hv.cs, tgt, m, 1, tgt, m, 1, k, m, k, -1.0, 1.0));
+        gg.add(typed(gd(Rt, 1, k, hv.p, hv.rs, hv.cs, tgt, m, 1, tgt, m, 1, k, m, k, -1.0, 1.0), tB));
       }
       if (L.bot_nbr) {
         double *tgt = L.rev ? YB(j - 1, 1) : YB(j + 1, 0);
-        gg.add(gd(Rb, 1, k, hv.p + (int64_t)(nl - k) * hv.rs, hv.rs, hv.cs, tgt, m, 1, tgt, m, 1, k, m, k, -1.0, 1.0));
+        gg.add(typed(gd(Rb, 1, k, (double *)((char *)hv.p + (int64_t)(nl - k) * hv.rs * (int64_t)es), hv.rs, hv.cs,
+                        tgt, m, 1, tgt, m, 1, k, m, k, -1.0, 1.0),
+                     tB));
       }
     }
     pp.gemm(gg);
@@ -1005,17 +1009,19 @@ extern "C" int spike_solve_ex(spike_handle h, double *F, int64_t ldf, int nrhs, 
     }
     mark(2);
     // ---------------- D^T stage (Eq. sweeps_in_D): X_i = L^{-T}(w + U^{-T}[y_top; 0; y_bot])
-    memset_op(H, sizeof(double) * (size_t)n * m);
+    memset_op(H, es * (size_t)n * m);
     GemmBatch gp;
     std::vector<SweepDesc> sc(nlv, empty_sweep()), sd(nlv, empty_sweep());
     for (int i = 0; i < nlv; ++i) {
       const LeafDev &L = c->hl[i];
       const int nl = (int)L.len;
       const View fv = rview(L, W), hv = rview(L, H);
-      if (i > 0) gp.add(gd(nullptr, 0, 0, nullptr, 0, 0, YB(i, 0), m, 1, rows(H, L.start), m, 1, k, m, 0, 0.0, 1.0));
+      if (i > 0)
+        gp.add(typed(gd(nullptr, 0, 0, nullptr, 0, 0, YB(i, 0), m, 1, rows(H, L.start), m, 1, k, m, 0, 0.0, 1.0), tC));
       if (i + 1 < nlv)
-        gp.add(gd(nullptr, 0, 0, nullptr, 0, 0, YB(i, 1), m, 1, rows(H, L.start + L.len - k), m, 1, k, m, 0, 0.0,
-                  1.0));
+        gp.add(typed(gd(nullptr, 0, 0, nullptr, 0, 0, YB(i, 1), m, 1, rows(H, L.start + L.len - k), m, 1, k, m, 0,
+                        0.0, 1.0),
+                     tC));
       if (L.top_nbr && L.bot_nbr) sc[i] = sdesc(c, i, UT, 0, nl, m, hv, nullptr, none, 0, hv);
       else if (L.bot_nbr) sc[i] = sdesc(c, i, UT, nl - k, nl, m, hv, nullptr, none, 0, hv);
       SweepDesc d = sdesc(c, i, LT, 0, nl, m, fv, nullptr, none, 0, fv);
@@ -1030,22 +1036,163 @@ extern "C" int spike_solve_ex(spike_handle h, double *F, int64_t ldf, int nrhs, 
     pp.gemm(gp);
     if (piv) {
       // W += H, then the pivoted L^T sweep in place
+      std::vector<SweepDesc> e0 = e0_dummy(nlv);
       pp.stage(sc, e0, -1, -1, c->ldf, c->dofs, k);
       const int64_t cnt = n * (int64_t)m;
-      pp.ops.push_back([=](char *) { return launch_axpy(W, H, 1.0, cnt, s); });
-      pp.stage(sd, e0, LT, -1, c->ldf, c->dofs, k);
+      double *Wd = (double *)W, *Hd = (double *)H;
+      pp.ops.push_back([=](char *) { return launch_axpy(Wd, Hd, 1.0, cnt, s); });
+      std::vector<SweepDesc> e1 = e0_dummy(nlv);
+      pp.stage(sd, e1, LT, -1, c->ldf, c->dofs, k);
     } else {
       pp.stage(sc, sd, -1, -1, c->ldf, c->dofs, k);
     }
   }
-  if (m > 1) {
-    double *dst = Fd;
-    const int64_t ldx = ld;
-    pp.ops.push_back([=](char *) { return launch_transpose(W, dst, n, m, ldx, 0, s); });
+}
+
+extern "C" int spike_solve_ex(spike_handle h, double *F, int64_t ldf, int nrhs, char trans) {
+  if (!valid(h)) return SPIKE_EHANDLE;
+  if (!F) return -2;
+  spike_ctx *c = h;
+  const int64_t n = c->pl.n;
+  if (ldf < n) return -3;
+  if (nrhs < 0) return -4;
+  const int tr = (trans == 'N' || trans == 'n') ? 0 : ((trans == 'T' || trans == 't' || trans == 'C' || trans == 'c') ? 1 : -1);
+  if (tr < 0) return -5;
+  if (c->pivot && c->zero_col) return (int)std::min<int64_t>(c->zero_col, INT_MAX);
+  if (nrhs == 0) return 0;
+  const int k = c->k, nlv = c->nleaves, m = nrhs;
+  const int64_t km = (int64_t)k * m;
+  const size_t es = c->es;
+  cudaStream_t s = c->stream;
+
+  // Work layout: the sweeps run on a ROW-major copy W of F (row r holds the m
+  // right-hand-side entries contiguously), so a block row and its window rows
+  // touch a few contiguous lines instead of m lines n*8 bytes apart.
+  const bool fdev = is_device_ptr(F);
+  const bool mixed = c->f32 != 0;
+  size_t off = 0;
+  auto carve = [&](size_t bytes) {
+    size_t o = off;
+    off = (off + bytes + 255) & ~size_t(255);
+    return o;
+  };
+  const size_t nm8 = sizeof(double) * (size_t)n * m;
+  const size_t o_f = fdev ? 0 : carve(nm8);
+  const size_t o_w = (m > 1 || mixed) ? carve(es * (size_t)n * m) : 0;
+  const size_t o_h = carve(es * (size_t)n * m);
+  const size_t o_y = carve(sizeof(double) * (size_t)nlv * 2 * km);
+  size_t maxm = 1;
+  for (auto &lvv : c->pl.levels) maxm = std::max(maxm, lvv.size());
+  const size_t o_t = carve(sizeof(double) * maxm * 2 * km);
+  const size_t o_p = carve(sizeof(double) * (size_t)nlv * km);
+  // mixed precision: F0 (the right-hand side), X (FP64 solution), R (residual), norms
+  const size_t o_f0 = mixed ? carve(nm8) : 0;
+  const size_t o_x = mixed ? carve(nm8) : 0;
+  const size_t o_r = mixed ? carve(nm8) : 0;
+  const size_t o_nrm = mixed ? carve(sizeof(unsigned long long) * (1 + 2 * (size_t)m)) : 0;
+  SP_TRY(ensure(&c->scr, &c->scr_bytes, off, s));
+  double *Fd = F;
+  int64_t ld = ldf;
+  if (!fdev) {
+    Fd = (double *)(c->scr + o_f);
+    ld = n;
+    SP_CUDA(cudaMemcpy2DAsync(Fd, sizeof(double) * n, F, sizeof(double) * ldf, sizeof(double) * n, m,
+                              cudaMemcpyHostToDevice, s));
   }
-  mark(3);
-  SP_TRY(pp.run(c));
-  if (timing) (tr ? c->tdone : c->ndone) = true;
+  SolveBufs B;
+  B.W = (m > 1 || mixed) ? (void *)(c->scr + o_w) : (void *)Fd;  // FP64, m == 1: column-major == row-major
+  B.H = c->scr + o_h;
+  B.Y = (double *)(c->scr + o_y);
+  B.TM = (double *)(c->scr + o_t);
+  B.PP = (double *)(c->scr + o_p);
+  cudaEvent_t *evs = tr ? c->tev : c->nev;
+
+  if (!mixed) {
+    Pipeline pp;
+    pp.st = s;
+    if (c->timing) {
+      cudaEvent_t e = evs[0];
+      pp.ops.push_back([=](char *) { return (int)cudaEventRecord(e, s); });
+    }
+    if (m > 1) {
+      double *src = Fd, *dst = (double *)B.W;
+      const int64_t ldx = ld;
+      pp.ops.push_back([=](char *) { return launch_transpose(src, dst, n, m, ldx, 1, s); });
+    }
+    build_solve(c, pp, B, m, tr, true);
+    if (m > 1) {
+      double *src = (double *)B.W, *dst = Fd;
+      const int64_t ldx = ld;
+      pp.ops.push_back([=](char *) { return launch_transpose(src, dst, n, m, ldx, 0, s); });
+    }
+    if (c->timing) {
+      cudaEvent_t e = evs[3];
+      pp.ops.push_back([=](char *) { return (int)cudaEventRecord(e, s); });
+    }
+    SP_TRY(pp.run(c));
+    if (c->timing) (tr ? c->tdone : c->ndone) = true;
+  } else {
+    // FP64 iterative refinement around the FP32 SPIKE solve
+    double *F0 = (double *)(c->scr + o_f0), *X = (double *)(c->scr + o_x), *R = (double *)(c->scr + o_r);
+    unsigned long long *nrm = (unsigned long long *)(c->scr + o_nrm);
+    if (c->timing) SP_CUDA(cudaEventRecord(evs[0], s));
+    SP_CUDA(cudaMemcpy2DAsync(F0, sizeof(double) * n, Fd, sizeof(double) * ld, sizeof(double) * n, m,
+                              cudaMemcpyDeviceToDevice, s));
+    SP_CUDA(cudaMemsetAsync(X, 0, nm8, s));
+    const double *rhs = F0;  // first step: x = 0, r = F
+    int steps = 0;
+    double worst = INFINITY;
+    std::vector<unsigned long long> hn(1 + 2 * (size_t)m);
+    for (;;) {
+      Pipeline pp;
+      pp.st = s;
+      pp.f32 = 1;
+      {
+        const double *src = rhs;
+        float *dst = (float *)B.W;
+        pp.ops.push_back([=](char *) { return launch_to_work32(src, n, dst, n, m, s); });
+      }
+      build_solve(c, pp, B, m, tr, steps == 0);
+      {
+        const float *d = (const float *)B.W;
+        pp.ops.push_back([=](char *) { return launch_add_work32(X, n, d, n, m, s); });
+      }
+      // r = F - op(A) x (FP64, original band) and the per-column backward errors
+      pp.ops.push_back([=](char *) { return (int)cudaMemsetAsync(nrm, 0, sizeof(unsigned long long) * (1 + 2 * (size_t)m), s); });
+      {
+        const double *band = c->band64;
+        const int64_t ldb = c->ldab64;
+        const int kl = c->pl.kl, ku = c->pl.ku;
+        pp.ops.push_back([=](char *) { return launch_residual(band, ldb, n, kl, ku, X, F0, R, m, tr, nrm, s); });
+      }
+      SP_TRY(pp.run(c));
+      ++steps;
+      SP_CUDA(cudaMemcpyAsync(hn.data(), nrm, sizeof(unsigned long long) * hn.size(), cudaMemcpyDeviceToHost, s));
+      SP_CUDA(cudaStreamSynchronize(s));
+      auto as_d = [](unsigned long long b) {
+        double d;
+        memcpy(&d, &b, sizeof(d));
+        return d;
+      };
+      const double an = as_d(hn[0]);
+      worst = 0.0;
+      for (int col = 0; col < m; ++col) {
+        const double r = as_d(hn[1 + 2 * col]), x = as_d(hn[2 + 2 * col]);
+        const double be = (an > 0 && x > 0) ? r / (an * x) : (r == 0 ? 0.0 : INFINITY);
+        worst = std::max(worst, be);
+      }
+      if (!(worst > SPIKE_MIXED_TOL) || steps >= SPIKE_MIXED_MAX_STEPS) break;
+      rhs = R;
+    }
+    c->last_iters = steps;
+    c->last_berr = worst;
+    SP_CUDA(cudaMemcpy2DAsync(Fd, sizeof(double) * ld, X, sizeof(double) * n, sizeof(double) * n, m,
+                              cudaMemcpyDeviceToDevice, s));
+    if (c->timing) {
+      SP_CUDA(cudaEventRecord(evs[3], s));
+      (tr ? c->tdone : c->ndone) = true;
+    }
+  }
   if (!fdev) {
     SP_CUDA(cudaMemcpy2DAsync(F, sizeof(double) * ldf, Fd, sizeof(double) * n, sizeof(double) * n, m,
                               cudaMemcpyDeviceToHost, s));
@@ -1072,6 +1219,9 @@ extern "C" int spike_get_info(spike_handle h, spike_info *out) {
   out->boosts = h->boosts;
   out->zero_pivot_col = h->zero_col;
   out->device_bytes = (int64_t)(h->mem_bytes + h->scr_bytes + h->dargs_bytes);
+  out->mixed = h->f32;
+  out->refine_steps = h->last_iters;
+  out->refine_berr = h->last_berr;
   return 0;
 }
 

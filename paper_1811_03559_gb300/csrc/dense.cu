@@ -52,7 +52,10 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmDesc *descs, int ndesc) 
         kq = idx >> 6;
       }
       double v = 0.0;
-      if (i0 + i < D.M && kk + kq < D.K) v = D.A[(int64_t)(i0 + i) * D.a_rs + (int64_t)(kk + kq) * D.a_cs];
+      if (i0 + i < D.M && kk + kq < D.K) {
+        const int64_t o = (int64_t)(i0 + i) * D.a_rs + (int64_t)(kk + kq) * D.a_cs;
+        v = (D.types & G_A32) ? (double)((const float *)D.A)[o] : D.A[o];
+      }
       As[kq][i] = v;
       int j, kb;
       if (b_jfast) {
@@ -63,7 +66,10 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmDesc *descs, int ndesc) 
         j = idx >> 4;
       }
       double w = 0.0;
-      if (j0 + j < D.N && kk + kb < D.K) w = D.B[(int64_t)(kk + kb) * D.b_rs + (int64_t)(j0 + j) * D.b_cs];
+      if (j0 + j < D.N && kk + kb < D.K) {
+        const int64_t o = (int64_t)(kk + kb) * D.b_rs + (int64_t)(j0 + j) * D.b_cs;
+        w = (D.types & G_B32) ? (double)((const float *)D.B)[o] : D.B[o];
+      }
       Bs[kb][j] = w;
     }
     __syncthreads();
@@ -90,8 +96,13 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmDesc *descs, int ndesc) 
       const int j = j0 + tx + 16 * v;
       if (j >= D.N) continue;
       double r = D.alpha * acc[u][v];
-      if (D.beta != 0.0) r = fma(D.beta, D.C0[(int64_t)i * D.c0_rs + (int64_t)j * D.c0_cs], r);
-      D.C[(int64_t)i * D.c_rs + (int64_t)j * D.c_cs] = r;
+      if (D.beta != 0.0) {
+        const int64_t o = (int64_t)i * D.c0_rs + (int64_t)j * D.c0_cs;
+        r = fma(D.beta, (D.types & G_C032) ? (double)((const float *)D.C0)[o] : D.C0[o], r);
+      }
+      const int64_t oc = (int64_t)i * D.c_rs + (int64_t)j * D.c_cs;
+      if (D.types & G_C32) ((float *)D.C)[oc] = (float)r;
+      else D.C[oc] = r;
     }
   }
 }
@@ -370,6 +381,56 @@ int launch_transpose(const double *in, double *out, int64_t rows, int cols, int6
   return (int)cudaGetLastError();
 }
 
+// Column-major FP64 <-> row-major FP32 work array (mixed-precision refinement).
+__global__ void k_work32(const double *__restrict__ in, int64_t ld, float *__restrict__ w, double *x,
+                         const float *__restrict__ d, int64_t rows, int cols, int add) {
+  __shared__ double t[32][33];
+  const int64_t r0 = (int64_t)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  if (!add) {
+    for (int q = ty; q < 32; q += 8) {
+      const int64_t r = r0 + tx;
+      const int c = c0 + q;
+      t[q][tx] = (r < rows && c < cols) ? in[(int64_t)c * ld + r] : 0.0;
+    }
+    __syncthreads();
+    for (int q = ty; q < 32; q += 8) {
+      const int64_t r = r0 + q;
+      const int c = c0 + tx;
+      if (r < rows && c < cols) w[r * cols + c] = (float)t[tx][q];
+    }
+  } else {
+    for (int q = ty; q < 32; q += 8) {
+      const int64_t r = r0 + q;
+      const int c = c0 + tx;
+      t[tx][q] = (r < rows && c < cols) ? (double)d[r * cols + c] : 0.0;
+    }
+    __syncthreads();
+    for (int q = ty; q < 32; q += 8) {
+      const int64_t r = r0 + tx;
+      const int c = c0 + q;
+      if (r < rows && c < cols) x[(int64_t)c * ld + r] += t[q][tx];
+    }
+  }
+}
+
+int launch_to_work32(const double *in, int64_t ld, float *out, int64_t rows, int cols, void *stream) {
+  if (rows <= 0 || cols <= 0) return 0;
+  dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((cols + 31) / 32));
+  k_work32<<<grid, 256, 0, (cudaStream_t)stream>>>(in, ld, out, nullptr, nullptr, rows, cols, 0);
+  count_launch();
+  return (int)cudaGetLastError();
+}
+
+int launch_add_work32(double *x, int64_t ld, const float *d, int64_t rows, int cols, void *stream) {
+  if (rows <= 0 || cols <= 0) return 0;
+  dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((cols + 31) / 32));
+  k_work32<<<grid, 256, 0, (cudaStream_t)stream>>>(nullptr, ld, nullptr, x, d, rows, cols, 1);
+  count_launch();
+  return (int)cudaGetLastError();
+}
+
 // -------------------------------------------------------- block sums
 // out[e] = sum_{i < count} in[i*stride + e], summed in index order (deterministic).
 __global__ void k_sum_blocks(const SumDesc *d) {
@@ -445,6 +506,60 @@ __global__ void __launch_bounds__(256) k_berr(const double *__restrict__ band, i
     atomicMax(&scratch[2 + 2 * c], (unsigned long long)__double_as_longlong(xmax));
     if (c == 0) atomicMax(&scratch[0], (unsigned long long)__double_as_longlong(amax));
   }
+}
+
+// R = F - op(A) X for the refinement loop, with the same norm reductions as k_berr.
+__global__ void __launch_bounds__(256) k_resid(const double *__restrict__ band, int64_t ldab, int64_t n, int kl,
+                                               int ku, const double *X, const double *F, double *R, int trans,
+                                               unsigned long long *norms) {
+  const int c = blockIdx.y;
+  const double *x = X + (int64_t)c * n;
+  const double *f = F + (int64_t)c * n;
+  double *rr = R + (int64_t)c * n;
+  double rmax = 0.0, xmax = 0.0, amax = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0, a = 0.0;
+    if (!trans) {
+      const int64_t jlo = i - kl > 0 ? i - kl : 0, jhi = i + ku < n - 1 ? i + ku : n - 1;
+      for (int64_t j = jlo; j <= jhi; ++j) {
+        const double v = band[j * ldab + ku + i - j];
+        s = fma(v, x[j], s);
+        a += fabs(v);
+      }
+    } else {
+      const int64_t jlo = i - ku > 0 ? i - ku : 0, jhi = i + kl < n - 1 ? i + kl : n - 1;
+      for (int64_t j = jlo; j <= jhi; ++j) {
+        const double v = band[i * ldab + ku + j - i];
+        s = fma(v, x[j], s);
+        a += fabs(v);
+      }
+    }
+    const double r = f[i] - s;
+    rr[i] = r;
+    rmax = fmax(rmax, fabs(r));
+    xmax = fmax(xmax, fabs(x[i]));
+    amax = fmax(amax, a);
+  }
+  for (int o = 16; o; o >>= 1) {
+    rmax = fmax(rmax, __shfl_xor_sync(FULLMASK, rmax, o));
+    xmax = fmax(xmax, __shfl_xor_sync(FULLMASK, xmax, o));
+    amax = fmax(amax, __shfl_xor_sync(FULLMASK, amax, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&norms[1 + 2 * c], (unsigned long long)__double_as_longlong(rmax));
+    atomicMax(&norms[2 + 2 * c], (unsigned long long)__double_as_longlong(xmax));
+    if (c == 0) atomicMax(&norms[0], (unsigned long long)__double_as_longlong(amax));
+  }
+}
+
+int launch_residual(const double *band, int64_t ldab, int64_t n, int kl, int ku, const double *X, const double *F,
+                    double *R, int nrhs, int trans, unsigned long long *norms, void *stream) {
+  int bx = (int)((n + 255) / 256);
+  if (bx > 152 * 8) bx = 152 * 8;
+  dim3 grid(bx, nrhs);
+  k_resid<<<grid, 256, 0, (cudaStream_t)stream>>>(band, ldab, n, kl, ku, X, F, R, trans, norms);
+  count_launch();
+  return (int)cudaGetLastError();
 }
 
 int launch_berr(const double *band, int64_t ldab, int64_t n, int kl, int ku, const double *X, const double *F,

@@ -88,14 +88,16 @@ struct SweepDesc {
 // A(i,k) = A[i*a_rs + k*a_cs] (M x K), B(k,j) = B[k*b_rs + j*b_cs] (K x N),
 // C(i,j) = C[i*c_rs + j*c_cs]; C0 likewise (not read when beta == 0).  Negative
 // strides express reversed (Q) and transposed views.  K = 0 gives a scaled copy.
+// `types` marks operands stored in FP32 (bit 1 A, 2 B, 4 C0, 8 C); arithmetic is FP64.
 struct GemmDesc {
   const double *A, *B, *C0;
   double *C;
   int64_t a_rs, a_cs, b_rs, b_cs, c0_rs, c0_cs, c_rs, c_cs;
   int M, N, K, tiles_n;
   double alpha, beta;
-  int tile0, pad;
+  int tile0, types;
 };
+enum GemmTypes { G_A32 = 1, G_B32 = 2, G_C032 = 4, G_C32 = 8 };
 
 // Batched dense LU with partial pivoting (first index of the largest |entry|).
 struct LuDesc {
@@ -128,25 +130,26 @@ struct SumDesc {
 // ------------------------------------------------------------ launchers
 // Each returns cudaError_t as int (0 = success) and counts its kernel launches.
 void count_launch(int n = 1);
+// f32 != 0: the leaf storage (factors, spike columns, sweep operands) is FP32 (mixed-precision handles).
 int launch_repack(const double *band, int64_t ldab, int kl, int ku, int64_t n, int k, int ldf, int dofs,
-                  const LeafDev *leaves, int nleaves, double *fb, unsigned long long *amax_bits, void *stream,
-                  int64_t max_leaf_len);
+                  const LeafDev *leaves, int nleaves, void *fb, unsigned long long *amax_bits, void *stream,
+                  int64_t max_leaf_len, int f32);
 int launch_couplings(const double *band, int64_t ldab, int kl, int ku, int64_t n, int k, const LeafDev *leaves,
                      int nleaves, double *couple, void *stream);
-int launch_zinit(const LeafDev *leaves, int nleaves, int k, const double *couple, double *zbuf,
-                 const int64_t *zoff, int pivot, void *stream);
+int launch_zinit(const LeafDev *leaves, int nleaves, int k, const double *couple, void *zbuf,
+                 const int64_t *zoff, int f32, void *stream);
 // Block LU of every leaf followed, in the same CTA, by the leaf's spike sweeps
 // (sweeps[2*leaf], sweeps[2*leaf+1]; empty slots have ncols == 0).
-int launch_factor_nopiv(const LeafDev *leaves, int nleaves, int k, int ldf, double *fb, double *dinv, double *zbuf,
+int launch_factor_nopiv(const LeafDev *leaves, int nleaves, int k, int ldf, void *fb, void *dinv, void *zbuf,
                         const int64_t *zoff, const unsigned long long *amax_bits, double boost_eps,
-                        unsigned long long *status, const SweepDesc *sweeps, void *stream);
+                        unsigned long long *status, const SweepDesc *sweeps, void *stream, int f32);
 int launch_factor_piv(const LeafDev *leaves, int nleaves, int k, int ldf, double *fb, double *dinv, int *ipiv,
                       unsigned long long *status, void *stream);
 // Runs per_cta consecutive descriptors per CTA (a leaf's sweep sequence), ncta CTAs.
-int launch_sweeps(const SweepDesc *descs, int ncta, int per_cta, int ldf, int dofs, void *stream);
+int launch_sweeps(const SweepDesc *descs, int ncta, int per_cta, int ldf, int dofs, void *stream, int f32 = 0);
 int launch_piv_sweep(int kind, const SweepDesc *descs, int ndesc, int k, int ldf, int dofs, void *stream);
-int launch_tips0(const LeafDev *leaves, int nleaves, int k, const double *zbuf, const int64_t *zoff, double *spk,
-                 void *stream);
+int launch_tips0(const LeafDev *leaves, int nleaves, int k, const void *zbuf, const int64_t *zoff, double *spk,
+                 void *stream, int f32);
 int launch_gemm(const GemmDesc *d, int ndesc, int total_tiles, void *stream);
 constexpr int GEMM_TILE = 64;
 int launch_getrf(const LuDesc *d, int ndesc, int maxn, unsigned long long *status, void *stream);
@@ -157,6 +160,14 @@ int launch_assemble_M(const double *const *v, const double *const *w, int k, int
 int launch_axpy(double *y, const double *x, double alpha, int64_t count, void *stream);
 int launch_transpose(const double *in, double *out, int64_t rows, int cols, int64_t ld, int to_row_major,
                      void *stream);
+// Column-major FP64 (rows x cols, ld) -> row-major FP32 work array.
+int launch_to_work32(const double *in, int64_t ld, float *out, int64_t rows, int cols, void *stream);
+// Column-major FP64 x (ld) += row-major FP32 correction d.
+int launch_add_work32(double *x, int64_t ld, const float *d, int64_t rows, int cols, void *stream);
+// Residual for iterative refinement: R = F - op(A) X (all column-major FP64, ld = n) and, as bit
+// patterns of non-negative doubles, norms[1+2c] = ||R_c||_inf, norms[2+2c] = ||X_c||_inf, norms[0] = ||op(A)||_inf.
+int launch_residual(const double *band, int64_t ldab, int64_t n, int kl, int ku, const double *X, const double *F,
+                    double *R, int nrhs, int trans, unsigned long long *norms, void *stream);
 int launch_sum_blocks(const SumDesc *d, int ndesc, int64_t max_elems, void *stream);
 // Backward-error reduction: scratch receives, as bit patterns of non-negative doubles,
 // [0] ||op(A)||_inf, [1+2c] ||op(A)x_c - f_c||_inf, [2+2c] ||x_c||_inf.

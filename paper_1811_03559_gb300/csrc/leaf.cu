@@ -32,9 +32,10 @@ constexpr size_t SWEEP_SMEM = sizeof(double) * ((size_t)WCH * NB + NB * NB + NB 
 // ------------------------------------------------------------------ repack
 // User band (LAPACK layout, global frame) -> per-leaf LU band (local frame),
 // zero outside A_i's band, plus max|a_ij| for the boosting threshold.
+template <typename T>
 __global__ void __launch_bounds__(256) k_repack(const double *__restrict__ band, int64_t ldab, int kl, int ku,
                                                 int64_t n, int k, int ldf, int dofs, const LeafDev *leaves,
-                                                double *fb, unsigned long long *amax_bits) {
+                                                T *fb, unsigned long long *amax_bits) {
   const LeafDev L = leaves[blockIdx.y];
   const int64_t nl = L.len;
   const int64_t ncols_per_blk = 8;
@@ -52,7 +53,7 @@ __global__ void __launch_bounds__(256) k_repack(const double *__restrict__ band,
       const int64_t off = gi - gj;
       if (off >= -ku && off <= kl) v = band[gj * ldab + ku + off];
     }
-    fb[(L.start + c) * ldf + d] = v;
+    fb[(L.start + c) * ldf + d] = (T)v;
     lmax = fmax(lmax, fabs(v));
   }
   for (int o = 16; o; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(FULLMASK, lmax, o));
@@ -60,10 +61,15 @@ __global__ void __launch_bounds__(256) k_repack(const double *__restrict__ band,
 }
 
 int launch_repack(const double *band, int64_t ldab, int kl, int ku, int64_t n, int k, int ldf, int dofs,
-                  const LeafDev *leaves, int nleaves, double *fb, unsigned long long *amax_bits, void *stream,
-                  int64_t max_leaf_len) {
+                  const LeafDev *leaves, int nleaves, void *fb, unsigned long long *amax_bits, void *stream,
+                  int64_t max_leaf_len, int f32) {
   dim3 grid((unsigned)((max_leaf_len + 7) / 8), (unsigned)nleaves);
-  k_repack<<<grid, 256, 0, (cudaStream_t)stream>>>(band, ldab, kl, ku, n, k, ldf, dofs, leaves, fb, amax_bits);
+  if (f32)
+    k_repack<float><<<grid, 256, 0, (cudaStream_t)stream>>>(band, ldab, kl, ku, n, k, ldf, dofs, leaves, (float *)fb,
+                                                            amax_bits);
+  else
+    k_repack<double><<<grid, 256, 0, (cudaStream_t)stream>>>(band, ldab, kl, ku, n, k, ldf, dofs, leaves,
+                                                             (double *)fb, amax_bits);
   count_launch();
   return (int)cudaGetLastError();
 }
@@ -111,30 +117,34 @@ int launch_couplings(const double *band, int64_t ldab, int kl, int ku, int64_t n
 
 // Z init (Z already zeroed): R_top into rows [0,k) of columns [0,k) for leaves that
 // need the top spike (both neighbours), R_bot into rows [nl-k, nl) of columns [k, 2k).
-__global__ void k_zinit(const LeafDev *leaves, int k, const double *couple, double *zbuf, const int64_t *zoff) {
+template <typename T>
+__global__ void k_zinit(const LeafDev *leaves, int k, const double *couple, T *zbuf, const int64_t *zoff) {
   const LeafDev L = leaves[blockIdx.x];
   const int64_t nl = L.len;
   const int64_t kk = (int64_t)k * k;
   const double *Rt = couple + (int64_t)blockIdx.x * 2 * kk;
   const double *Rb = Rt + kk;
-  double *Z = zbuf + zoff[blockIdx.x];
+  T *Z = zbuf + zoff[blockIdx.x];
   const bool mid = L.top_nbr && L.bot_nbr;
   for (int64_t idx = threadIdx.x; idx < kk; idx += blockDim.x) {
     const int a = (int)(idx % k), b = (int)(idx / k);  // row a fastest -> coalesced column-major writes
-    if (mid) Z[(int64_t)b * nl + a] = Rt[(int64_t)a * k + b];
-    if (L.bot_nbr) Z[(int64_t)(k + b) * nl + (nl - k + a)] = Rb[(int64_t)a * k + b];
+    if (mid) Z[(int64_t)b * nl + a] = (T)Rt[(int64_t)a * k + b];
+    if (L.bot_nbr) Z[(int64_t)(k + b) * nl + (nl - k + a)] = (T)Rb[(int64_t)a * k + b];
   }
 }
 
-int launch_zinit(const LeafDev *leaves, int nleaves, int k, const double *couple, double *zbuf, const int64_t *zoff,
-                 int pivot, void *stream) {
-  (void)pivot;
-  k_zinit<<<nleaves, 256, 0, (cudaStream_t)stream>>>(leaves, k, couple, zbuf, zoff);
+int launch_zinit(const LeafDev *leaves, int nleaves, int k, const double *couple, void *zbuf, const int64_t *zoff,
+                 int f32, void *stream) {
+  if (f32)
+    k_zinit<float><<<nleaves, 256, 0, (cudaStream_t)stream>>>(leaves, k, couple, (float *)zbuf, zoff);
+  else
+    k_zinit<double><<<nleaves, 256, 0, (cudaStream_t)stream>>>(leaves, k, couple, (double *)zbuf, zoff);
   count_launch();
   return (int)cudaGetLastError();
 }
 
-__device__ void sweep_run(const SweepDesc &D, int ldf, int dofs, double *sm);
+template <typename T>
+__device__ void sweep_run(const SweepDesc &D, int ldf, int dofs, T *sm);
 
 // -------------------------------------------------- non-pivoting block LU
 // Blocked right-looking band LU (no pivoting, diagonal boosting, Sec. 2.3) of one
@@ -144,25 +154,27 @@ __device__ void sweep_run(const SweepDesc &D, int ldf, int dofs, double *sm);
 // Per block of NB columns: panel LU in shared memory (NB columns x NB+k rows),
 // U12 = L11^{-1} A12 (and the fused Z rows), then A22 -= L21 U12 on the k x k
 // window (and the fused Z rows below the panel).
+template <typename T>
 __global__ void __launch_bounds__(NTHREADS, 1)
-    k_factor_nopiv(const LeafDev *leaves, int k, int ldf, double *fb_all, double *dinv_all, double *zbuf,
+    k_factor_nopiv(const LeafDev *leaves, int k, int ldf, T *fb_all, T *dinv_all, T *zbuf,
                    const int64_t *zoff, const unsigned long long *amax_bits, double boost_eps,
                    unsigned long long *status, const SweepDesc *sweeps) {
-  extern __shared__ double smem[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *smem = (T *)smem_raw;
   const LeafDev L = leaves[blockIdx.x];
   const int64_t nl = L.len;
-  double *fb = fb_all + L.start * (int64_t)ldf;
-  double *dinv = dinv_all + L.start;
+  T *fb = fb_all + L.start * (int64_t)ldf;
+  T *dinv = dinv_all + L.start;
   const bool fuse = L.top_nbr && L.bot_nbr;
-  double *Z = zbuf + zoff[blockIdx.x];
+  T *Z = zbuf + zoff[blockIdx.x];
   const int kz = fuse ? k : 0;
   const int PLD = NB + k + 1;
   const int TLD = CW + 1;
-  double *P = smem;              // NB columns x PLD rows, column-major
-  double *T = smem + NB * PLD;   // NB rows x TLD, row-major
-  __shared__ double s_rinv;
+  T *P = smem;                // NB columns x PLD rows, column-major
+  T *T12 = smem + NB * PLD;   // NB rows x TLD, row-major
+  __shared__ T s_rinv;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const double tau = boost_eps * __longlong_as_double((long long)*amax_bits);
+  const T tau = (T)(boost_eps * __longlong_as_double((long long)*amax_bits));
   unsigned long long nboost = 0;
 
   for (int64_t j0 = 0; j0 < nl; j0 += NB) {
@@ -170,13 +182,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int prow = (int)min((int64_t)(jb + k), nl - j0);
     // (a) panel load
     for (int base = tid; base < NB * PLD; base += NTHREADS * 8) {
-      double v[8];
+      T v[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int idx = base + u * NTHREADS;
         const int c = idx / PLD, r = idx - c * PLD;
         v[u] = (idx < NB * PLD && c < jb && r < prow && r - c <= k && c - r <= k) ? fb[(j0 + c) * ldf + k + r - c]
-                                                                                   : 0.0;
+                                                                                   : (T)0;
       }
 #pragma unroll
       for (int u = 0; u < 8; ++u)
@@ -186,24 +198,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // (b) panel LU
     for (int c = 0; c < jb; ++c) {
       if (tid == 0) {
-        double piv = P[c * PLD + c];
+        T piv = P[c * PLD + c];
         if (isnan(piv)) {
           atomicOr(&status[2], 1ull);
-        } else if (!(fabs(piv) >= tau) || piv == 0.0) {
-          piv = (piv < 0.0) ? -tau : tau;
+        } else if (!(fabs(piv) >= tau) || piv == (T)0) {
+          piv = (piv < (T)0) ? -tau : tau;
           ++nboost;
-          if (piv == 0.0) {
+          if (piv == (T)0) {
             const int64_t gcol = L.rev ? (L.start + nl - 1 - (j0 + c)) : (L.start + j0 + c);
             atomicMin(&status[1], (unsigned long long)(gcol + 1));
           }
           P[c * PLD + c] = piv;
         }
-        const double rinv = 1.0 / piv;
+        const T rinv = (T)1 / piv;
         s_rinv = rinv;
         dinv[j0 + c] = rinv;
       }
       __syncthreads();
-      const double rinv = s_rinv;
+      const T rinv = s_rinv;
       const int rlast = min(c + k, prow - 1);
       const int nr = rlast - c;
       for (int r = c + 1 + tid; r <= rlast; r += NTHREADS) P[c * PLD + r] *= rinv;
@@ -227,12 +239,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int nq = min(CW, ntot - q0);
       __syncthreads();
       for (int base = tid; base < NB * nq; base += NTHREADS * 8) {
-        double v[8];
+        T v[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const int idx = base + u * NTHREADS;
           const int a = idx % NB, qq = idx / NB, q = q0 + qq;
-          double w = 0.0;
+          T w = (T)0;
           if (idx < NB * nq && a < jb) {
             if (q < kc) {
               if (jb + q - a <= k) w = fb[(j0 + jb + q) * ldf + k + a - jb - q];
@@ -245,33 +257,33 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const int idx = base + u * NTHREADS;
-          if (idx < NB * nq) T[(idx % NB) * TLD + idx / NB] = v[u];
+          if (idx < NB * nq) T12[(idx % NB) * TLD + idx / NB] = v[u];
         }
       }
       __syncthreads();
       // TRSM with the unit lower L11 = P[0:jb, 0:jb]: one column per thread
       for (int qq = tid; qq < nq; qq += NTHREADS) {
-        double x[NB];
+        T x[NB];
 #pragma unroll
-        for (int a = 0; a < NB; ++a) x[a] = T[a * TLD + qq];
+        for (int a = 0; a < NB; ++a) x[a] = T12[a * TLD + qq];
 #pragma unroll
         for (int a = 1; a < NB; ++a) {
-          double s = x[a];
+          T s = x[a];
 #pragma unroll
           for (int b = 0; b < a; ++b) s = fma(-P[b * PLD + a], x[b], s);
           x[a] = s;
         }
 #pragma unroll
-        for (int a = 0; a < NB; ++a) T[a * TLD + qq] = x[a];
+        for (int a = 0; a < NB; ++a) T12[a * TLD + qq] = x[a];
       }
       __syncthreads();
       for (int idx = tid; idx < NB * nq; idx += NTHREADS) {
         const int a = idx % NB, qq = idx / NB, q = q0 + qq;
         if (a < jb) {
           if (q < kc) {
-            if (jb + q - a <= k) fb[(j0 + jb + q) * ldf + k + a - jb - q] = T[a * TLD + qq];
+            if (jb + q - a <= k) fb[(j0 + jb + q) * ldf + k + a - jb - q] = T12[a * TLD + qq];
           } else {
-            Z[(int64_t)(q - kc) * nl + j0 + a] = T[a * TLD + qq];
+            Z[(int64_t)(q - kc) * nl + j0 + a] = T12[a * TLD + qq];
           }
         }
       }
@@ -285,11 +297,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const bool anyz = (q0 + min(qq0 + 16, nq) - 1) >= kc;
         int astart = anyz ? (jb + i0 - k) : (jb + max(i0, qa) - k);
         astart = max(astart, 0);
-        double acc[16];
+        T acc[16];
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
           const int qq = qq0 + q, qabs = q0 + qq;
-          double v = 0.0;
+          T v = (T)0;
           if (vi && qq < nq) {
             if (qabs < kc) v = fb[(j0 + jb + qabs) * ldf + k + i - qabs];
             else v = Z[(int64_t)(qabs - kc) * nl + j0 + jb + i];
@@ -297,8 +309,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           acc[q] = v;
         }
         for (int a = astart; a < jb; ++a) {
-          const double l = vi ? P[a * PLD + jb + i] : 0.0;
-          const double *trow = T + a * TLD + qq0;
+          const T l = vi ? P[a * PLD + jb + i] : (T)0;
+          const T *trow = T12 + a * TLD + qq0;
 #pragma unroll
           for (int q = 0; q < 16; ++q) acc[q] = fma(-l, trow[q], acc[q]);
         }
@@ -317,20 +329,29 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (tid == 0 && nboost) atomicAdd(&status[0], nboost);
   // the leaf's spike sweeps, in the same CTA (shared memory reused)
   __syncthreads();
-  sweep_run(sweeps[2 * blockIdx.x], ldf, k, smem);
+  sweep_run<T>(sweeps[2 * blockIdx.x], ldf, k, smem);
   __syncthreads();
-  sweep_run(sweeps[2 * blockIdx.x + 1], ldf, k, smem);
+  sweep_run<T>(sweeps[2 * blockIdx.x + 1], ldf, k, smem);
 }
 
-int launch_factor_nopiv(const LeafDev *leaves, int nleaves, int k, int ldf, double *fb, double *dinv, double *zbuf,
+int launch_factor_nopiv(const LeafDev *leaves, int nleaves, int k, int ldf, void *fb, void *dinv, void *zbuf,
                         const int64_t *zoff, const unsigned long long *amax_bits, double boost_eps,
-                        unsigned long long *status, const SweepDesc *sweeps, void *stream) {
-  size_t smem = sizeof(double) * ((size_t)NB * (NB + k + 1) + (size_t)NB * (CW + 1));
+                        unsigned long long *status, const SweepDesc *sweeps, void *stream, int f32) {
+  const size_t es = f32 ? sizeof(float) : sizeof(double);
+  size_t smem = es * ((size_t)NB * (NB + k + 1) + (size_t)NB * (CW + 1));
   if (smem < SWEEP_SMEM) smem = SWEEP_SMEM;
-  cudaError_t e = cudaFuncSetAttribute(k_factor_nopiv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return (int)e;
-  k_factor_nopiv<<<nleaves, NTHREADS, smem, (cudaStream_t)stream>>>(leaves, k, ldf, fb, dinv, zbuf, zoff, amax_bits,
-                                                                     boost_eps, status, sweeps);
+  cudaError_t e;
+  if (f32) {
+    e = cudaFuncSetAttribute(k_factor_nopiv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    k_factor_nopiv<float><<<nleaves, NTHREADS, smem, (cudaStream_t)stream>>>(
+        leaves, k, ldf, (float *)fb, (float *)dinv, (float *)zbuf, zoff, amax_bits, boost_eps, status, sweeps);
+  } else {
+    e = cudaFuncSetAttribute(k_factor_nopiv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    k_factor_nopiv<double><<<nleaves, NTHREADS, smem, (cudaStream_t)stream>>>(
+        leaves, k, ldf, (double *)fb, (double *)dinv, (double *)zbuf, zoff, amax_bits, boost_eps, status, sweeps);
+  }
   count_launch();
   return (int)cudaGetLastError();
 }
@@ -432,37 +453,46 @@ int launch_factor_piv(const LeafDev *leaves, int nleaves, int k, int ldf, double
 //       lanes <-> rows with shuffles otherwise),
 //   (3) store.
 // Coefficients: LN/UN use column c of the band, UT/LT column r (transposed access).
-__device__ __forceinline__ double coef(int kind, const double *fb, int ldf, int dofs, int64_t r, int64_t c) {
+template <typename T>
+__device__ __forceinline__ T coef(int kind, const T *fb, int ldf, int dofs, int64_t r, int64_t c) {
   if (kind == LN || kind == UN) return fb[c * ldf + dofs + r - c];
   return fb[r * ldf + dofs + c - r];
 }
 
 // acc[q] += sum_j Tw[j*NB] * X(row_j, col_base + q), rows row_j = row_0 + j (stride xstep),
 // for q < C.  Columns past `lastc` are clamped (their accumulators are never stored).
-template <int C>
-__device__ __forceinline__ void window_fma(double *acc, const double *tw, const double *xrow, int64_t xstep,
-                                           int64_t xcs, int col_base, int lastc, int count) {
+template <typename T, int C>
+__device__ __forceinline__ void window_fma(T *acc, const T *tw, const T *xrow, int64_t xstep, int64_t xcs,
+                                           int col_base, int lastc, int count) {
   int64_t coff[C];
 #pragma unroll
   for (int q = 0; q < C; ++q) coff[q] = (int64_t)min(col_base + q, lastc) * xcs;
   for (int j = 0; j < count; ++j) {
-    const double t = tw[j * NB];
+    const T t = tw[j * NB];
 #pragma unroll
     for (int q = 0; q < C; ++q) acc[q] = fma(t, xrow[coff[q]], acc[q]);
     xrow += xstep;
   }
 }
 
-__device__ void sweep_run(const SweepDesc &D, int ldf, int dofs, double *sm) {
+template <typename T>
+__device__ void sweep_run(const SweepDesc &D, int ldf, int dofs, T *sm) {
   if (D.ncols <= 0 || D.r1 <= D.r0) return;
+  // descriptor pointers carry the leaf's storage type T
+  const T *dfb = (const T *)D.fb;
+  const T *ddinv = (const T *)D.dinv;
+  const T *dga = (const T *)D.ga;
+  const T *dgb = (const T *)D.gb;
+  T *dx = (T *)D.x;
+  const T gbs = (T)D.gb_scale;
   const int kind = D.kind, kw = D.kw;
   const bool FWD = (kind == LN || kind == UT);
   const bool UNIT = (kind == LN || kind == LT);
   const int GLD = SCW + 1;
-  double *Tw = sm;                 // WCH x NB   : Tw[j*NB + a] = T(row(a), wrow(j))
-  double *Td = Tw + WCH * NB;      // NB x NB    : Td[a'*NB + a] = T(row(a), row(a'))
-  double *dsm = Td + NB * NB;      // NB
-  double *Gs = dsm + NB;           // NB x GLD
+  T *Tw = sm;                 // WCH x NB   : Tw[j*NB + a] = T(row(a), wrow(j))
+  T *Td = Tw + WCH * NB;      // NB x NB    : Td[a'*NB + a] = T(row(a), row(a'))
+  T *dsm = Td + NB * NB;      // NB
+  T *Gs = dsm + NB;           // NB x GLD
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nwarps = NTHREADS / 32;
 
@@ -498,33 +528,33 @@ __device__ void sweep_run(const SweepDesc &D, int ldf, int dofs, double *sm) {
       }
       __syncthreads();
       {
-        double v[NB * NB / NTHREADS];
+        T v[NB * NB / NTHREADS];
 #pragma unroll
         for (int u = 0; u < NB * NB / NTHREADS; ++u) {
           const int idx = tid + u * NTHREADS;
           const int ap = idx / NB, a = idx - ap * NB;
-          v[u] = (ap < a && a < nbk && a - ap <= kw) ? coef(kind, D.fb, ldf, dofs, row(a), row(ap)) : 0.0;
+          v[u] = (ap < a && a < nbk && a - ap <= kw) ? coef<T>(kind, dfb, ldf, dofs, row(a), row(ap)) : (T)0;
         }
 #pragma unroll
         for (int u = 0; u < NB * NB / NTHREADS; ++u) Td[tid + u * NTHREADS] = v[u];
       }
-      for (int a = tid; a < NB; a += NTHREADS) dsm[a] = (a < nbk) ? (UNIT ? 1.0 : D.dinv[row(a)]) : 0.0;
+      for (int a = tid; a < NB; a += NTHREADS) dsm[a] = (a < nbk) ? (UNIT ? (T)1 : ddinv[row(a)]) : (T)0;
 
-      double acc[16];
+      T acc[16];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+      for (int q = 0; q < 16; ++q) acc[q] = (T)0;
       for (int jc0 = jlo; jc0 < jhi; jc0 += WCH) {
         const int jce = min(jhi, jc0 + WCH);
         __syncthreads();
         const int tot = (jce - jc0) * NB;
         for (int base = tid; base < tot; base += NTHREADS * 8) {
-          double v[8];
+          T v[8];
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
             const int idx = base + u * NTHREADS;
             const int jj = idx / NB, a = idx - jj * NB, j = jc0 + jj;
             v[u] = (idx < tot && a < nbk && (FWD ? (j >= a) : (j <= kw - 1 - a)))
-                       ? coef(kind, D.fb, ldf, dofs, row(a), wrow(j)) : 0.0;
+                       ? coef<T>(kind, dfb, ldf, dofs, row(a), wrow(j)) : (T)0;
           }
 #pragma unroll
           for (int u = 0; u < 8; ++u)
@@ -536,14 +566,14 @@ __device__ void sweep_run(const SweepDesc &D, int ldf, int dofs, double *sm) {
         const int js = jc0 + split * per, je = min(jce, js + per);
         // A predicated-off DFMA still occupies the FP64 pipe, so the accumulation loop is
         // instantiated for the exact column count; edge columns are clamped, not predicated.
-        const double *xw = D.x + wrow(js) * D.x_rs;
+        const T *xw = dx + wrow(js) * D.x_rs;
         const int64_t step = D.x_rs;  // wrow(j+1) = wrow(j) + 1 in both sweep directions
         const int lastc = c0 + cw - 1;
-        if (cpw <= 1) window_fma<1>(acc, Tw + (js - jc0) * NB + lane, xw, step, D.x_cs, col_base, lastc, je - js);
-        else if (cpw <= 2) window_fma<2>(acc, Tw + (js - jc0) * NB + lane, xw, step, D.x_cs, col_base, lastc, je - js);
-        else if (cpw <= 4) window_fma<4>(acc, Tw + (js - jc0) * NB + lane, xw, step, D.x_cs, col_base, lastc, je - js);
-        else if (cpw <= 8) window_fma<8>(acc, Tw + (js - jc0) * NB + lane, xw, step, D.x_cs, col_base, lastc, je - js);
-        else window_fma<16>(acc, Tw + (js - jc0) * NB + lane, xw, step, D.x_cs, col_base, lastc, je - js);
+        if (cpw <= 1) window_fma<T, 1>(acc, Tw + (js - jc0) * NB + lane, xw, step, D.x_cs, col_base, lastc, je - js);
+        else if (cpw <= 2) window_fma<T, 2>(acc, Tw + (js - jc0) * NB + lane, xw, step, D.x_cs, col_base, lastc, je - js);
+        else if (cpw <= 4) window_fma<T, 4>(acc, Tw + (js - jc0) * NB + lane, xw, step, D.x_cs, col_base, lastc, je - js);
+        else if (cpw <= 8) window_fma<T, 8>(acc, Tw + (js - jc0) * NB + lane, xw, step, D.x_cs, col_base, lastc, je - js);
+        else window_fma<T, 16>(acc, Tw + (js - jc0) * NB + lane, xw, step, D.x_cs, col_base, lastc, je - js);
       }
       __syncthreads();
       for (int s = 0; s < nsplit; ++s) {
@@ -554,10 +584,10 @@ __device__ void sweep_run(const SweepDesc &D, int ldf, int dofs, double *sm) {
             for (int q = 0; q < 16; ++q) {
               const int col = col_base + q;
               if (q < cpw && col < c0 + cw) {
-                double g;
+                T g;
                 if (s == 0) {
-                  g = D.ga[r * D.ga_rs + (int64_t)col * D.ga_cs];
-                  if (D.gb) g = fma(D.gb_scale, D.gb[r * D.gb_rs + (int64_t)col * D.gb_cs], g);
+                  g = dga[r * D.ga_rs + (int64_t)col * D.ga_cs];
+                  if (dgb) g = fma(gbs, dgb[r * D.gb_rs + (int64_t)col * D.gb_cs], g);
                 } else {
                   g = Gs[lane * GLD + (col - c0)];
                 }
@@ -568,7 +598,7 @@ __device__ void sweep_run(const SweepDesc &D, int ldf, int dofs, double *sm) {
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
               const int col = col_base + q;
-              if (q < cpw && col < c0 + cw) Gs[lane * GLD + (col - c0)] = 0.0;
+              if (q < cpw && col < c0 + cw) Gs[lane * GLD + (col - c0)] = (T)0;
             }
           }
         }
@@ -577,10 +607,10 @@ __device__ void sweep_run(const SweepDesc &D, int ldf, int dofs, double *sm) {
       // in-block triangular solve
       if (cw >= 64) {
         for (int cc = tid; cc < cw; cc += NTHREADS) {
-          double xv[NB];
+          T xv[NB];
 #pragma unroll
           for (int a = 0; a < NB; ++a) {
-            double s = Gs[a * GLD + cc];
+            T s = Gs[a * GLD + cc];
 #pragma unroll
             for (int ap = 0; ap < a; ++ap) s = fma(-Td[ap * NB + a], xv[ap], s);
             xv[a] = s * dsm[a];
@@ -590,11 +620,11 @@ __device__ void sweep_run(const SweepDesc &D, int ldf, int dofs, double *sm) {
         }
       } else {
         for (int cc = warp; cc < cw; cc += nwarps) {
-          double s = Gs[lane * GLD + cc];
-          double xf = 0.0;
+          T s = Gs[lane * GLD + cc];
+          T xf = (T)0;
 #pragma unroll
           for (int ap = 0; ap < NB; ++ap) {
-            const double xa = __shfl_sync(FULLMASK, s, ap) * dsm[ap];
+            const T xa = __shfl_sync(FULLMASK, s, ap) * dsm[ap];
             if (lane == ap) xf = xa;
             if (lane > ap) s = fma(-Td[ap * NB + lane], xa, s);
           }
@@ -605,12 +635,12 @@ __device__ void sweep_run(const SweepDesc &D, int ldf, int dofs, double *sm) {
       if (D.x_cs == 1) {  // row-major X: columns contiguous
         for (int idx = tid; idx < nbk * cw; idx += NTHREADS) {
           const int cc = idx % cw, a = idx / cw;
-          D.x[row(a) * D.x_rs + (c0 + cc)] = Gs[a * GLD + cc];
+          dx[row(a) * D.x_rs + (c0 + cc)] = Gs[a * GLD + cc];
         }
       } else {
         for (int idx = tid; idx < nbk * cw; idx += NTHREADS) {
           const int a = idx % nbk, cc = idx / nbk;
-          D.x[row(a) * D.x_rs + (int64_t)(c0 + cc) * D.x_cs] = Gs[a * GLD + cc];
+          dx[row(a) * D.x_rs + (int64_t)(c0 + cc) * D.x_cs] = Gs[a * GLD + cc];
         }
       }
     }
@@ -618,19 +648,27 @@ __device__ void sweep_run(const SweepDesc &D, int ldf, int dofs, double *sm) {
   }
 }
 
+template <typename T>
 __global__ void __launch_bounds__(NTHREADS, 1) k_sweeps(const SweepDesc *descs, int per_cta, int ldf, int dofs) {
-  extern __shared__ double sm[];
+  extern __shared__ __align__(16) unsigned char sm_raw[];
   for (int s = 0; s < per_cta; ++s) {
-    sweep_run(descs[(int64_t)blockIdx.x * per_cta + s], ldf, dofs, sm);
+    sweep_run<T>(descs[(int64_t)blockIdx.x * per_cta + s], ldf, dofs, (T *)sm_raw);
     __syncthreads();
   }
 }
 
-int launch_sweeps(const SweepDesc *descs, int ncta, int per_cta, int ldf, int dofs, void *stream) {
+int launch_sweeps(const SweepDesc *descs, int ncta, int per_cta, int ldf, int dofs, void *stream, int f32) {
   if (ncta <= 0 || per_cta <= 0) return 0;
-  cudaError_t e = cudaFuncSetAttribute(k_sweeps, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_SMEM);
-  if (e != cudaSuccess) return (int)e;
-  k_sweeps<<<ncta, NTHREADS, SWEEP_SMEM, (cudaStream_t)stream>>>(descs, per_cta, ldf, dofs);
+  cudaError_t e;
+  if (f32) {
+    e = cudaFuncSetAttribute(k_sweeps<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_SMEM);
+    if (e != cudaSuccess) return (int)e;
+    k_sweeps<float><<<ncta, NTHREADS, SWEEP_SMEM, (cudaStream_t)stream>>>(descs, per_cta, ldf, dofs);
+  } else {
+    e = cudaFuncSetAttribute(k_sweeps<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_SMEM);
+    if (e != cudaSuccess) return (int)e;
+    k_sweeps<double><<<ncta, NTHREADS, SWEEP_SMEM, (cudaStream_t)stream>>>(descs, per_cta, ldf, dofs);
+  }
   count_launch();
   return (int)cudaGetLastError();
 }
@@ -697,12 +735,13 @@ int launch_piv_sweep(int kind, const SweepDesc *descs, int ndesc, int k, int ldf
 // Spike tips of each leaf in the global frame from the swept Z:
 //   forward leaf : W = Z_top, V = Z_bot;   reversed leaf: V = Q Z_top, W = Q Z_bot.
 // spk layout: [V/W][leaf][top/bottom] k x k row-major (level 0).
-__global__ void k_tips0(const LeafDev *leaves, int nleaves, int k, const double *zbuf, const int64_t *zoff,
+template <typename T>
+__global__ void k_tips0(const LeafDev *leaves, int nleaves, int k, const T *zbuf, const int64_t *zoff,
                         double *spk) {
   const int i = blockIdx.x;
   const LeafDev L = leaves[i];
   const int64_t nl = L.len;
-  const double *Z = zbuf + zoff[i];
+  const T *Z = zbuf + zoff[i];
   const int64_t kk = (int64_t)k * k;
   const bool mid = L.top_nbr && L.bot_nbr;
   for (int64_t idx = threadIdx.x; idx < kk; idx += blockDim.x) {
@@ -710,7 +749,7 @@ __global__ void k_tips0(const LeafDev *leaves, int nleaves, int k, const double 
     // local rows of global top/bottom tip row j
     const int64_t lt = L.rev ? (nl - 1 - j) : j;             // global top row j
     const int64_t lb = L.rev ? (k - 1 - j) : (nl - k + j);   // global bottom row j
-    const double *Ztop = Z, *Zbot = Z + (int64_t)k * nl;
+    const T *Ztop = Z, *Zbot = Z + (int64_t)k * nl;
     // spike coupled through the local top rows is W (fwd) / V (rev); through the bottom: V (fwd) / W (rev)
     const int s_top = L.rev ? 0 : 1, s_bot = L.rev ? 1 : 0;
     if (mid) {
@@ -726,9 +765,12 @@ __global__ void k_tips0(const LeafDev *leaves, int nleaves, int k, const double 
   }
 }
 
-int launch_tips0(const LeafDev *leaves, int nleaves, int k, const double *zbuf, const int64_t *zoff, double *spk,
-                 void *stream) {
-  k_tips0<<<nleaves, 256, 0, (cudaStream_t)stream>>>(leaves, nleaves, k, zbuf, zoff, spk);
+int launch_tips0(const LeafDev *leaves, int nleaves, int k, const void *zbuf, const int64_t *zoff, double *spk,
+                 void *stream, int f32) {
+  if (f32)
+    k_tips0<float><<<nleaves, 256, 0, (cudaStream_t)stream>>>(leaves, nleaves, k, (const float *)zbuf, zoff, spk);
+  else
+    k_tips0<double><<<nleaves, 256, 0, (cudaStream_t)stream>>>(leaves, nleaves, k, (const double *)zbuf, zoff, spk);
   count_launch();
   return (int)cudaGetLastError();
 }
