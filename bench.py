@@ -202,6 +202,114 @@ def load_traffic():
     return d.get("dram_bytes_per_launch_full"), d
 
 
+def serving_leg(dev, requests, streams, max_batch, passes=2, seed=None):
+    """Many-matrix serving workload (inputs.SERVING) through the native serving engine.
+
+    The catalogue bands live in device memory (the caller's; the budget covers the
+    factorizations, their scratch and the workspaces).  Right-hand sides come from
+    pinned host memory and results go back to pinned host memory: every request's
+    latency is submit -> X in host memory.  Arrivals are open-loop (Poisson, replayed
+    on the host clock).  The trace runs `passes` times on the same server: the first
+    pass starts with nothing factored, later passes find the most popular matrices
+    resident (the budget holds about three quarters of the working set).
+    """
+    import collections
+    import torch
+    from paper_1811_03559_gb300 import inputs, serve, spike
+    cfg = dict(inputs.SERVING)
+    cfg["requests"] = requests
+    if seed is not None:
+        cfg["seed"] = seed
+    ns, ks, _ = inputs.serving_catalogue(cfg)
+    arrivals, mids, nrhs, trans, mixed = inputs.serving_trace(cfg)
+    used = sorted(set(int(x) for x in mids))
+    t_gen = time.perf_counter()
+    bands = {i: inputs.make_band_torch(int(ns[i]), int(ks[i]), int(ks[i]), 7919 * cfg["seed"] + i, cfg["dd"], dev)
+             for i in used}
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    nmax = int(ns.max())
+    fbuf = torch.empty(cfg["nrhs_max"] * nmax, dtype=torch.float64).uniform_(-1.0, 1.0).pin_memory().numpy()
+    cap = 1 << 29  # 4 GB of pinned result space, reused as a ring
+    arena = torch.empty(cap, dtype=torch.float64).pin_memory().numpy()
+    budget = int(cfg["budget_gb"] * 1e9)
+    S = serve.Server(budget, streams=streams, max_batch_rhs=max_batch, nrhs_hint=16)
+    for i in used:
+        S.add_matrix(i, bands[i], int(ks[i]), int(ks[i]))
+    out = {"workload": "%d requests, Poisson %g/s, %d matrices (n log-uniform [%d, %d], k uniform {4..128 step 4}, "
+                       "DD %g), Zipf(%g) popularity, nrhs U[1,%d], %d%% T, %d%% mixed, %g GB budget"
+                       % (requests, cfg["rate"], cfg["matrices"], cfg["n_lo"], cfg["n_hi"], cfg["dd"], cfg["zipf"],
+                          cfg["nrhs_max"], round(100 * cfg["trans_t"]), round(100 * cfg["mixed"]), cfg["budget_gb"]),
+           "matrices_used": len(used), "catalogue_gb": sum(8.0 * ns[i] * (2 * ks[i] + 1) for i in used) / 1e9,
+           "streams": streams, "max_batch_rhs": max_batch, "catalogue_gen_s": t_gen,
+           "data": "synthetic (torch generator on the device for the bands, seeded per matrix)", "passes": []}
+    launches0 = spike.kernel_launches()
+    prev = S.stats()
+    for ps in range(passes):
+        outstanding = collections.deque()
+        head = 0
+        lat0 = len(S.latencies())
+        t0 = time.perf_counter()
+        lag = 0.0
+        for i in range(requests):
+            target = t0 + arrivals[i]
+            now = time.perf_counter()
+            while now < target:
+                if target - now > 5e-4:
+                    time.sleep(target - now - 3e-4)
+                now = time.perf_counter()
+            lag = max(lag, now - target)
+            n, m = int(ns[mids[i]]), int(nrhs[i])
+            sz = n * m
+            if head + sz > cap:
+                head = 0
+            lo, hi = head, head + sz
+            # regions are handed out in ring order, so the oldest outstanding ones are the
+            # first that the new region can overlap
+            while outstanding and not (outstanding[0][2] <= lo or outstanding[0][1] >= hi):
+                S.wait(outstanding.popleft()[0])
+            X = arena[lo:hi].reshape(m, n)
+            rid, _ = S.submit(int(mids[i]), fbuf[:sz].reshape(m, n), X, trans=str(trans[i]), mixed=bool(mixed[i]))
+            outstanding.append((rid, lo, hi))
+            head = hi
+        S.drain()
+        wall = time.perf_counter() - t0
+        st = S.stats()
+        lat = np.sort(S.latencies()[lat0:])
+        rank = lambda q: float(lat[max(1, int(np.ceil(q * len(lat)))) - 1])
+        done = st["completed"] - prev["completed"]
+        rhs = st["rhs"] - prev["rhs"]
+        out["passes"].append({
+            "pass": ps, "p50_ms": rank(0.5), "p99_ms": rank(0.99), "max_ms": float(lat[-1]),
+            "mean_ms": float(lat.mean()), "solves_per_s": done / wall, "rhs_per_s": rhs / wall,
+            "offered_per_s": requests / arrivals[-1], "wall_s": wall, "failed": st["failed"] - prev["failed"],
+            "batches": st["batches"] - prev["batches"], "mean_requests_per_batch": done / max(1, st["batches"] - prev["batches"]),
+            "factorizations": st["factorizations"] - prev["factorizations"],
+            "evictions": st["evictions"] - prev["evictions"], "peak_gb": st["peak_bytes"] / 1e9,
+            "max_submit_lag_ms": 1e3 * lag})
+        prev = st
+    out["gpu_launches"] = int(spike.kernel_launches() - launches0)
+    # accuracy of served results: one request per (trans, precision) on the largest used matrix
+    big = max(used, key=lambda i: ns[i] * ks[i])
+    n, k = int(ns[big]), int(ks[big])
+    berr = {}
+    for tr in "NT":
+        for mx in (False, True):
+            F = np.ascontiguousarray(fbuf[: 4 * n].reshape(4, n))
+            rid, X = S.submit(big, F, trans=tr, mixed=mx)
+            S.wait(rid)
+            be = spike.backward_error(bands[big], k, k, torch.from_numpy(X).to(dev), torch.from_numpy(F).to(dev), tr)
+            berr["%s_%s" % (tr, "mixed" if mx else "fp64")] = float(be.max())
+    out["backward_error_max"] = max(berr.values())
+    out["backward_error"] = berr
+    out["check_matrix"] = {"n": n, "k": k}
+    S.close()
+    w = out["passes"][-1]
+    out.update({"p50_ms": w["p50_ms"], "p99_ms": w["p99_ms"], "solves_per_s": w["solves_per_s"],
+                "rhs_per_s": w["rhs_per_s"]})
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -218,6 +326,11 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer (e2e) leg, e.g. under a profiler")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision variant")
+    ap.add_argument("--no-serve", action="store_true", help="skip the many-matrix serving leg")
+    ap.add_argument("--serve-requests", type=int, default=10_000)
+    ap.add_argument("--serve-streams", type=int, default=8)
+    ap.add_argument("--serve-batch", type=int, default=64)
+    ap.add_argument("--serve-passes", type=int, default=2)
     args = ap.parse_args()
     n, k, p, m, dd, seed = args.n, args.k, args.p, args.nrhs, args.dd, 1
     workload = "n=%d kl=ku=%d p=%d nrhs=%d DD=%g: spike_factor + spike_solve N + spike_solve T" % (n, k, p, m, dd)
@@ -380,6 +493,10 @@ def main():
             e2e_s += dt
     e2e_step_s = e2e_s / args.e2e_steps if args.e2e_steps > 0 else float("nan")
 
+    serving = None
+    if not args.no_serve and rank == 0:
+        serving = serving_leg(dev, args.serve_requests, args.serve_streams, args.serve_batch, args.serve_passes)
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -414,6 +531,7 @@ def main():
                 "d2h_bytes_per_step": int(2 * 8 * n * m), "steps": args.e2e_steps,
                 "ms_per_step": e2e_step_s * 1e3},
         "variants": {"mixed_fp32_fp64_refinement": mixed},
+        "serving": serving,
         "gpu_launches": int(launches),
         "clocks": clocks,
     }

@@ -64,6 +64,14 @@ extern "C" {
  * spike_get_info reports the steps and the final backward error).  Non-pivoting
  * only (SPIKE_ENOTSUP with pivot = 1). */
 #define SPIKE_FLAG_MIXED 4
+/* Batch-invariant solves: every right-hand side of a solve gets the same bits whatever
+ * the number of columns solved with it and its position among them.  The window
+ * products of the triangular sweeps are then summed over a fixed set of sub-ranges
+ * instead of a split that depends on the column count (a few percent slower on
+ * wide solves); everything else on the solve path is column-independent already, and
+ * mixed-precision refinement stops per column.  Lets independent requests be merged
+ * into one solve without changing any result (the serving engine sets it). */
+#define SPIKE_FLAG_BATCH_INVARIANT 8
 #define SPIKE_MIXED_TOL 1e-14
 #define SPIKE_MIXED_MAX_STEPS 10
 
@@ -162,6 +170,28 @@ int spike_solve(spike_handle h, double *F, int nrhs, char trans);
 
 /* As spike_solve with an explicit leading dimension ldf >= n. */
 int spike_solve_ex(spike_handle h, double *F, int64_t ldf, int nrhs, char trans);
+
+/* Device bytes that a factorization of (n, kl, ku, p, pivot, opt) will use, without
+ * touching a GPU.  *resident: held by the handle until spike_free (block factors,
+ * spike tips, reduced-system LUs and, with SPIKE_FLAG_MIXED, the FP64 band copy).
+ * *transient: scratch that spike_factor allocates and frees inside the call (the
+ * spike right-hand sides, plus a staged copy of the band when host_band != 0).
+ * Neither counts the handle's descriptor buffer (a few hundred KB at most) nor solve
+ * scratch (see spike_solve_ws).  Returns 0, -i for an invalid argument i, or
+ * SPIKE_ENOTSUP. */
+int spike_factor_bytes(int64_t n, int kl, int ku, int p, int pivot, const spike_options *opt, int host_band,
+                       int64_t *resident, int64_t *transient);
+
+/* Device scratch bytes that spike_solve_ws needs for nrhs columns of the handle
+ * (host_f != 0: F will be host memory and is staged in the workspace too). */
+int spike_solve_workspace(spike_handle h, int nrhs, char trans, int host_f, int64_t *bytes);
+
+/* spike_solve_ex on caller-provided device scratch: workspace (ws_bytes >= the
+ * figure of spike_solve_workspace, else -7).  The handle then keeps no solve
+ * scratch of its own, so many resident handles can share a few workspaces, one per
+ * stream.  The workspace must not be reused until the solve's GPU work on the
+ * handle's stream has completed.  Results are those of spike_solve_ex. */
+int spike_solve_ws(spike_handle h, double *F, int64_t ldf, int nrhs, char trans, void *workspace, int64_t ws_bytes);
 
 /* Set the cudaStream_t used by the handle (NULL = legacy default stream). */
 int spike_set_stream(spike_handle h, void *stream);

@@ -134,6 +134,8 @@ struct spike_ctx {
   char *fbc = nullptr, *dinvc = nullptr;  // leaf factors / reciprocals, element size es
   double *couple = nullptr, *spk = nullptr, *mlu = nullptr, *ident = nullptr;
   int f32 = 0;                             // SPIKE_FLAG_MIXED: FP32 leaf factors and sweeps
+  int invariant = 0;                       // SPIKE_FLAG_BATCH_INVARIANT
+  int in_solve = 0;                        // descriptors being built belong to a solve
   size_t es = sizeof(double);
   double *band64 = nullptr;                // mixed: FP64 copy of the band for the refinement residuals
   int64_t ldab64 = 0;
@@ -259,6 +261,7 @@ static SweepDesc sdesc(spike_ctx *c, int i, int kind, int r0, int r1, int ncols,
   d.ncols = ncols;
   d.kind = kind;
   d.kw = (kind == UN || kind == UT) ? c->dofs : c->k;  // U has 2k superdiagonals when pivoting
+  d.fixed_split = (c->invariant && c->in_solve) ? 1 : 0;
   d.ga = g.p;
   d.ga_rs = g.rs;
   d.ga_cs = g.cs;
@@ -355,6 +358,85 @@ struct Pipeline {
 // ============================================================== factor
 static int factor_reduced_level(spike_ctx *c, int lv, char *tmp, size_t tmp_bytes);
 
+// Device memory of one factorization: the persistent block (owned by the handle) and
+// the scratch that spike_factor uses and frees before returning.  Offsets are 256-byte
+// aligned carvings of one allocation each.
+struct FactorLayout {
+  int k = 0, dofs = 0, ldf = 0;
+  int64_t zacc = 0, maxlen = 0, nmerge = 0;
+  size_t o_fb = 0, o_dinv = 0, o_b64 = 0, o_ipiv = 0, o_cpl = 0, o_spk = 0, o_mlu = 0, o_mpiv = 0, o_id = 0,
+         o_st = 0, mem = 0;
+  size_t s_band = 0, s_z = 0, s_zoff = 0, s_leaf = 0, s_tmp = 0, tmp_bytes = 0, scr = 0;
+  std::vector<int64_t> zoff;
+};
+
+static void factor_layout(const Plan &pl, int pivot, int f32, int64_t ldab, bool band_dev, FactorLayout &L) {
+  const int64_t n = pl.n;
+  const int k = pl.k, nlv = pl.nleaves;
+  const size_t es = f32 ? sizeof(float) : sizeof(double);
+  const int64_t kk = (int64_t)k * k;
+  L.k = k;
+  L.dofs = pivot ? 2 * k : k;
+  L.ldf = (L.dofs + k + 1 + 1) & ~1;
+  L.zoff.assign(nlv, 0);
+  L.zacc = 0;
+  L.maxlen = 0;
+  for (int i = 0; i < nlv; ++i) {
+    L.zoff[i] = L.zacc;
+    L.zacc += pl.leaves[i].len * 2 * (int64_t)k;
+    L.maxlen = std::max(L.maxlen, pl.leaves[i].len);
+  }
+  L.nmerge = 0;
+  size_t maxm = 1;
+  for (auto &lv : pl.levels) {
+    L.nmerge += (int64_t)lv.size();
+    maxm = std::max(maxm, lv.size());
+  }
+  const int nspk = std::max((int)pl.levels.size(), 1);
+  size_t off = 0;
+  auto carve = [&](size_t bytes) {
+    size_t o = off;
+    off = (off + bytes + 255) & ~size_t(255);
+    return o;
+  };
+  L.o_fb = carve(es * (size_t)n * L.ldf);
+  L.o_dinv = carve(es * (size_t)n);
+  L.o_b64 = f32 ? carve(sizeof(double) * (size_t)n * ldab) : 0;
+  L.o_ipiv = pivot ? carve(sizeof(int) * (size_t)n) : 0;
+  L.o_cpl = carve(sizeof(double) * (size_t)nlv * 2 * kk);
+  L.o_spk = carve(sizeof(double) * (size_t)nspk * 2 * nlv * 2 * kk);
+  L.o_mlu = carve(sizeof(double) * (size_t)std::max<int64_t>(L.nmerge, 1) * 4 * kk);
+  L.o_mpiv = carve(sizeof(int) * (size_t)std::max<int64_t>(L.nmerge, 1) * 2 * k);
+  L.o_id = carve(sizeof(double) * (size_t)kk);
+  L.o_st = carve(sizeof(unsigned long long) * 8);
+  L.mem = off;
+  off = 0;
+  L.s_band = band_dev ? 0 : carve(sizeof(double) * (size_t)n * ldab);
+  L.s_z = carve(es * (size_t)L.zacc);
+  L.s_zoff = carve(sizeof(int64_t) * (size_t)nlv);
+  L.s_leaf = carve(sizeof(LeafDev) * (size_t)nlv);
+  L.tmp_bytes = sizeof(double) * maxm * 5 * kk;
+  L.s_tmp = carve(L.tmp_bytes);
+  L.scr = off;
+}
+
+extern "C" int spike_factor_bytes(int64_t n, int kl, int ku, int p, int pivot, const spike_options *opt,
+                                  int host_band, int64_t *resident, int64_t *transient) {
+  if (!resident) return -8;
+  if (!transient) return -9;
+  if (pivot != 0 && pivot != 1) return -5;
+  Plan pl;
+  const int rc = make_plan(n, kl, ku, p, opt ? opt->K : 0.0, opt ? opt->nrhs_hint : 0, opt ? opt->flags : 0, pl);
+  if (rc != 0) return rc;
+  const int f32 = (opt && (opt->flags & SPIKE_FLAG_MIXED)) ? 1 : 0;
+  if (f32 && pivot) return SPIKE_ENOTSUP;
+  FactorLayout L;
+  factor_layout(pl, pivot, f32, (int64_t)kl + ku + 1, host_band == 0, L);
+  *resident = (int64_t)L.mem;
+  *transient = (int64_t)L.scr;
+  return 0;
+}
+
 extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int kl, int ku, int p, int pivot,
                                const spike_options *opt, spike_handle *out) {
   if (!out) return -9;
@@ -381,12 +463,11 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
   c->stream = opt ? (cudaStream_t)opt->stream : nullptr;
   c->k = pl.k;
   c->pivot = pivot;
-  c->dofs = pivot ? 2 * pl.k : pl.k;
-  c->ldf = (c->dofs + pl.k + 1 + 1) & ~1;
   c->nleaves = pl.nleaves;
   c->NL = (int)pl.levels.size();
   c->timing = opt && (opt->flags & SPIKE_FLAG_TIMING);
   c->f32 = (opt && (opt->flags & SPIKE_FLAG_MIXED)) ? 1 : 0;
+  c->invariant = (opt && (opt->flags & SPIKE_FLAG_BATCH_INVARIANT)) ? 1 : 0;
   c->es = c->f32 ? sizeof(float) : sizeof(double);
   if (c->f32 && pivot) {
     delete c;
@@ -406,10 +487,15 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
     return code;
   };
 
+  const bool band_dev = is_device_ptr(band);
+  FactorLayout FL;
+  factor_layout(pl, pivot, c->f32, ldab, band_dev, FL);
+  c->dofs = FL.dofs;
+  c->ldf = FL.ldf;
+  const std::vector<int64_t> &zoff = FL.zoff;
+  const int64_t zacc = FL.zacc, maxlen = FL.maxlen;
   // leaves
   c->hl.resize(nlv);
-  std::vector<int64_t> zoff(nlv);
-  int64_t zacc = 0, maxlen = 0;
   for (int i = 0; i < nlv; ++i) {
     const Leaf &L = pl.leaves[i];
     LeafDev d;
@@ -420,9 +506,6 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
     d.bot_nbr = L.rev ? L.has_prev : L.has_next;
     d.pad = 0;
     c->hl[i] = d;
-    zoff[i] = zacc;
-    zacc += L.len * 2 * (int64_t)k;
-    maxlen = std::max(maxlen, L.len);
   }
   int64_t nmerge = 0;
   c->merge_off.resize(c->NL + 1);
@@ -434,25 +517,11 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
   c->total_merges = (int)nmerge;
   c->schur.assign(c->NL, {});
 
-  // persistent memory layout
+  // persistent memory (layout in factor_layout)
   const int nspk = std::max(c->NL, 1);
-  size_t off = 0;
-  auto carve = [&](size_t bytes) {
-    size_t o = off;
-    off = (off + bytes + 255) & ~size_t(255);
-    return o;
-  };
-  const size_t o_fb = carve(c->es * (size_t)n * c->ldf);
-  const size_t o_dinv = carve(c->es * (size_t)n);
-  const size_t o_b64 = c->f32 ? carve(sizeof(double) * (size_t)n * ldab) : 0;
-  const size_t o_ipiv = pivot ? carve(sizeof(int) * (size_t)n) : 0;
-  const size_t o_cpl = carve(sizeof(double) * (size_t)nlv * 2 * kk);
-  const size_t o_spk = carve(sizeof(double) * (size_t)nspk * 2 * nlv * 2 * kk);
-  const size_t o_mlu = carve(sizeof(double) * (size_t)std::max<int64_t>(nmerge, 1) * 4 * kk);
-  const size_t o_mpiv = carve(sizeof(int) * (size_t)std::max<int64_t>(nmerge, 1) * 2 * k);
-  const size_t o_id = carve(sizeof(double) * (size_t)kk);
-  const size_t o_st = carve(sizeof(unsigned long long) * 8);
-  c->mem_bytes = off;
+  const size_t o_fb = FL.o_fb, o_dinv = FL.o_dinv, o_b64 = FL.o_b64, o_ipiv = FL.o_ipiv, o_cpl = FL.o_cpl,
+               o_spk = FL.o_spk, o_mlu = FL.o_mlu, o_mpiv = FL.o_mpiv, o_id = FL.o_id, o_st = FL.o_st;
+  c->mem_bytes = FL.mem;
   {
     cudaError_t e = cudaMallocAsync((void **)&c->mem, c->mem_bytes, s);
     if (e != cudaSuccess) {
@@ -475,22 +544,9 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
   c->ident = (double *)(c->mem + o_id);
   c->status = (unsigned long long *)(c->mem + o_st);
 
-  // factor-time scratch: staged band (host input), Z, per-merge temporaries, arg buffer
-  const bool band_dev = is_device_ptr(band);
-  size_t soff = 0;
-  auto scarve = [&](size_t bytes) {
-    size_t o = soff;
-    soff = (soff + bytes + 255) & ~size_t(255);
-    return o;
-  };
-  const size_t s_band = band_dev ? 0 : scarve(sizeof(double) * (size_t)n * ldab);
-  const size_t s_z = scarve(c->es * (size_t)zacc);
-  const size_t s_zoff = scarve(sizeof(int64_t) * (size_t)nlv);
-  const size_t s_leaf = scarve(sizeof(LeafDev) * (size_t)nlv);
-  size_t maxm = 1;
-  for (auto &lvv : pl.levels) maxm = std::max(maxm, lvv.size());
-  const size_t s_tmp = scarve(sizeof(double) * maxm * 5 * kk);
-  const size_t tmp_bytes = sizeof(double) * maxm * 5 * kk;
+  // factor-time scratch: staged band (host input), Z, per-merge temporaries
+  const size_t s_band = FL.s_band, s_z = FL.s_z, s_zoff = FL.s_zoff, s_leaf = FL.s_leaf, s_tmp = FL.s_tmp;
+  const size_t tmp_bytes = FL.tmp_bytes, soff = FL.scr;
   char *fscr = nullptr;
   {
     cudaError_t e = cudaMallocAsync((void **)&fscr, soff, s);
@@ -780,7 +836,14 @@ struct SolveBufs {
 // Record the SPIKE solve of op(A) X = W (Sec. 2.1-2.3 for N, Sec. 4 for T) on the
 // row-major work array W, in place.  f32: W and H are FP32 and the leaf sweeps run
 // in FP32 (mixed-precision handles); the reduced system is always FP64.
+static void build_solve_body(spike_ctx *c, Pipeline &pp, const SolveBufs &B, int m, int tr, bool marks);
 static void build_solve(spike_ctx *c, Pipeline &pp, const SolveBufs &B, int m, int tr, bool marks) {
+  c->in_solve = 1;
+  build_solve_body(c, pp, B, m, tr, marks);
+  c->in_solve = 0;
+}
+
+static void build_solve_body(spike_ctx *c, Pipeline &pp, const SolveBufs &B, int m, int tr, bool marks) {
   const int64_t n = c->pl.n;
   const int k = c->k, nlv = c->nleaves;
   const int64_t kk = (int64_t)k * k, km = (int64_t)k * m;
@@ -1049,9 +1112,14 @@ static void build_solve(spike_ctx *c, Pipeline &pp, const SolveBufs &B, int m, i
   }
 }
 
-extern "C" int spike_solve_ex(spike_handle h, double *F, int64_t ldf, int nrhs, char trans) {
+// The solve.  Scratch comes from `ws` (ws_bytes) when given, else from the handle's own
+// buffer (grown on demand).  With need != nullptr only the scratch size is computed
+// (F may then be null; host_f says whether F would be host memory).
+static int solve_impl(spike_handle h, double *F, int64_t ldf, int nrhs, char trans, char *ws, int64_t ws_bytes,
+                      int64_t *need, bool host_f) {
+  if (need) *need = 0;
   if (!valid(h)) return SPIKE_EHANDLE;
-  if (!F) return -2;
+  if (!F && !need) return -2;
   spike_ctx *c = h;
   const int64_t n = c->pl.n;
   if (ldf < n) return -3;
@@ -1068,7 +1136,7 @@ extern "C" int spike_solve_ex(spike_handle h, double *F, int64_t ldf, int nrhs, 
   // Work layout: the sweeps run on a ROW-major copy W of F (row r holds the m
   // right-hand-side entries contiguously), so a block row and its window rows
   // touch a few contiguous lines instead of m lines n*8 bytes apart.
-  const bool fdev = is_device_ptr(F);
+  const bool fdev = need ? !host_f : is_device_ptr(F);
   const bool mixed = c->f32 != 0;
   size_t off = 0;
   auto carve = [&](size_t bytes) {
@@ -1090,21 +1158,33 @@ extern "C" int spike_solve_ex(spike_handle h, double *F, int64_t ldf, int nrhs, 
   const size_t o_x = mixed ? carve(nm8) : 0;
   const size_t o_r = mixed ? carve(nm8) : 0;
   const size_t o_nrm = mixed ? carve(sizeof(unsigned long long) * (1 + 2 * (size_t)m)) : 0;
-  SP_TRY(ensure(&c->scr, &c->scr_bytes, off, s));
+  const size_t o_act = mixed ? carve(sizeof(int) * (size_t)m) : 0;
+  if (need) {
+    *need = (int64_t)off;
+    return 0;
+  }
+  char *base;
+  if (ws) {
+    if (ws_bytes < (int64_t)off) return -7;
+    base = ws;
+  } else {
+    SP_TRY(ensure(&c->scr, &c->scr_bytes, off, s));
+    base = c->scr;
+  }
   double *Fd = F;
   int64_t ld = ldf;
   if (!fdev) {
-    Fd = (double *)(c->scr + o_f);
+    Fd = (double *)(base + o_f);
     ld = n;
     SP_CUDA(cudaMemcpy2DAsync(Fd, sizeof(double) * n, F, sizeof(double) * ldf, sizeof(double) * n, m,
                               cudaMemcpyHostToDevice, s));
   }
   SolveBufs B;
-  B.W = (m > 1 || mixed) ? (void *)(c->scr + o_w) : (void *)Fd;  // FP64, m == 1: column-major == row-major
-  B.H = c->scr + o_h;
-  B.Y = (double *)(c->scr + o_y);
-  B.TM = (double *)(c->scr + o_t);
-  B.PP = (double *)(c->scr + o_p);
+  B.W = (m > 1 || mixed) ? (void *)(base + o_w) : (void *)Fd;  // FP64, m == 1: column-major == row-major
+  B.H = base + o_h;
+  B.Y = (double *)(base + o_y);
+  B.TM = (double *)(base + o_t);
+  B.PP = (double *)(base + o_p);
   cudaEvent_t *evs = tr ? c->tev : c->nev;
 
   if (!mixed) {
@@ -1132,9 +1212,14 @@ extern "C" int spike_solve_ex(spike_handle h, double *F, int64_t ldf, int nrhs, 
     SP_TRY(pp.run(c));
     if (c->timing) (tr ? c->tdone : c->ndone) = true;
   } else {
-    // FP64 iterative refinement around the FP32 SPIKE solve
-    double *F0 = (double *)(c->scr + o_f0), *X = (double *)(c->scr + o_x), *R = (double *)(c->scr + o_r);
-    unsigned long long *nrm = (unsigned long long *)(c->scr + o_nrm);
+    // FP64 iterative refinement around the FP32 SPIKE solve.  Each column stops
+    // (its x is frozen) at the first step whose backward error is <= SPIKE_MIXED_TOL,
+    // so a column's result does not depend on the other columns solved with it.
+    double *F0 = (double *)(base + o_f0), *X = (double *)(base + o_x), *R = (double *)(base + o_r);
+    unsigned long long *nrm = (unsigned long long *)(base + o_nrm);
+    int *dact = (int *)(base + o_act);
+    std::vector<int> act((size_t)m, 1);
+    SP_CUDA(cudaMemcpyAsync(dact, act.data(), sizeof(int) * (size_t)m, cudaMemcpyHostToDevice, s));
     if (c->timing) SP_CUDA(cudaEventRecord(evs[0], s));
     SP_CUDA(cudaMemcpy2DAsync(F0, sizeof(double) * n, Fd, sizeof(double) * ld, sizeof(double) * n, m,
                               cudaMemcpyDeviceToDevice, s));
@@ -1155,7 +1240,7 @@ extern "C" int spike_solve_ex(spike_handle h, double *F, int64_t ldf, int nrhs, 
       build_solve(c, pp, B, m, tr, steps == 0);
       {
         const float *d = (const float *)B.W;
-        pp.ops.push_back([=](char *) { return launch_add_work32(X, n, d, n, m, s); });
+        pp.ops.push_back([=](char *) { return launch_add_work32(X, n, d, n, m, dact, s); });
       }
       // r = F - op(A) x (FP64, original band) and the per-column backward errors
       pp.ops.push_back([=](char *) { return (int)cudaMemsetAsync(nrm, 0, sizeof(unsigned long long) * (1 + 2 * (size_t)m), s); });
@@ -1176,12 +1261,21 @@ extern "C" int spike_solve_ex(spike_handle h, double *F, int64_t ldf, int nrhs, 
       };
       const double an = as_d(hn[0]);
       worst = 0.0;
+      bool any = false, changed = false;
       for (int col = 0; col < m; ++col) {
         const double r = as_d(hn[1 + 2 * col]), x = as_d(hn[2 + 2 * col]);
         const double be = (an > 0 && x > 0) ? r / (an * x) : (r == 0 ? 0.0 : INFINITY);
         worst = std::max(worst, be);
+        if (!act[col]) continue;
+        if (be > SPIKE_MIXED_TOL) {
+          any = true;
+        } else {
+          act[col] = 0;
+          changed = true;
+        }
       }
-      if (!(worst > SPIKE_MIXED_TOL) || steps >= SPIKE_MIXED_MAX_STEPS) break;
+      if (!any || steps >= SPIKE_MIXED_MAX_STEPS) break;
+      if (changed) SP_CUDA(cudaMemcpyAsync(dact, act.data(), sizeof(int) * (size_t)m, cudaMemcpyHostToDevice, s));
       rhs = R;
     }
     c->last_iters = steps;
@@ -1199,6 +1293,25 @@ extern "C" int spike_solve_ex(spike_handle h, double *F, int64_t ldf, int nrhs, 
     SP_CUDA(cudaStreamSynchronize(s));
   }
   return 0;
+}
+
+extern "C" int spike_solve_ex(spike_handle h, double *F, int64_t ldf, int nrhs, char trans) {
+  return solve_impl(h, F, ldf, nrhs, trans, nullptr, 0, nullptr, false);
+}
+
+extern "C" int spike_solve_workspace(spike_handle h, int nrhs, char trans, int host_f, int64_t *bytes) {
+  if (!bytes) return -5;
+  *bytes = 0;
+  if (!valid(h)) return SPIKE_EHANDLE;
+  if (nrhs < 0) return -2;
+  if (trans != 'N' && trans != 'n' && trans != 'T' && trans != 't' && trans != 'C' && trans != 'c') return -3;
+  return solve_impl(h, nullptr, h->pl.n, nrhs, trans, nullptr, 0, bytes, host_f != 0);
+}
+
+extern "C" int spike_solve_ws(spike_handle h, double *F, int64_t ldf, int nrhs, char trans, void *workspace,
+                              int64_t ws_bytes) {
+  if (!workspace) return -6;
+  return solve_impl(h, F, ldf, nrhs, trans, (char *)workspace, ws_bytes, nullptr, false);
 }
 
 extern "C" int spike_solve(spike_handle h, double *F, int nrhs, char trans) {

@@ -8,12 +8,25 @@
 #include <algorithm>
 #include <atomic>
 #include <cstdint>
+#include <mutex>
+#include <unordered_map>
 
 #include "internal.h"
 
 namespace spk {
 
 #define FULLMASK 0xffffffffu
+
+int smem_at_least(const void *func, size_t bytes) {
+  static std::mutex mu;
+  static std::unordered_map<const void *, size_t> cur;
+  std::lock_guard<std::mutex> g(mu);
+  size_t &c = cur[func];
+  if (c >= bytes) return 0;
+  const cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) c = bytes;
+  return (int)e;
+}
 
 // --------------------------------------------------------------- GEMM
 // 64 x 64 output tile per CTA, 256 threads, each a 4 x 4 sub-tile (rows ty+16u,
@@ -207,7 +220,7 @@ int launch_getrf(const LuDesc *d, int ndesc, int maxn, unsigned long long *statu
   size_t smem = (size_t)maxn * maxn * sizeof(double);
   if (smem > (size_t)GETRF_SMEM_BYTES) smem = 0;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_getrf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = (cudaError_t)smem_at_least((const void *)k_getrf, smem);
     if (e != cudaSuccess) return (int)e;
   }
   k_getrf<<<ndesc, 256, smem, (cudaStream_t)stream>>>(d, status);
@@ -220,8 +233,12 @@ int launch_getrf(const LuDesc *d, int ndesc, int maxn, unsigned long long *statu
 // trans 1: M^T x = b (U^T forward, L^T backward, swaps undone in reverse).
 constexpr int TRS_COLS = 16;
 
+// SMEM_LU: the n x n factor is first copied to shared memory (row stride n + 1), so the
+// column reads of every elimination step are shared-memory broadcasts instead of strided
+// global loads; the arithmetic and its order are the same in both forms.
+template <bool SMEM_LU>
 __global__ void __launch_bounds__(256) k_getrs(const TrsDesc *descs, int ndesc) {
-  extern __shared__ double Bs[];  // n x TRS_COLS
+  extern __shared__ double trs_sm[];  // [LU n x (n+1)] when SMEM_LU, then B n x TRS_COLS
   const int tile = blockIdx.x;
   int lo = 0, hi = ndesc - 1;
   while (lo < hi) {
@@ -232,9 +249,21 @@ __global__ void __launch_bounds__(256) k_getrs(const TrsDesc *descs, int ndesc) 
   const TrsDesc D = descs[lo];
   const int col0 = (tile - D.tile0) * TRS_COLS;
   const int nc = min(TRS_COLS, D.ncols - col0);
-  const int n = D.n, lda = D.lda;
-  const double *LU = D.lu;
+  const int n = D.n;
   const int tid = threadIdx.x;
+  const double *LU = D.lu;
+  int lda = D.lda;
+  double *Bs = trs_sm;
+  if (SMEM_LU) {
+    double *L = trs_sm;
+    for (int idx = tid; idx < n * n; idx += 256) {
+      const int i = idx / n, j = idx - i * n;
+      L[i * (n + 1) + j] = D.lu[(int64_t)i * D.lda + j];
+    }
+    LU = L;
+    lda = n + 1;
+    Bs = trs_sm + (size_t)n * (n + 1);
+  }
   for (int idx = tid; idx < n * TRS_COLS; idx += 256) {
     const int i = idx / TRS_COLS, c = idx % TRS_COLS;
     Bs[idx] = (c < nc) ? D.alpha * D.b[(int64_t)i * D.ldb + col0 + c] : 0.0;
@@ -303,12 +332,20 @@ __global__ void __launch_bounds__(256) k_getrs(const TrsDesc *descs, int ndesc) 
 
 int launch_getrs(const TrsDesc *d, int ndesc, int total_tiles, int maxn, void *stream) {
   if (ndesc <= 0 || total_tiles <= 0) return 0;
-  const size_t smem = (size_t)maxn * TRS_COLS * sizeof(double);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_getrs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t bsm = (size_t)maxn * TRS_COLS * sizeof(double);
+  const size_t lsm = (size_t)maxn * (maxn + 1) * sizeof(double);
+  cudaError_t e;
+  if (bsm + lsm <= 200 * 1024) {
+    e = (cudaError_t)smem_at_least((const void *)k_getrs<true>, bsm + lsm);
     if (e != cudaSuccess) return (int)e;
+    k_getrs<true><<<total_tiles, 256, bsm + lsm, (cudaStream_t)stream>>>(d, ndesc);
+  } else {
+    if (bsm > 48 * 1024) {
+      e = (cudaError_t)smem_at_least((const void *)k_getrs<false>, bsm);
+      if (e != cudaSuccess) return (int)e;
+    }
+    k_getrs<false><<<total_tiles, 256, bsm, (cudaStream_t)stream>>>(d, ndesc);
   }
-  k_getrs<<<total_tiles, 256, smem, (cudaStream_t)stream>>>(d, ndesc);
   count_launch();
   return (int)cudaGetLastError();
 }
@@ -382,8 +419,9 @@ int launch_transpose(const double *in, double *out, int64_t rows, int cols, int6
 }
 
 // Column-major FP64 <-> row-major FP32 work array (mixed-precision refinement).
+// add mode: x += d for the columns with active[c] != 0 (all when active is null).
 __global__ void k_work32(const double *__restrict__ in, int64_t ld, float *__restrict__ w, double *x,
-                         const float *__restrict__ d, int64_t rows, int cols, int add) {
+                         const float *__restrict__ d, int64_t rows, int cols, int add, const int *active) {
   __shared__ double t[32][33];
   const int64_t r0 = (int64_t)blockIdx.x * 32;
   const int c0 = blockIdx.y * 32;
@@ -410,7 +448,7 @@ __global__ void k_work32(const double *__restrict__ in, int64_t ld, float *__res
     for (int q = ty; q < 32; q += 8) {
       const int64_t r = r0 + tx;
       const int c = c0 + q;
-      if (r < rows && c < cols) x[(int64_t)c * ld + r] += t[q][tx];
+      if (r < rows && c < cols && (!active || active[c])) x[(int64_t)c * ld + r] += t[q][tx];
     }
   }
 }
@@ -418,15 +456,16 @@ __global__ void k_work32(const double *__restrict__ in, int64_t ld, float *__res
 int launch_to_work32(const double *in, int64_t ld, float *out, int64_t rows, int cols, void *stream) {
   if (rows <= 0 || cols <= 0) return 0;
   dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((cols + 31) / 32));
-  k_work32<<<grid, 256, 0, (cudaStream_t)stream>>>(in, ld, out, nullptr, nullptr, rows, cols, 0);
+  k_work32<<<grid, 256, 0, (cudaStream_t)stream>>>(in, ld, out, nullptr, nullptr, rows, cols, 0, nullptr);
   count_launch();
   return (int)cudaGetLastError();
 }
 
-int launch_add_work32(double *x, int64_t ld, const float *d, int64_t rows, int cols, void *stream) {
+int launch_add_work32(double *x, int64_t ld, const float *d, int64_t rows, int cols, const int *active,
+                      void *stream) {
   if (rows <= 0 || cols <= 0) return 0;
   dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((cols + 31) / 32));
-  k_work32<<<grid, 256, 0, (cudaStream_t)stream>>>(nullptr, ld, nullptr, x, d, rows, cols, 1);
+  k_work32<<<grid, 256, 0, (cudaStream_t)stream>>>(nullptr, ld, nullptr, x, d, rows, cols, 1, active);
   count_launch();
   return (int)cudaGetLastError();
 }
@@ -552,8 +591,159 @@ __global__ void __launch_bounds__(256) k_resid(const double *__restrict__ band, 
   }
 }
 
+// Tiled form for many right-hand sides: one CTA owns RT consecutive rows of op(A).
+// Row i of op(A) holds the entries at columns i - lo + d, d in [0, W), W = lo + hi + 1
+// (lo = kl, hi = ku for N; swapped for T).  The CTA stages those RT x W entries once
+// (as[li][d], row stride WP) and then, for each chunk of MC columns, the RT + W - 1
+// rows of X the tile touches (xs[r][c], row stride MC + 1), so every global load is a
+// contiguous run: band columns (N) or band rows (T), and X columns.  Thread (tr, tc)
+// accumulates RPT consecutive rows of column tc in ascending d; results are staged
+// in smem and written a column at a time, lanes over rows.
+template <int RPT>
+__global__ void __launch_bounds__(256) k_resid_tile(const double *__restrict__ band, int64_t ldab, int64_t n, int kl,
+                                                    int ku, const double *__restrict__ X, const double *__restrict__ F,
+                                                    double *R, int nrhs, int trans, int RT, int MC, int WP,
+                                                    unsigned long long *norms) {
+  extern __shared__ double smr[];
+  const int lo = trans ? ku : kl, hi = trans ? kl : ku, W = lo + hi + 1;
+  const int XT = RT + W - 1, XP = MC + 1;
+  double *as = smr;                     // RT x WP
+  double *xs = as + (size_t)RT * WP;    // XT x XP
+  double *rs = xs + (size_t)XT * XP;    // RT x XP
+  const int64_t i0 = (int64_t)blockIdx.x * RT;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // band tile, zero outside the matrix
+  if (!trans) {
+    // column j of A holds rows j-ku .. j+kl contiguously: band[j*ldab + ku + i - j]
+    for (int jj = warp; jj < RT + W - 1; jj += 8) {
+      const int64_t j = i0 - lo + jj;
+      for (int li = lane; li < RT; li += 32) {
+        const int64_t i = i0 + li;
+        const int d = (int)(j - i) + lo;
+        if (d < 0 || d >= W) continue;
+        as[li * WP + d] = (i < n && j >= 0 && j < n) ? band[j * ldab + ku + i - j] : 0.0;
+      }
+    }
+  } else {
+    // row i of A^T is column i of A: band[i*ldab + d] with j = i - ku + d
+    for (int idx = tid; idx < RT * W; idx += 256) {
+      const int li = idx / W, d = idx - li * W;
+      const int64_t i = i0 + li, j = i - lo + d;
+      as[li * WP + d] = (i < n && j >= 0 && j < n) ? band[i * ldab + d] : 0.0;
+    }
+  }
+  __syncthreads();
+  if (tid < ((RT + 31) & ~31)) {  // whole warps: the reduction below shuffles
+    double a = 0.0;
+    if (tid < RT && i0 + tid < n)
+      for (int d = 0; d < W; ++d) a += fabs(as[tid * WP + d]);
+    for (int o = 16; o; o >>= 1) a = fmax(a, __shfl_xor_sync(FULLMASK, a, o));
+    if (lane == 0) atomicMax(&norms[0], (unsigned long long)__double_as_longlong(a));
+  }
+  const int tc = tid % MC, tr = tid / MC;  // 256 / MC row lanes x RPT rows = RT
+  for (int c0 = 0; c0 < nrhs; c0 += MC) {
+    const int mc = min(MC, nrhs - c0);
+    __syncthreads();
+    for (int idx = tid; idx < XT * MC; idx += 256) {
+      const int r = idx % XT, c = idx / XT;
+      const int64_t j = i0 - lo + r;
+      xs[r * XP + c] = (c < mc && j >= 0 && j < n) ? X[(int64_t)(c0 + c) * n + j] : 0.0;
+    }
+    __syncthreads();
+    if (tr * RPT < RT) {
+      double acc[RPT];
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) acc[q] = 0.0;
+      const double *ap = as + (size_t)(tr * RPT) * WP;
+      const double *xp = xs + (size_t)(tr * RPT) * XP + tc;
+      for (int d = 0; d < W; ++d) {
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) acc[q] = fma(ap[q * WP + d], xp[(q + d) * XP], acc[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) rs[(tr * RPT + q) * XP + tc] = acc[q];
+    }
+    __syncthreads();
+    for (int c = warp; c < mc; c += 8) {
+      const int64_t col = c0 + c;
+      double rmax = 0.0, xmax = 0.0;
+      for (int li = lane; li < RT; li += 32) {
+        const int64_t i = i0 + li;
+        if (i >= n) continue;
+        const double r = F[col * n + i] - rs[li * XP + c];
+        if (R) R[col * n + i] = r;
+        rmax = fmax(rmax, fabs(r));
+        xmax = fmax(xmax, fabs(xs[(li + lo) * XP + c]));
+      }
+      for (int o = 16; o; o >>= 1) {
+        rmax = fmax(rmax, __shfl_xor_sync(FULLMASK, rmax, o));
+        xmax = fmax(xmax, __shfl_xor_sync(FULLMASK, xmax, o));
+      }
+      if (lane == 0) {
+        atomicMax(&norms[1 + 2 * col], (unsigned long long)__double_as_longlong(rmax));
+        atomicMax(&norms[2 + 2 * col], (unsigned long long)__double_as_longlong(xmax));
+      }
+    }
+  }
+}
+
+// Tile shape for k_resid_tile: MC columns per chunk (>= 8), RT rows, all in <= 200 KB
+// of shared memory.  Returns false when no shape fits (very wide bands).
+static bool resid_tile_shape(int kl, int ku, int nrhs, int *RT, int *MC, int *WP, int *RPT, size_t *smem) {
+  const int W = kl + ku + 1;
+  const int wp = (W % 2 == 1) ? W + 1 : W;  // WP - 1 odd: the column-wise band loads spread over banks
+  for (int mc = (nrhs >= 32 ? 32 : (nrhs >= 16 ? 16 : 8)); mc >= 8; mc /= 2) {
+    const int TR = 256 / mc;
+    for (int rpt = 8; rpt >= 1; rpt /= 2) {
+      const int rt = TR * rpt;
+      if (rt > 64) continue;
+      const size_t bytes = sizeof(double) * ((size_t)rt * wp + (size_t)(rt + W - 1) * (mc + 1) + (size_t)rt * (mc + 1));
+      if (bytes <= 200 * 1024) {
+        *RT = rt;
+        *MC = mc;
+        *WP = wp;
+        *RPT = rpt;
+        *smem = bytes;
+        return true;
+      }
+    }
+  }
+  return false;
+}
+
+static int launch_resid_tile(const double *band, int64_t ldab, int64_t n, int kl, int ku, const double *X,
+                             const double *F, double *R, int nrhs, int trans, unsigned long long *norms,
+                             cudaStream_t st, bool *done) {
+  *done = false;
+  int RT, MC, WP, RPT;
+  size_t smem;
+  if (nrhs < 8 || !resid_tile_shape(kl, ku, nrhs, &RT, &MC, &WP, &RPT, &smem)) return 0;
+  const unsigned grid = (unsigned)((n + RT - 1) / RT);
+  cudaError_t e = cudaSuccess;
+#define SPK_RESID(RP)                                                                                         \
+  case RP:                                                                                                    \
+    e = (cudaError_t)smem_at_least((const void *)k_resid_tile<RP>, smem);                                     \
+    if (e != cudaSuccess) return (int)e;                                                                      \
+    k_resid_tile<RP><<<grid, 256, smem, st>>>(band, ldab, n, kl, ku, X, F, R, nrhs, trans, RT, MC, WP, norms); \
+    break;
+  switch (RPT) {
+    SPK_RESID(1)
+    SPK_RESID(2)
+    SPK_RESID(4)
+    SPK_RESID(8)
+    default: return 0;
+  }
+#undef SPK_RESID
+  count_launch();
+  *done = true;
+  return (int)cudaGetLastError();
+}
+
 int launch_residual(const double *band, int64_t ldab, int64_t n, int kl, int ku, const double *X, const double *F,
                     double *R, int nrhs, int trans, unsigned long long *norms, void *stream) {
+  bool done;
+  const int e = launch_resid_tile(band, ldab, n, kl, ku, X, F, R, nrhs, trans, norms, (cudaStream_t)stream, &done);
+  if (e || done) return e;
   int bx = (int)((n + 255) / 256);
   if (bx > 152 * 8) bx = 152 * 8;
   dim3 grid(bx, nrhs);
@@ -564,6 +754,10 @@ int launch_residual(const double *band, int64_t ldab, int64_t n, int kl, int ku,
 
 int launch_berr(const double *band, int64_t ldab, int64_t n, int kl, int ku, const double *X, const double *F,
                 int nrhs, int trans, unsigned long long *scratch, void *stream) {
+  bool done;
+  const int e = launch_resid_tile(band, ldab, n, kl, ku, X, F, nullptr, nrhs, trans, scratch, (cudaStream_t)stream,
+                                  &done);
+  if (e || done) return e;
   int bx = (int)((n + 255) / 256);
   if (bx > 152 * 8) bx = 152 * 8;
   dim3 grid(bx, nrhs);

@@ -74,7 +74,7 @@ struct SweepDesc {
   int r0, r1, ncols;   // ncols == 0: empty slot
   int kind;            // SweepKind
   int kw;              // off-diagonal width of the triangle (k, or 2k for U in pivoting mode)
-  int pad;
+  int fixed_split;     // 1: batch-invariant summation order of the window products
   const double *ga;
   int64_t ga_rs, ga_cs;
   const double *gb;
@@ -130,6 +130,10 @@ struct SumDesc {
 // ------------------------------------------------------------ launchers
 // Each returns cudaError_t as int (0 = success) and counts its kernel launches.
 void count_launch(int n = 1);
+// Raise a kernel's dynamic shared-memory limit to at least `bytes`, never lowering it.
+// The limit is a process-wide attribute of the function: lowering it while another host
+// thread launches the same kernel with a larger request would make that launch fail.
+int smem_at_least(const void *func, size_t bytes);
 // f32 != 0: the leaf storage (factors, spike columns, sweep operands) is FP32 (mixed-precision handles).
 int launch_repack(const double *band, int64_t ldab, int kl, int ku, int64_t n, int k, int ldf, int dofs,
                   const LeafDev *leaves, int nleaves, void *fb, unsigned long long *amax_bits, void *stream,
@@ -163,7 +167,7 @@ int launch_transpose(const double *in, double *out, int64_t rows, int cols, int6
 // Column-major FP64 (rows x cols, ld) -> row-major FP32 work array.
 int launch_to_work32(const double *in, int64_t ld, float *out, int64_t rows, int cols, void *stream);
 // Column-major FP64 x (ld) += row-major FP32 correction d.
-int launch_add_work32(double *x, int64_t ld, const float *d, int64_t rows, int cols, void *stream);
+int launch_add_work32(double *x, int64_t ld, const float *d, int64_t rows, int cols, const int *active, void *stream);
 // Residual for iterative refinement: R = F - op(A) X (all column-major FP64, ld = n) and, as bit
 // patterns of non-negative doubles, norms[1+2c] = ||R_c||_inf, norms[2+2c] = ||X_c||_inf, norms[0] = ||op(A)||_inf.
 int launch_residual(const double *band, int64_t ldab, int64_t n, int kl, int ku, const double *X, const double *F,

@@ -27,6 +27,7 @@ namespace spk {
 
 constexpr int WCH = 256;  // sweep window rows per staged chunk
 constexpr int SCW = 128;  // RHS columns per sweep pass: 8 warps x 16 accumulators
+constexpr int WSPLIT = NTHREADS / 32;  // fixed sub-ranges of each window chunk (one per warp)
 constexpr size_t SWEEP_SMEM = sizeof(double) * ((size_t)WCH * NB + NB * NB + NB + (size_t)NB * (SCW + 1));
 
 // ------------------------------------------------------------------ repack
@@ -342,12 +343,12 @@ int launch_factor_nopiv(const LeafDev *leaves, int nleaves, int k, int ldf, void
   if (smem < SWEEP_SMEM) smem = SWEEP_SMEM;
   cudaError_t e;
   if (f32) {
-    e = cudaFuncSetAttribute(k_factor_nopiv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = (cudaError_t)smem_at_least((const void *)k_factor_nopiv<float>, smem);
     if (e != cudaSuccess) return (int)e;
     k_factor_nopiv<float><<<nleaves, NTHREADS, smem, (cudaStream_t)stream>>>(
         leaves, k, ldf, (float *)fb, (float *)dinv, (float *)zbuf, zoff, amax_bits, boost_eps, status, sweeps);
   } else {
-    e = cudaFuncSetAttribute(k_factor_nopiv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = (cudaError_t)smem_at_least((const void *)k_factor_nopiv<double>, smem);
     if (e != cudaSuccess) return (int)e;
     k_factor_nopiv<double><<<nleaves, NTHREADS, smem, (cudaStream_t)stream>>>(
         leaves, k, ldf, (double *)fb, (double *)dinv, (double *)zbuf, zoff, amax_bits, boost_eps, status, sweeps);
@@ -498,11 +499,34 @@ __device__ void sweep_run(const SweepDesc &D, int ldf, int dofs, T *sm) {
 
   for (int c0 = 0; c0 < D.ncols; c0 += SCW) {
     const int cw = min(SCW, D.ncols - c0);
-    int nsplit = (cw < nwarps) ? (nwarps / cw) : 1;
-    const int groups = nwarps / nsplit;
-    const int cpw = (cw + groups - 1) / groups;
-    const int grp = warp % groups, split = warp / groups;
-    const int col_base = c0 + grp * cpw;
+    const bool fixed = D.fixed_split != 0;
+    // Column split.  Default: with few columns (cw < nwarps) the window rows are split
+    // over nsplit = nwarps / cw warp groups and the partial sums are combined at the
+    // end, so the rounding of a column depends on how many columns share the pass.
+    // fixed_split (batch-invariant): every staged window chunk is cut into WSPLIT fixed
+    // sub-ranges whose products are subtracted from G one at a time in ascending order;
+    // with few columns warp w owns sub-range w for all columns, otherwise a warp owns a
+    // column group and walks the sub-ranges itself.  Each column then sees the same
+    // sequence of roundings whatever the other right-hand sides of the pass.
+    int nsplit, cpw, col_base, split;
+    bool by_split;
+    if (fixed) {
+      by_split = cw < nwarps;
+      nsplit = WSPLIT;
+      cpw = by_split ? cw : (cw + nwarps - 1) / nwarps;
+      col_base = by_split ? c0 : c0 + warp * cpw;
+      split = by_split ? warp : 0;
+    } else {
+      nsplit = (cw < nwarps) ? (nwarps / cw) : 1;
+      const int groups = nwarps / nsplit;
+      cpw = (cw + groups - 1) / groups;
+      const int grp = warp % groups;
+      split = warp / groups;
+      col_base = c0 + grp * cpw;
+      by_split = false;
+    }
+    const int lastc = c0 + cw - 1;
+    const bool owns = col_base <= lastc;
     const int nblk = (D.r1 - D.r0 + NB - 1) / NB;
     for (int bk = 0; bk < nblk; ++bk) {
       int64_t b0, b1;
@@ -539,6 +563,18 @@ __device__ void sweep_run(const SweepDesc &D, int ldf, int dofs, T *sm) {
         for (int u = 0; u < NB * NB / NTHREADS; ++u) Td[tid + u * NTHREADS] = v[u];
       }
       for (int a = tid; a < NB; a += NTHREADS) dsm[a] = (a < nbk) ? (UNIT ? (T)1 : ddinv[row(a)]) : (T)0;
+      if (fixed) {  // G block first (rows past the block end are zero)
+        for (int idx = tid; idx < NB * cw; idx += NTHREADS) {
+          const int a = idx % NB, cc = idx / NB, col = c0 + cc;
+          T g = (T)0;
+          if (a < nbk) {
+            const int64_t r = row(a);
+            g = dga[r * D.ga_rs + (int64_t)col * D.ga_cs];
+            if (dgb) g = fma(gbs, dgb[r * D.gb_rs + (int64_t)col * D.gb_cs], g);
+          }
+          Gs[a * GLD + cc] = g;
+        }
+      }
 
       T acc[16];
 #pragma unroll
@@ -561,48 +597,76 @@ __device__ void sweep_run(const SweepDesc &D, int ldf, int dofs, T *sm) {
             if (base + u * NTHREADS < tot) Tw[base + u * NTHREADS] = v[u];
         }
         __syncthreads();
-        const int len = jce - jc0;
-        const int per = (len + nsplit - 1) / nsplit;
-        const int js = jc0 + split * per, je = min(jce, js + per);
+        const int per = (jce - jc0 + nsplit - 1) / nsplit;
         // A predicated-off DFMA still occupies the FP64 pipe, so the accumulation loop is
         // instantiated for the exact column count; edge columns are clamped, not predicated.
-        const T *xw = dx + wrow(js) * D.x_rs;
-        const int64_t step = D.x_rs;  // wrow(j+1) = wrow(j) + 1 in both sweep directions
-        const int lastc = c0 + cw - 1;
-        if (cpw <= 1) window_fma<T, 1>(acc, Tw + (js - jc0) * NB + lane, xw, step, D.x_cs, col_base, lastc, je - js);
-        else if (cpw <= 2) window_fma<T, 2>(acc, Tw + (js - jc0) * NB + lane, xw, step, D.x_cs, col_base, lastc, je - js);
-        else if (cpw <= 4) window_fma<T, 4>(acc, Tw + (js - jc0) * NB + lane, xw, step, D.x_cs, col_base, lastc, je - js);
-        else if (cpw <= 8) window_fma<T, 8>(acc, Tw + (js - jc0) * NB + lane, xw, step, D.x_cs, col_base, lastc, je - js);
-        else window_fma<T, 16>(acc, Tw + (js - jc0) * NB + lane, xw, step, D.x_cs, col_base, lastc, je - js);
-      }
-      __syncthreads();
-      for (int s = 0; s < nsplit; ++s) {
-        if (split == s) {
+        auto partial = [&](int sp) {
+          const int js = min(jce, jc0 + sp * per), je = min(jce, js + per);
+          const T *xw = dx + wrow(js) * D.x_rs;
+          const int64_t step = D.x_rs;  // wrow(j+1) = wrow(j) + 1 in both sweep directions
+          const T *tw = Tw + (js - jc0) * NB + lane;
+          if (cpw <= 1) window_fma<T, 1>(acc, tw, xw, step, D.x_cs, col_base, lastc, je - js);
+          else if (cpw <= 2) window_fma<T, 2>(acc, tw, xw, step, D.x_cs, col_base, lastc, je - js);
+          else if (cpw <= 4) window_fma<T, 4>(acc, tw, xw, step, D.x_cs, col_base, lastc, je - js);
+          else if (cpw <= 8) window_fma<T, 8>(acc, tw, xw, step, D.x_cs, col_base, lastc, je - js);
+          else window_fma<T, 16>(acc, tw, xw, step, D.x_cs, col_base, lastc, je - js);
+        };
+        auto subtract = [&]() {
           if (lane < nbk) {
-            const int64_t r = row(lane);
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
               const int col = col_base + q;
-              if (q < cpw && col < c0 + cw) {
-                T g;
-                if (s == 0) {
-                  g = dga[r * D.ga_rs + (int64_t)col * D.ga_cs];
-                  if (dgb) g = fma(gbs, dgb[r * D.gb_rs + (int64_t)col * D.gb_cs], g);
-                } else {
-                  g = Gs[lane * GLD + (col - c0)];
-                }
-                Gs[lane * GLD + (col - c0)] = g - acc[q];
-              }
-            }
-          } else if (s == 0) {
-#pragma unroll
-            for (int q = 0; q < 16; ++q) {
-              const int col = col_base + q;
-              if (q < cpw && col < c0 + cw) Gs[lane * GLD + (col - c0)] = (T)0;
+              if (q < cpw && col <= lastc) Gs[lane * GLD + (col - c0)] -= acc[q];
             }
           }
+#pragma unroll
+          for (int q = 0; q < 16; ++q) acc[q] = (T)0;
+        };
+        if (!fixed) {
+          partial(split);  // accumulates across chunks; combined after the last one
+        } else if (by_split) {
+          partial(warp);
+          for (int sp = 0; sp < WSPLIT; ++sp) {
+            __syncthreads();
+            if (warp == sp) subtract();
+          }
+        } else if (owns) {
+          for (int sp = 0; sp < WSPLIT; ++sp) {
+            partial(sp);
+            subtract();
+          }
         }
-        __syncthreads();
+      }
+      __syncthreads();
+      if (!fixed) {
+        for (int s = 0; s < nsplit; ++s) {
+          if (split == s) {
+            if (lane < nbk) {
+              const int64_t r = row(lane);
+#pragma unroll
+              for (int q = 0; q < 16; ++q) {
+                const int col = col_base + q;
+                if (q < cpw && col < c0 + cw) {
+                  T g;
+                  if (s == 0) {
+                    g = dga[r * D.ga_rs + (int64_t)col * D.ga_cs];
+                    if (dgb) g = fma(gbs, dgb[r * D.gb_rs + (int64_t)col * D.gb_cs], g);
+                  } else {
+                    g = Gs[lane * GLD + (col - c0)];
+                  }
+                  Gs[lane * GLD + (col - c0)] = g - acc[q];
+                }
+              }
+            } else if (s == 0) {
+#pragma unroll
+              for (int q = 0; q < 16; ++q) {
+                const int col = col_base + q;
+                if (q < cpw && col < c0 + cw) Gs[lane * GLD + (col - c0)] = (T)0;
+              }
+            }
+          }
+          __syncthreads();
+        }
       }
       // in-block triangular solve
       if (cw >= 64) {
@@ -661,11 +725,11 @@ int launch_sweeps(const SweepDesc *descs, int ncta, int per_cta, int ldf, int do
   if (ncta <= 0 || per_cta <= 0) return 0;
   cudaError_t e;
   if (f32) {
-    e = cudaFuncSetAttribute(k_sweeps<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_SMEM);
+    e = (cudaError_t)smem_at_least((const void *)k_sweeps<float>, SWEEP_SMEM);
     if (e != cudaSuccess) return (int)e;
     k_sweeps<float><<<ncta, NTHREADS, SWEEP_SMEM, (cudaStream_t)stream>>>(descs, per_cta, ldf, dofs);
   } else {
-    e = cudaFuncSetAttribute(k_sweeps<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_SMEM);
+    e = (cudaError_t)smem_at_least((const void *)k_sweeps<double>, SWEEP_SMEM);
     if (e != cudaSuccess) return (int)e;
     k_sweeps<double><<<ncta, NTHREADS, SWEEP_SMEM, (cudaStream_t)stream>>>(descs, per_cta, ldf, dofs);
   }

@@ -1,0 +1,569 @@
+// Serving engine of libspike.so (spike_serve.h): a catalogue of banded matrices, their
+// factorizations kept resident in device memory under a byte budget (least recently
+// used evicted first), and workers that each own one host thread and one CUDA stream.
+//
+// A factorization is reused for every later request on its matrix, N and T alike
+// (Sec. 4 reuses the factors of Sec. 2 for the transpose solve).  Waiting requests
+// with the same (matrix, trans, precision) are merged into one multi-column solve:
+// the factors and spike tips are then read once for all of them.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "spike.h"
+#include "spike_serve.h"
+
+namespace {
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+void sleep_us(int us) {
+  if (us > 0) std::this_thread::sleep_for(std::chrono::microseconds(us));
+}
+
+struct Req {
+  int64_t mid = 0;
+  const double *F = nullptr;
+  double *X = nullptr;
+  int nrhs = 0;
+  char trans = 'N';
+  int prec = 0;
+  double t_submit = 0.0, t_done = 0.0;
+  int status = 0;
+  bool done = false;
+};
+
+// One factorization of a matrix (precision 0 = FP64, 1 = mixed).
+struct Fac {
+  spike_handle h = nullptr;
+  int64_t bytes = 0;      // counted against the budget (a reservation while factoring)
+  uint64_t last_use = 0;  // LRU clock
+  bool resident = false;  // factored and held
+  bool busy = false;      // a worker is factoring or solving with it
+};
+
+struct Mat {
+  const double *band = nullptr;
+  int64_t ldab = 0, n = 0;
+  int kl = 0, ku = 0, pivot = 0, p = 1;
+  bool host = true;
+  Fac fac[2];
+};
+
+// Per-worker device buffers: solve workspace and the merged right-hand sides.
+struct WorkerBuf {
+  char *ws = nullptr;
+  int64_t ws_bytes = 0;
+  double *fb = nullptr;
+  int64_t fb_bytes = 0;
+};
+
+}  // namespace
+
+struct spike_server_s {
+  spike_server_config cfg;
+  int dev = 0;
+  bool dry = false;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::unordered_map<int64_t, Mat> mats;
+  std::deque<Req> reqs;  // index = request id (deque: stable references)
+  std::deque<int64_t> pending;
+  std::vector<std::thread> th;
+  std::vector<cudaStream_t> st;
+  std::vector<WorkerBuf> wb;
+  bool stop = false;
+  int64_t used = 0, peak = 0;
+  uint64_t tick = 0;
+  int running = 0;  // workers between taking a batch and finishing it
+  int waiting = 0;  // of those, workers blocked in admit()
+  int64_t batches = 0, rhs = 0, nfact = 0, nevict = 0, nwait = 0, failed = 0, completed = 0;
+  int max_batch = 0;
+  double t_first = -1.0, t_last = 0.0;
+  std::vector<double> lat;
+  cudaMemPool_t pool = nullptr;
+  uint64_t pool_old = 0;
+  std::string last_error;  // CUDA error text of the last failed request (worker threads' own)
+};
+
+namespace {
+
+using Lock = std::unique_lock<std::mutex>;
+
+void account(spike_server_s *S, int64_t delta) {
+  S->used += delta;
+  S->peak = std::max(S->peak, S->used);
+}
+
+// Make room for `bytes` more device bytes: evict least recently used factorizations
+// that no worker is using.  Waits while another worker that is not itself waiting
+// holds memory that it will release; returns false when the bytes cannot fit (so two
+// workers never wait on each other).
+bool admit(spike_server_s *S, Lock &lk, int64_t bytes, std::vector<spike_handle> &victims) {
+  if (bytes > S->cfg.budget_bytes) return false;
+  while (S->used + bytes > S->cfg.budget_bytes) {
+    Fac *v = nullptr;
+    for (auto &kv : S->mats)
+      for (auto &f : kv.second.fac)
+        if (f.resident && !f.busy && (!v || f.last_use < v->last_use)) v = &f;
+    if (v) {
+      victims.push_back(v->h);
+      account(S, -v->bytes);
+      v->h = nullptr;
+      v->bytes = 0;
+      v->resident = false;
+      ++S->nevict;
+      continue;
+    }
+    if (S->running - S->waiting <= 1) return false;  // nobody else will release anything
+    ++S->nwait;
+    ++S->waiting;
+    S->cv_done.wait(lk);
+    --S->waiting;
+  }
+  account(S, bytes);
+  return true;
+}
+
+// Take the oldest waiting request whose factorization is not in use, and every other
+// waiting request with the same key, up to max_batch_rhs columns (the first is always
+// taken).  Returns false when nothing can run now.
+bool pick(spike_server_s *S, std::vector<int64_t> &batch) {
+  batch.clear();
+  size_t first = S->pending.size();
+  for (size_t i = 0; i < S->pending.size(); ++i) {
+    const Req &r = S->reqs[S->pending[i]];
+    if (!S->mats[r.mid].fac[r.prec].busy) {
+      first = i;
+      break;
+    }
+  }
+  if (first == S->pending.size()) return false;
+  const Req &r0 = S->reqs[S->pending[first]];
+  int cols = 0;
+  std::deque<int64_t> rest;
+  for (size_t i = 0; i < S->pending.size(); ++i) {
+    const int64_t id = S->pending[i];
+    const Req &r = S->reqs[id];
+    const bool same = i >= first && r.mid == r0.mid && r.prec == r0.prec && r.trans == r0.trans;
+    if (same && (batch.empty() || cols + r.nrhs <= S->cfg.max_batch_rhs)) {
+      batch.push_back(id);
+      cols += r.nrhs;
+    } else {
+      rest.push_back(id);
+    }
+  }
+  S->pending.swap(rest);
+  return true;
+}
+
+// Free evicted factorizations outside the lock (spike_free waits for the stream).
+void release(Lock &lk, std::vector<spike_handle> &victims, cudaStream_t st) {
+  if (victims.empty()) return;
+  lk.unlock();
+  for (auto h : victims) {
+    if (!h) continue;
+    spike_set_stream(h, st);
+    spike_free(h);
+  }
+  victims.clear();
+  lk.lock();
+}
+
+int grow(spike_server_s *S, Lock &lk, char **p, int64_t *have, int64_t need, cudaStream_t st) {
+  if (need <= *have) return 0;
+  std::vector<spike_handle> victims;
+  const bool ok = admit(S, lk, need - *have, victims);
+  release(lk, victims, st);
+  if (!ok) return SPIKE_ENOMEM;
+  lk.unlock();
+  int rc = 0;
+  if (!S->dry) {
+    if (*p) cudaFreeAsync(*p, st);
+    *p = nullptr;
+    if (cudaMallocAsync((void **)p, (size_t)need, st) != cudaSuccess) {
+      cudaGetLastError();
+      *p = nullptr;
+      rc = SPIKE_ENOMEM;
+    }
+  }
+  lk.lock();
+  if (rc) {
+    account(S, -*have - (need - *have));
+    *have = 0;
+    return rc;
+  }
+  *have = need;
+  return 0;
+}
+
+void worker(spike_server_s *S, int w) {
+  if (!S->dry) cudaSetDevice(S->dev);
+  cudaStream_t st = S->dry ? nullptr : S->st[w];
+  WorkerBuf &B = S->wb[w];
+  Lock lk(S->mu);
+  std::vector<int64_t> batch;
+  for (;;) {
+    while (!pick(S, batch)) {
+      if (S->stop && S->pending.empty()) return;
+      S->cv_work.wait(lk);
+    }
+    ++S->running;
+    const Req &r0 = S->reqs[batch[0]];
+    Mat &M = S->mats[r0.mid];
+    const int prec = r0.prec;
+    const char trans = r0.trans;
+    Fac &F = M.fac[prec];
+    F.busy = true;
+    int cols = 0;
+    for (int64_t id : batch) cols += S->reqs[id].nrhs;
+    int rc = 0;
+
+    // 1. factorization on first use (or after eviction)
+    if (!F.resident) {
+      spike_options o;
+      memset(&o, 0, sizeof(o));
+      o.K = S->cfg.K;
+      o.nrhs_hint = S->cfg.nrhs_hint > 0 ? S->cfg.nrhs_hint : 16;
+      o.flags = SPIKE_FLAG_STAGE_BALANCE | SPIKE_FLAG_BATCH_INVARIANT | (prec ? SPIKE_FLAG_MIXED : 0);
+      o.stream = st;
+      int64_t res = 0, tr = 0;
+      rc = spike_factor_bytes(M.n, M.kl, M.ku, M.p, M.pivot, &o, M.host ? 1 : 0, &res, &tr);
+      const int64_t slack = 1 << 20;  // descriptor buffer
+      const int64_t reserve = res + tr + slack;
+      std::vector<spike_handle> victims;
+      if (rc == 0 && !admit(S, lk, reserve, victims)) rc = SPIKE_ENOMEM;
+      release(lk, victims, st);
+      if (rc == 0) {
+        F.bytes = reserve;
+        lk.unlock();
+        spike_handle h = nullptr;
+        int64_t actual = res + slack;
+        if (S->dry) {
+          sleep_us(S->cfg.dryrun_factor_us);
+        } else {
+          rc = spike_factor_ex(M.band, M.ldab, M.n, M.kl, M.ku, M.p, M.pivot, &o, &h);
+          if (h) {
+            spike_info info;
+            if (spike_get_info(h, &info) == 0) actual = info.device_bytes;
+          }
+          if (rc < 0 && h) {
+            spike_free(h);
+            h = nullptr;
+          }
+        }
+        lk.lock();
+        ++S->nfact;
+        if (rc >= 0) {  // rc > 0: singular (pivoting); kept, its solves report rc
+          account(S, actual - F.bytes);
+          F.bytes = actual;
+          F.h = h;
+          F.resident = true;
+        } else {
+          account(S, -F.bytes);
+          F.bytes = 0;
+        }
+      }
+    }
+
+    // 2. buffers: merged right-hand sides and solve workspace of this worker
+    if (rc == 0) {
+      int64_t ws_need = 0;
+      if (S->dry) {
+        ws_need = (int64_t)sizeof(double) * M.n * cols * 2;
+      } else {
+        rc = spike_solve_workspace(F.h, cols, trans, 0, &ws_need);
+      }
+      if (rc == 0) rc = grow(S, lk, &B.ws, &B.ws_bytes, ws_need, st);
+      if (rc == 0) rc = grow(S, lk, (char **)&B.fb, &B.fb_bytes, (int64_t)sizeof(double) * M.n * cols, st);
+    }
+
+    // 3. the merged solve
+    if (rc == 0) {
+      std::vector<Req *> rs;
+      for (int64_t id : batch) rs.push_back(&S->reqs[id]);
+      spike_handle h = F.h;
+      lk.unlock();
+      const size_t col_bytes = sizeof(double) * (size_t)M.n;
+      if (S->dry) {
+        sleep_us(S->cfg.dryrun_solve_us);
+        for (Req *r : rs) memmove(r->X, r->F, col_bytes * r->nrhs);
+      } else {
+        int64_t off = 0;
+        for (Req *r : rs) {
+          if (!rc && cudaMemcpyAsync(B.fb + off * M.n, r->F, col_bytes * r->nrhs, cudaMemcpyDefault, st) != cudaSuccess)
+            rc = SPIKE_ECUDA;
+          off += r->nrhs;
+        }
+        if (!rc) rc = spike_set_stream(h, st);
+        if (!rc) rc = spike_solve_ws(h, B.fb, M.n, cols, trans, B.ws, B.ws_bytes);
+        off = 0;
+        for (Req *r : rs) {
+          if (!rc && cudaMemcpyAsync(r->X, B.fb + off * M.n, col_bytes * r->nrhs, cudaMemcpyDefault, st) != cudaSuccess)
+            rc = SPIKE_ECUDA;
+          off += r->nrhs;
+        }
+        if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = SPIKE_ECUDA;
+      }
+      lk.lock();
+      if (!S->dry && F.h) {
+        spike_info info;  // the descriptor buffer may have grown
+        if (spike_get_info(F.h, &info) == 0) {
+          account(S, info.device_bytes - F.bytes);
+          F.bytes = info.device_bytes;
+        }
+      }
+    }
+
+    // 4. completion
+    if (rc != 0) {
+      const char *msg = spike_last_cuda_error();
+      S->last_error = std::string(spike_strerror(rc)) + (msg && *msg ? std::string(": ") + msg : std::string());
+    }
+    const double t = now_s();
+    for (int64_t id : batch) {
+      Req &r = S->reqs[id];
+      r.status = rc;
+      r.t_done = t;
+      r.done = true;
+      S->lat.push_back(1e3 * (t - r.t_submit));
+      if (rc == 0) ++S->completed;
+      else ++S->failed;
+    }
+    ++S->batches;
+    S->rhs += cols;
+    S->max_batch = std::max(S->max_batch, (int)batch.size());
+    S->t_last = t;
+    F.last_use = ++S->tick;
+    F.busy = false;
+    --S->running;
+    S->cv_done.notify_all();
+    S->cv_work.notify_all();
+  }
+}
+
+}  // namespace
+
+extern "C" int spike_server_create(const spike_server_config *cfg, spike_server *out) {
+  if (!out) return -2;
+  *out = nullptr;
+  if (!cfg || cfg->budget_bytes <= 0 || cfg->streams < 1 || cfg->streams > 64 || cfg->max_batch_rhs < 1 ||
+      cfg->p < 0)
+    return -1;
+  spike_server_s *S = new spike_server_s();
+  S->cfg = *cfg;
+  S->dry = (cfg->flags & SPIKE_SERVE_DRYRUN) != 0;
+  if (!S->dry) {
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+      cudaGetLastError();
+      delete S;
+      return SPIKE_ENOGPU;
+    }
+    cudaGetDevice(&S->dev);
+    // keep freed blocks of the stream-ordered allocator cached up to the budget, so
+    // evictions and re-factorizations reuse memory instead of remapping it
+    if (cudaDeviceGetDefaultMemPool(&S->pool, S->dev) == cudaSuccess) {
+      cudaMemPoolGetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &S->pool_old);
+      uint64_t thr = (uint64_t)cfg->budget_bytes;
+      cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    } else {
+      cudaGetLastError();
+      S->pool = nullptr;
+    }
+    S->st.resize(cfg->streams);
+    for (auto &s : S->st)
+      if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        s = nullptr;
+        spike_server_destroy(S);
+        return SPIKE_ECUDA;
+      }
+  }
+  S->wb.resize(cfg->streams);
+  for (int w = 0; w < cfg->streams; ++w) S->th.emplace_back(worker, S, w);
+  *out = S;
+  return 0;
+}
+
+extern "C" int spike_server_add_matrix(spike_server S, int64_t id, const double *band, int64_t ldab, int64_t n,
+                                       int kl, int ku, int pivot) {
+  if (!S) return -1;
+  if (!band) return -3;
+  if (n < 1) return -5;
+  if (kl < 0 || (n > 1 && kl >= n)) return -6;
+  if (ku < 0 || (n > 1 && ku >= n)) return -7;
+  if (ldab < (int64_t)kl + ku + 1) return -4;
+  if (pivot != 0 && pivot != 1) return -8;
+  if (std::max(kl, ku) > SPIKE_MAX_K) return SPIKE_ENOTSUP;
+  Mat M;
+  M.band = band;
+  M.ldab = ldab;
+  M.n = n;
+  M.kl = kl;
+  M.ku = ku;
+  M.pivot = pivot;
+  const int64_t k = std::max(1, std::max(kl, ku));
+  M.p = S->cfg.p > 0 ? S->cfg.p : (int)std::min<int64_t>(148, std::max<int64_t>(1, n / (8 * k)));
+  if (S->dry) {
+    M.host = true;
+  } else {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, band) != cudaSuccess) {
+      cudaGetLastError();
+      M.host = true;
+    } else {
+      M.host = !(a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged);
+    }
+  }
+  Lock lk(S->mu);
+  if (S->mats.count(id)) return -2;
+  S->mats.emplace(id, M);
+  return 0;
+}
+
+extern "C" int64_t spike_server_submit(spike_server S, int64_t matrix_id, const double *F, double *X, int nrhs,
+                                       char trans, int precision) {
+  if (!S) return -1;
+  if (!F) return -3;
+  if (!X) return -4;
+  if (nrhs < 1) return -5;
+  if (trans == 'n') trans = 'N';
+  if (trans == 't' || trans == 'C' || trans == 'c') trans = 'T';
+  if (trans != 'N' && trans != 'T') return -6;
+  if (precision != 0 && precision != 1) return -7;
+  Lock lk(S->mu);
+  auto it = S->mats.find(matrix_id);
+  if (it == S->mats.end()) return -2;
+  if (precision == 1 && it->second.pivot) return SPIKE_ENOTSUP;
+  Req r;
+  r.mid = matrix_id;
+  r.F = F;
+  r.X = X;
+  r.nrhs = nrhs;
+  r.trans = trans;
+  r.prec = precision;
+  r.t_submit = now_s();
+  if (S->t_first < 0) S->t_first = r.t_submit;
+  const int64_t id = (int64_t)S->reqs.size();
+  S->reqs.push_back(r);
+  S->pending.push_back(id);
+  S->cv_work.notify_one();
+  return id;
+}
+
+extern "C" int spike_server_wait(spike_server S, int64_t req, double *latency_ms) {
+  if (!S) return -1;
+  Lock lk(S->mu);
+  if (req < 0 || req >= (int64_t)S->reqs.size()) return -2;
+  S->cv_done.wait(lk, [&] { return S->reqs[req].done; });
+  const Req &r = S->reqs[req];
+  if (latency_ms) *latency_ms = 1e3 * (r.t_done - r.t_submit);
+  return r.status;
+}
+
+extern "C" int spike_server_drain(spike_server S) {
+  if (!S) return -1;
+  Lock lk(S->mu);
+  S->cv_done.wait(lk, [&] { return S->completed + S->failed == (int64_t)S->reqs.size(); });
+  return 0;
+}
+
+extern "C" int spike_server_stats_get(spike_server S, spike_server_stats *o) {
+  if (!S) return -1;
+  if (!o) return -2;
+  Lock lk(S->mu);
+  memset(o, 0, sizeof(*o));
+  o->submitted = (int64_t)S->reqs.size();
+  o->completed = S->completed;
+  o->failed = S->failed;
+  o->batches = S->batches;
+  o->rhs = S->rhs;
+  o->factorizations = S->nfact;
+  o->evictions = S->nevict;
+  o->admission_waits = S->nwait;
+  o->used_bytes = S->used;
+  o->peak_bytes = S->peak;
+  for (auto &kv : S->mats)
+    for (auto &f : kv.second.fac) o->resident += f.resident ? 1 : 0;
+  o->max_batch = S->max_batch;
+  if (!S->lat.empty()) {
+    std::vector<double> v = S->lat;
+    std::sort(v.begin(), v.end());
+    auto rank = [&](double q) {  // nearest-rank percentile
+      size_t i = (size_t)std::ceil(q * (double)v.size());
+      return v[std::min(v.size(), std::max<size_t>(i, 1)) - 1];
+    };
+    o->p50_ms = rank(0.50);
+    o->p99_ms = rank(0.99);
+    o->max_ms = v.back();
+    double s = 0.0;
+    for (double x : v) s += x;
+    o->mean_ms = s / (double)v.size();
+    o->span_s = S->t_last - S->t_first;
+    if (o->span_s > 0) {
+      o->solves_per_s = (double)S->completed / o->span_s;
+      o->rhs_per_s = (double)S->rhs / o->span_s;
+    }
+  }
+  return 0;
+}
+
+extern "C" int spike_server_latencies(spike_server S, double *ms, int64_t cap, int64_t *count) {
+  if (!S) return -1;
+  Lock lk(S->mu);
+  const int64_t n = (int64_t)S->lat.size();
+  if (count) *count = n;
+  if (ms)
+    for (int64_t i = 0; i < std::min(cap, n); ++i) ms[i] = S->lat[i];
+  return 0;
+}
+
+extern "C" const char *spike_server_last_error(spike_server S) {
+  if (!S) return "";
+  Lock lk(S->mu);
+  thread_local std::string copy;
+  copy = S->last_error;
+  return copy.c_str();
+}
+
+extern "C" void spike_server_destroy(spike_server S) {
+  if (!S) return;
+  {
+    Lock lk(S->mu);
+    S->stop = true;
+  }
+  S->cv_work.notify_all();
+  for (auto &t : S->th)
+    if (t.joinable()) t.join();
+  if (!S->dry) {
+    cudaSetDevice(S->dev);
+    for (auto &kv : S->mats)
+      for (auto &f : kv.second.fac)
+        if (f.h) spike_free(f.h);
+    for (size_t w = 0; w < S->wb.size(); ++w) {
+      cudaStream_t s = w < S->st.size() ? S->st[w] : nullptr;
+      if (S->wb[w].ws) cudaFreeAsync(S->wb[w].ws, s);
+      if (S->wb[w].fb) cudaFreeAsync(S->wb[w].fb, s);
+    }
+    for (auto &s : S->st)
+      if (s) {
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+      }
+    if (S->pool) cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &S->pool_old);
+  }
+  delete S;
+}

@@ -99,3 +99,59 @@ def make_problem(n, kl, ku, nrhs, seed, dist="uniform", dd=1.1, keep_sign=False,
 SMALL_P4 = dict(n=10_000, kl=8, ku=8, nrhs=1, p=4, dist="uniform", dd=1.1, seed=0)
 LARGE = dict(n=1_048_576, kls=(32, 128, 320), nrhs=(1, 64), ps=(64, 148, 192), dds=(1.01, 1.5), seed=1)
 PIVOT = dict(n=262_144, kls=(16, 64), nrhs=8, p=148, dist="normal", dd=0.3, keep_sign=True, seed=2)
+# Many-matrix serving workload: 10,000 requests arriving as a Poisson process at
+# 2000/s over a catalogue of 500 matrices (n log-uniform in [1e3, 2e5], k uniform in
+# {4, 8, ..., 128}, DD 1.1), matrix chosen by Zipf(1.1) rank, nrhs uniform in [1, 32],
+# 30 % transpose solves, 50 % mixed precision, 40 GB device budget.
+SERVING = dict(requests=10_000, rate=2000.0, matrices=500, n_lo=1_000, n_hi=200_000, k_choices=tuple(range(4, 129, 4)),
+               dd=1.1, zipf=1.1, nrhs_max=32, trans_t=0.3, mixed=0.5, budget_gb=40, seed=4)
+
+
+def serving_catalogue(cfg=SERVING, rng=None):
+    """(n, k) of every catalogue matrix, from the workload seed."""
+    rng = np.random.default_rng(cfg["seed"]) if rng is None else rng
+    m = cfg["matrices"]
+    ns = np.exp(rng.uniform(np.log(cfg["n_lo"]), np.log(cfg["n_hi"]), m)).astype(np.int64)
+    ks = rng.choice(np.asarray(cfg["k_choices"]), m)
+    return ns, ks, rng
+
+
+def serving_trace(cfg=SERVING, rng=None):
+    """Request stream: arrival times (s), matrix ids, nrhs, trans ('N'/'T'), mixed flags."""
+    rng = np.random.default_rng(cfg["seed"] + 1000) if rng is None else rng
+    r = cfg["requests"]
+    ranks = np.arange(1, cfg["matrices"] + 1, dtype=np.float64)
+    pz = ranks ** (-cfg["zipf"])
+    pz /= pz.sum()
+    arrivals = np.cumsum(rng.exponential(1.0 / cfg["rate"], r))
+    mids = rng.choice(cfg["matrices"], size=r, p=pz)  # matrix id = popularity rank - 1
+    nrhs = rng.integers(1, cfg["nrhs_max"] + 1, r)
+    trans = np.where(rng.random(r) < cfg["trans_t"], "T", "N")
+    mixed = rng.random(r) < cfg["mixed"]
+    return arrivals, mids, nrhs, trans, mixed
+
+
+def make_band_torch(n, kl, ku, seed, dd=1.1, device="cuda"):
+    """A band drawn on `device` with torch's generator (U[-1, 1], zero outside the matrix,
+    diagonal = dd x row off-diagonal |.| sum, as make_band).  Used where a catalogue of
+    hundreds of matrices is generated in device memory; its stream differs from make_band's."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    ldab = kl + ku + 1
+    band = torch.rand((n, ldab), generator=g, dtype=torch.float64, device=device) * 2.0 - 1.0
+    tot = torch.zeros(n, dtype=torch.float64, device=device)
+    for d in range(ldab):
+        off = d - ku  # A(j+off, j) = band[j, d]
+        if off < 0:
+            band[: min(n, -off), d] = 0.0
+        elif off > 0:
+            band[max(0, n - off):, d] = 0.0
+        if d == ku:
+            continue
+        if off >= 0:
+            tot[off:] += band[: n - off, d].abs()
+        else:
+            tot[: n + off] += band[-off:, d].abs()
+    band[:, ku] = dd * tot
+    return band

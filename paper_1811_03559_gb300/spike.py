@@ -43,13 +43,14 @@ class SpikeOptions(ctypes.Structure):
 EXPORTS = ["spike_plan", "spike_factor", "spike_factor_ex", "spike_solve", "spike_solve_ex", "spike_set_stream",
            "spike_get_info", "spike_get_tips", "spike_backward_error", "spike_get_timings", "spike_kernel_launches",
            "spike_free", "spike_strerror", "spike_last_cuda_error", "spike_backward_error_noalloc",
-           "spike_measure_fp64_peak"]
+           "spike_measure_fp64_peak", "spike_factor_bytes", "spike_solve_workspace", "spike_solve_ws"]
 SPIKE_ELIMIT = -1006
 NOALLOC_MAX_NRHS = 1024
 
 FLAG_TIMING = 1
 FLAG_STAGE_BALANCE = 2
 FLAG_MIXED = 4
+FLAG_BATCH_INVARIANT = 8
 MIXED_TOL = 1e-14
 STAGES = ["factor", "setup", "block_lu", "spikes", "reduced", "solve_n", "solve_n_d", "solve_n_reduced",
           "solve_n_retrieval", "solve_t", "solve_t_s", "solve_t_reduced", "solve_t_d"]
@@ -85,6 +86,10 @@ def lib():
         L.spike_backward_error_noalloc.argtypes = [dp, i64, i64, i32, i32, dp, dp, i32, ctypes.c_char, vp, dp]
         L.spike_get_timings.argtypes = [vp, dp, i32]
         L.spike_measure_fp64_peak.argtypes = [vp, dp]
+        L.spike_factor_bytes.argtypes = [i64, i32, i32, i32, i32, ctypes.POINTER(SpikeOptions), i32,
+                                         ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        L.spike_solve_workspace.argtypes = [vp, i32, ctypes.c_char, i32, ctypes.POINTER(i64)]
+        L.spike_solve_ws.argtypes = [vp, dp, i64, i32, ctypes.c_char, vp, i64]
         L.spike_kernel_launches.argtypes = []
         L.spike_kernel_launches.restype = ctypes.c_int64
         L.spike_free.argtypes = [vp]
@@ -138,13 +143,13 @@ class Factorization:
     """A SPIKE factorization handle (spike_factor_ex); free with .free() or by garbage collection."""
 
     def __init__(self, band, kl, ku, p, pivot=0, K=0.0, nrhs_hint=0, stream=None, timing=False, n=None,
-                 stage_balance=False, mixed=False):
+                 stage_balance=False, mixed=False, batch_invariant=False):
         rows, ldab = band.shape
         self.n, self.kl, self.ku = (rows if n is None else n), kl, ku
         n = self.n
         s = _torch_stream(band) if stream is None else ctypes.c_void_p(stream)
         flags = (FLAG_TIMING if timing else 0) | (FLAG_STAGE_BALANCE if stage_balance else 0) | \
-            (FLAG_MIXED if mixed else 0)
+            (FLAG_MIXED if mixed else 0) | (FLAG_BATCH_INVARIANT if batch_invariant else 0)
         self._opt = SpikeOptions(K=K, nrhs_hint=nrhs_hint, flags=flags, stream=s)
         h = ctypes.c_void_p()
         rc = lib().spike_factor_ex(_ptr(band), ldab, n, kl, ku, p, pivot, ctypes.byref(self._opt), ctypes.byref(h))
@@ -160,6 +165,24 @@ class Factorization:
         rc = lib().spike_solve_ex(self._h, _ptr(F), self.n, nrhs, trans.encode())
         if rc != 0:
             raise SpikeError(rc, "spike_solve_ex")
+        return F
+
+    def workspace_bytes(self, nrhs, trans="N", host_f=False):
+        """Device scratch that solve_ws needs for nrhs columns (spike_solve_workspace)."""
+        out = ctypes.c_int64(0)
+        rc = lib().spike_solve_workspace(self._h, nrhs, trans.encode(), 1 if host_f else 0, ctypes.byref(out))
+        if rc != 0:
+            raise SpikeError(rc, "spike_solve_workspace")
+        return out.value
+
+    def solve_ws(self, F, workspace, trans="N"):
+        """solve() on caller-provided device scratch (a CUDA uint8 tensor of workspace_bytes)."""
+        nrhs = 1 if F.ndim == 1 else F.shape[0]
+        assert F.shape[-1] == self.n
+        rc = lib().spike_solve_ws(self._h, _ptr(F), self.n, nrhs, trans.encode(),
+                                  ctypes.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size())
+        if rc != 0:
+            raise SpikeError(rc, "spike_solve_ws")
         return F
 
     def set_stream(self, stream):
@@ -215,6 +238,18 @@ def measure_fp64_peak(stream=None):
 def kernel_launches():
     """Kernels launched by libspike.so in this process so far."""
     return int(lib().spike_kernel_launches())
+
+
+def factor_bytes(n, kl, ku, p, pivot=0, mixed=False, host_band=False, K=0.0, nrhs_hint=0, stage_balance=False):
+    """(resident, transient) device bytes of a factorization, computed without a GPU."""
+    flags = (FLAG_STAGE_BALANCE if stage_balance else 0) | (FLAG_MIXED if mixed else 0)
+    opt = SpikeOptions(K=K, nrhs_hint=nrhs_hint, flags=flags)
+    res, tr = ctypes.c_int64(0), ctypes.c_int64(0)
+    rc = lib().spike_factor_bytes(n, kl, ku, p, pivot, ctypes.byref(opt), 1 if host_band else 0, ctypes.byref(res),
+                                  ctypes.byref(tr))
+    if rc != 0:
+        raise SpikeError(rc, "spike_factor_bytes")
+    return res.value, tr.value
 
 
 def factor(band, kl, ku, p, pivot=0, **kw):

@@ -153,6 +153,21 @@ def test_gpu_backward_error_kernel_matches_oracle():
             assert be_gpu[c] == pytest.approx(be_cpu, rel=1e-6, abs=1e-30)
 
 
+@pytest.mark.parametrize("n,kl,ku,m", [(1000, 12, 9, 8), (20_011, 5, 17, 40), (50, 3, 2, 16),
+                                        (5000, 320, 320, 33), (3000, 0, 7, 9), (4099, 128, 128, 64)])
+def test_gpu_backward_error_many_columns(n, kl, ku, m):
+    """The tiled residual (8 or more right-hand sides) against the oracle's, column by column:
+    ragged row tiles, n below one tile, a band too wide for 32-column chunks, kl = 0."""
+    band, rng = inputs.make_band(n, kl, ku, seed=4, dd=1.2)
+    X = rng.uniform(-1.0, 1.0, size=(m, n))
+    F = rng.uniform(-1.0, 1.0, size=(m, n))
+    for trans in ("N", "T"):
+        be_gpu = spike.backward_error(_dev(band), kl, ku, _dev(X), _dev(F), trans)
+        for c in range(m):
+            be_cpu = metrics.backward_error(band, kl, ku, X[c:c + 1], F[c:c + 1], trans)
+            assert be_gpu[c] == pytest.approx(be_cpu, rel=1e-12), (trans, c)
+
+
 # ------------------------------------------------------------------ spike tips vs definition
 def _sub_band(band, kl, ku, s, e):
     """Band of the diagonal block A[s:e, s:e]."""

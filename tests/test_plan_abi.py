@@ -21,9 +21,13 @@ def built():
 
 
 def test_abi_exports_every_declared_symbol(built):
-    hdr = open(os.path.join(ROOT, "include", "spike.h")).read()
-    names = set(re.findall(r"\b(spike_[a-z_]+)\s*\(", hdr))
-    assert {"spike_factor", "spike_solve", "spike_free", "spike_plan"} <= names
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            hdr = open(os.path.join(ROOT, "include", h)).read()
+            names |= set(re.findall(r"\b(spike_[a-z0-9_]+)\s*\(", hdr))
+    assert {"spike_factor", "spike_solve", "spike_free", "spike_plan", "spike_server_create",
+            "spike_server_submit", "spike_solve_ws", "spike_factor_bytes"} <= names
     for nm in names:
         assert hasattr(built, nm), nm
 

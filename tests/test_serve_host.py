@@ -1,0 +1,193 @@
+"""Host logic of the serving engine, run in its scheduler-only mode (no GPU).
+
+In SPIKE_SERVE_DRYRUN a "factorization" holds the bytes spike_factor_bytes predicts
+and a "solve" copies F to X after a configurable sleep, so admission, LRU eviction,
+request merging, budget accounting and latency statistics are checked here on the
+CPU; the GPU tests run the same engine on real factorizations.
+"""
+import math
+import time
+
+import numpy as np
+import pytest
+
+from paper_1811_03559_gb300 import serve, spike
+
+
+def _band(n, k, seed=0):
+    rng = np.random.default_rng(seed)
+    b = rng.uniform(-1, 1, size=(n, 2 * k + 1))
+    b[:, k] = 10.0
+    return b
+
+
+def _reserve(n, k, p, mixed=False):
+    """Bytes the engine reserves to factor (n, k) from a host band, and keeps afterwards."""
+    res, tr = spike.factor_bytes(n, k, k, p, 0, mixed=mixed, host_band=True, nrhs_hint=16, stage_balance=True)
+    return res + tr + (1 << 20), res + (1 << 20)
+
+
+def test_roundtrip_and_counters():
+    with serve.Server(1 << 30, streams=2, max_batch_rhs=16, dryrun=True) as S:
+        for mid in range(3):
+            S.add_matrix(mid, _band(1000 + 100 * mid, 4), 4, 4)
+        rng = np.random.default_rng(1)
+        reqs = []
+        for i in range(30):
+            mid = i % 3
+            F = rng.standard_normal((1 + i % 4, 1000 + 100 * mid))
+            rid, X = S.submit(mid, F, trans="NT"[i % 2], mixed=bool(i % 5 == 0))
+            reqs.append((rid, F, X))
+        for rid, F, X in reqs:
+            assert S.wait(rid) >= 0.0
+            assert np.array_equal(X, F)
+        st = S.stats()
+        assert st["submitted"] == st["completed"] == 30 and st["failed"] == 0
+        assert st["rhs"] == sum(F.shape[0] for _, F, _ in reqs)
+        # each (matrix, precision) is factored once and stays resident
+        keys = {(i % 3, i % 5 == 0) for i in range(30)}
+        assert st["factorizations"] == len(keys) == st["resident"]
+        assert st["evictions"] == 0
+
+
+def test_waiting_requests_are_merged_per_key():
+    """One worker busy on matrix 1; meanwhile N and T requests for matrix 0 queue up.
+    The N ones are merged into one solve, the T ones into another."""
+    with serve.Server(1 << 30, streams=1, max_batch_rhs=64, dryrun=True, dryrun_solve_us=200_000) as S:
+        S.add_matrix(0, _band(500, 3), 3, 3)
+        S.add_matrix(1, _band(500, 3), 3, 3)
+        F = np.ones((1, 500))
+        r_busy, _ = S.submit(1, F)
+        time.sleep(0.05)  # the worker has taken it and is "solving"
+        ids = [S.submit(0, F, trans=t)[0] for t in "NTNTN"]
+        for r in [r_busy] + ids:
+            S.wait(r)
+        st = S.stats()
+        assert st["batches"] == 3
+        assert st["max_batch"] == 3
+
+
+def test_batch_column_cap():
+    with serve.Server(1 << 30, streams=1, max_batch_rhs=7, dryrun=True, dryrun_solve_us=100_000) as S:
+        S.add_matrix(0, _band(400, 2), 2, 2)
+        S.add_matrix(1, _band(400, 2), 2, 2)
+        r_busy, _ = S.submit(1, np.ones((1, 400)))
+        time.sleep(0.05)
+        ids = [S.submit(0, np.ones((3, 400)))[0] for _ in range(5)]  # 15 columns
+        for r in [r_busy] + ids:
+            S.wait(r)
+        st = S.stats()
+        # 3 + 3 fit under 7 columns, a third would not: batches of 2, 2, 1
+        assert st["batches"] == 1 + 3 and st["max_batch"] == 2
+
+
+def test_lru_eviction_order_and_budget():
+    n, k, p = 4000, 4, 8
+    reserve, keep = _reserve(n, k, p)
+    ws = 24 * n  # dry-run workspace + merged right-hand sides for one column
+    budget = 2 * keep + (reserve - keep) + ws + keep // 2  # room for two resident, not three
+    with serve.Server(budget, streams=1, max_batch_rhs=4, p=p, dryrun=True) as S:
+        for mid in "ABC":
+            S.add_matrix(ord(mid), _band(n, k), k, k)
+        F = np.ones((1, n))
+
+        def run(mid):
+            S.wait(S.submit(ord(mid), F)[0])
+            return S.stats()
+
+        run("A"), run("B"), run("A")
+        st = run("C")  # B is the least recently used: evicted
+        assert (st["factorizations"], st["evictions"]) == (3, 1)
+        st = run("A")  # still resident
+        assert st["factorizations"] == 3
+        st = run("B")  # C is now the least recently used
+        assert (st["factorizations"], st["evictions"]) == (4, 2)
+        assert st["peak_bytes"] <= budget
+        assert st["resident"] == 2
+
+
+def test_budget_holds_under_concurrency():
+    n, k = 3000, 6
+    reserve, keep = _reserve(n, k, 6)
+    budget = 3 * reserve + 4 * 24 * 3000 * 8
+    with serve.Server(budget, streams=4, max_batch_rhs=8, p=6, dryrun=True, dryrun_factor_us=2000,
+                      dryrun_solve_us=500) as S:
+        for mid in range(12):
+            S.add_matrix(mid, _band(n, k), k, k)
+        rng = np.random.default_rng(3)
+        ids = []
+        for i in range(300):
+            mid = int(rng.zipf(1.3)) % 12
+            rid, X = S.submit(mid, rng.standard_normal((int(rng.integers(1, 8)), n)))
+            ids.append(rid)
+        S.drain()
+        st = S.stats()
+        assert st["completed"] == 300 and st["failed"] == 0
+        assert st["peak_bytes"] <= budget
+        assert st["evictions"] > 0
+        assert st["factorizations"] == st["evictions"] + st["resident"]
+
+
+def test_request_larger_than_budget_fails_cleanly():
+    n, k = 20_000, 16
+    reserve, _ = _reserve(n, k, 10)
+    with serve.Server(reserve // 2, streams=2, p=10, dryrun=True) as S:
+        S.add_matrix(0, _band(n, k), k, k)
+        S.add_matrix(1, _band(500, 2), 2, 2)
+        rid, _ = S.submit(0, np.ones((1, n)))
+        with pytest.raises(spike.SpikeError) as e:
+            S.wait(rid)
+        assert e.value.code == spike.SPIKE_ENOMEM
+        rid2, X = S.submit(1, np.full((1, 500), 2.0))  # the server keeps serving
+        S.wait(rid2)
+        assert np.all(X == 2.0)
+        st = S.stats()
+        assert st["failed"] == 1 and st["completed"] == 1
+
+
+def test_argument_errors():
+    with serve.Server(1 << 28, dryrun=True) as S:
+        S.add_matrix(5, _band(300, 2), 2, 2, pivot=1)
+        with pytest.raises(spike.SpikeError) as e:
+            S.add_matrix(5, _band(300, 2), 2, 2)
+        assert e.value.code == -2
+        with pytest.raises(spike.SpikeError) as e:
+            S.submit(5, np.ones((1, 300)), mixed=True)  # mixed needs a non-pivoting factorization
+        assert e.value.code == spike.SPIKE_ENOTSUP
+        with pytest.raises(KeyError):
+            S.submit(6, np.ones((1, 300)))
+        with pytest.raises(spike.SpikeError):
+            S.submit(5, np.ones((1, 300)), trans="X")
+    with pytest.raises(spike.SpikeError):
+        serve.Server(0, dryrun=True)
+
+
+def test_latency_statistics_are_nearest_rank():
+    with serve.Server(1 << 30, streams=3, dryrun=True, dryrun_solve_us=300) as S:
+        for mid in range(4):
+            S.add_matrix(mid, _band(256, 2), 2, 2)
+        for i in range(101):
+            S.submit(i % 4, np.ones((1, 256)))
+            if i % 10 == 0:
+                time.sleep(0.002)
+        S.drain()
+        st = S.stats()
+        lat = np.sort(S.latencies())
+        assert len(lat) == 101
+        rank = lambda q: lat[max(1, math.ceil(q * len(lat))) - 1]
+        assert st["p50_ms"] == rank(0.5) and st["p99_ms"] == rank(0.99) and st["max_ms"] == lat[-1]
+        assert st["mean_ms"] == pytest.approx(lat.mean())
+        assert st["solves_per_s"] == pytest.approx(101 / st["span_s"])
+
+
+def test_workers_run_concurrently():
+    solve_us = 150_000
+    with serve.Server(1 << 30, streams=4, dryrun=True, dryrun_solve_us=solve_us) as S:
+        for mid in range(4):
+            S.add_matrix(mid, _band(256, 2), 2, 2)
+        t0 = time.perf_counter()
+        ids = [S.submit(mid, np.ones((1, 256)))[0] for mid in range(4)]
+        for r in ids:
+            S.wait(r)
+        dt = time.perf_counter() - t0
+        assert dt < 3.5 * solve_us * 1e-6  # four solves overlapped, not serialised (4x)
