@@ -202,6 +202,26 @@ def load_traffic():
     return d.get("dram_bytes_per_launch_full"), d
 
 
+def tuning_leg(band, k, nrhs):
+    """The load-balancing constant K measured on one block (Sec. 3.3), a partition-ratio sweep
+    at p = 148 (the paper's ratio experiment), and the fastest worker count (spike_tune)."""
+    from paper_1811_03559_gb300 import spike
+    ps = [128, 148, 152, 192]
+    rs = [1.0, 1.5, 2.0, 2.5, 3.0, 4.0]
+    t0 = time.perf_counter()
+    res, table = spike.tune(band, k, k, nrhs, ps, r13_candidates=rs, nsolves=2)
+    cols = ["paper_ratio_measured_K", "stage_balance"] + ["R13=%g" % r for r in rs]
+    info_formula, _, _ = spike.plan(band.shape[0], k, k, 148, K=res["K_measured"], nrhs_hint=nrhs)
+    return {"K_measured": res["K_measured"],
+            "formula_R13_at_measured_K": info_formula["R13"],
+            "best": {"p": res["best_p"], "mode": ["paper_ratio", "stage_balance", "explicit_R13"][res["best_mode"]],
+                     "R13": res["best_R13"], "ms": res["best_ms"]},
+            "default_ms": res["default_ms"], "columns": cols,
+            "table_ms": {str(p): [round(float(x), 2) for x in row] for p, row in zip(ps, table)},
+            "step": "factor + 2 N solves, nrhs = %d (zero right-hand sides; times do not depend on values)" % nrhs,
+            "seconds": time.perf_counter() - t0}
+
+
 def serving_leg(dev, requests, streams, max_batch, passes=2, seed=None):
     """Many-matrix serving workload (inputs.SERVING) through the native serving engine.
 
@@ -327,6 +347,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer (e2e) leg, e.g. under a profiler")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision variant")
     ap.add_argument("--no-serve", action="store_true", help="skip the many-matrix serving leg")
+    ap.add_argument("--no-tune", action="store_true", help="skip the partition tuning leg")
     ap.add_argument("--serve-requests", type=int, default=10_000)
     ap.add_argument("--serve-streams", type=int, default=8)
     ap.add_argument("--serve-batch", type=int, default=64)
@@ -493,6 +514,9 @@ def main():
             e2e_s += dt
     e2e_step_s = e2e_s / args.e2e_steps if args.e2e_steps > 0 else float("nan")
 
+    tuning = None
+    if not args.no_tune and rank == 0:
+        tuning = tuning_leg(band, k, m)
     serving = None
     if not args.no_serve and rank == 0:
         serving = serving_leg(dev, args.serve_requests, args.serve_streams, args.serve_batch, args.serve_passes)
@@ -532,6 +556,7 @@ def main():
                 "ms_per_step": e2e_step_s * 1e3},
         "variants": {"mixed_fp32_fp64_refinement": mixed},
         "serving": serving,
+        "tuning": tuning,
         "gpu_launches": int(launches),
         "clocks": clocks,
     }

@@ -114,7 +114,10 @@ typedef struct {
   int32_t flags;
   /* cudaStream_t for all work of the handle; NULL = the legacy default stream. */
   void *stream;
-  int64_t reserved[4];
+  /* > 0: use this partition ratio R13 = n1/n3 (R12 = R13/2) instead of the formula or
+   * SPIKE_FLAG_STAGE_BALANCE -- for ratio sweeps and tuned configurations (Sec. 3.3). */
+  double R13;
+  int64_t reserved[3];
 } spike_options;
 
 /* Description of a partition plan / factorization. */
@@ -225,6 +228,37 @@ int spike_get_timings(spike_handle h, double *ms, int count);
  * per SM), in TFLOP/s (2 flop per FMA).  The roofline denominator of the FP64
  * kernels.  Synchronises `stream`. */
 int spike_measure_fp64_peak(void *stream, double *tflops);
+
+/* The machine constant K = K2/K1 of the load-balancing model (Sec. 3.3: solve cost per
+ * row and right-hand side over factorization cost per row and band column), measured
+ * as the paper prescribes: (solve time) / (factorization time) of one block with
+ * nrhs = k, here the leading min(n, 65536) rows of `band` (device pointer) factored
+ * as a single block (one CTA: block LU, then the two full sweeps of the solve).  The
+ * run is repeated once and the second timing kept.  Synchronises `stream`. */
+int spike_measure_K(const double *band, int64_t ldab, int64_t n, int kl, int ku, void *stream, double *K);
+
+/* Result of spike_tune. */
+typedef struct {
+  double K_measured;    /* spike_measure_K on the same matrix */
+  int32_t best_p;       /* fastest worker count among the candidates */
+  int32_t best_mode;    /* 0: the paper's ratio with K_measured, 1: SPIKE_FLAG_STAGE_BALANCE, 2: explicit R13 */
+  double best_R13;      /* partition ratio of the fastest configuration */
+  double best_ms;       /* its factor + nsolves solves time */
+  double default_ms;    /* p_candidates[0] with SPIKE_FLAG_STAGE_BALANCE */
+  int32_t tried;        /* configurations timed */
+  int32_t reserved;
+} spike_tune_result;
+
+/* Time factor + nsolves N solves of nrhs columns on the caller's matrix (device band,
+ * non-pivoting) for every worker count in p_candidates and every sizing: the paper's
+ * ratio with the measured K, stage balance, and each explicit R13 of r13_candidates
+ * (nr entries, may be 0), after one untimed warm-up run.  table_ms (may be NULL)
+ * receives np x (2 + nr) milliseconds, row-major.  The timings are CUDA events on
+ * `stream` around the whole calls (factor's host round trips included).  Allocates
+ * n x nrhs doubles of right-hand sides.  Synchronises `stream`. */
+int spike_tune(const double *band, int64_t ldab, int64_t n, int kl, int ku, int nrhs, int nsolves,
+               const int *p_candidates, int np, const double *r13_candidates, int nr, void *stream,
+               double *table_ms, spike_tune_result *out);
 
 /* Number of CUDA kernels this library has launched in the process so far. */
 int64_t spike_kernel_launches(void);

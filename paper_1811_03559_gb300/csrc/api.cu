@@ -229,7 +229,8 @@ extern "C" int spike_plan(int64_t n, int kl, int ku, int p, const spike_options 
                           int64_t *leaf_offsets, int32_t *leaf_flags) {
   if (!out) return -6;
   Plan pl;
-  const int rc = make_plan(n, kl, ku, p, opt ? opt->K : 0.0, opt ? opt->nrhs_hint : 0, opt ? opt->flags : 0, pl);
+  const int rc = make_plan(n, kl, ku, p, opt ? opt->K : 0.0, opt ? opt->nrhs_hint : 0, opt ? opt->flags : 0,
+                     opt ? opt->R13 : 0.0, pl);
   if (rc != 0) return rc;  // -1 n, -2 kl, -3 ku, -4 p, or SPIKE_ENOTSUP
   fill_info(pl, out);
   for (int i = 0; i < pl.nleaves; ++i) {
@@ -426,7 +427,8 @@ extern "C" int spike_factor_bytes(int64_t n, int kl, int ku, int p, int pivot, c
   if (!transient) return -9;
   if (pivot != 0 && pivot != 1) return -5;
   Plan pl;
-  const int rc = make_plan(n, kl, ku, p, opt ? opt->K : 0.0, opt ? opt->nrhs_hint : 0, opt ? opt->flags : 0, pl);
+  const int rc = make_plan(n, kl, ku, p, opt ? opt->K : 0.0, opt ? opt->nrhs_hint : 0, opt ? opt->flags : 0,
+                     opt ? opt->R13 : 0.0, pl);
   if (rc != 0) return rc;
   const int f32 = (opt && (opt->flags & SPIKE_FLAG_MIXED)) ? 1 : 0;
   if (f32 && pivot) return SPIKE_ENOTSUP;
@@ -454,7 +456,8 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
     return SPIKE_ENOGPU;
   }
   Plan pl;
-  int rc = make_plan(n, kl, ku, p, opt ? opt->K : 0.0, opt ? opt->nrhs_hint : 0, opt ? opt->flags : 0, pl);
+  int rc = make_plan(n, kl, ku, p, opt ? opt->K : 0.0, opt ? opt->nrhs_hint : 0, opt ? opt->flags : 0,
+                     opt ? opt->R13 : 0.0, pl);
   if (rc != 0) return map_plan_rc(rc);
   pl.pivot = pivot;
 

@@ -44,8 +44,8 @@ struct Plan {
   std::vector<std::vector<Merge>> levels;  // merge levels, applied in order
 };
 
-// Returns 0 or -(argument index) on invalid input.
-int make_plan(int64_t n, int kl, int ku, int t, double K, int nrhs_hint, int flags, Plan &out);
+// Returns 0 or -(argument index) on invalid input.  r13 > 0 overrides the partition ratio.
+int make_plan(int64_t n, int kl, int ku, int t, double K, int nrhs_hint, int flags, double r13, Plan &out);
 
 // ------------------------------------------------------- device descriptors
 

@@ -18,7 +18,7 @@
 //
 // With SPIKE_FLAG_STAGE_BALANCE the ratio is instead the paper's solve-stage limit
 // R13 = 2 (or its factorization limit when no solve is expected), which balances
-// each stage separately (see spike.h).
+// each stage separately (see spike.h); an explicit R13 (options.R13 > 0) overrides both.
 //
 // Readings where the paper is silent: sizes are floored, the remainder rows go
 // one at a time to the inner partitions starting at the second one; a 2x2
@@ -64,7 +64,7 @@ static void build_levels(Plan &pl, const std::vector<int> &part_first_leaf) {
     }
 }
 
-int make_plan(int64_t n, int kl, int ku, int t, double K, int nrhs_hint, int flags, Plan &pl) {
+int make_plan(int64_t n, int kl, int ku, int t, double K, int nrhs_hint, int flags, double r13, Plan &pl) {
   if (n < 1) return -1;
   if (kl < 0) return -2;
   if (ku < 0) return -3;
@@ -82,6 +82,7 @@ int make_plan(int64_t n, int kl, int ku, int t, double K, int nrhs_hint, int fla
   const double rho = (nrhs_hint > 0) ? (double)nrhs_hint / pl.k : 0.0;
   pl.R13 = (1.0 + 1.5 * pl.K + 2.0 * pl.K * rho) / (1.0 + pl.K * rho);
   if (flags & SPIKE_FLAG_STAGE_BALANCE) pl.R13 = (rho > 0.0) ? 2.0 : 1.0 + 1.5 * pl.K;
+  if (r13 > 0.0) pl.R13 = r13;
   pl.R12 = pl.R13 / 2.0;
   const int64_t k = pl.k;
 

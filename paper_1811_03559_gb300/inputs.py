@@ -155,3 +155,20 @@ def make_band_torch(n, kl, ku, seed, dd=1.1, device="cuda"):
             tot[: n + off] += band[-off:, d].abs()
     band[:, ku] = dd * tot
     return band
+
+
+def band_matvec_torch(band, kl, ku, X, trans="N"):
+    """band_matvec on torch tensors (any device): op(A) X in FP64, input construction only."""
+    import torch
+    n = band.shape[0]
+    Y = torch.zeros_like(X, dtype=torch.float64)
+    for d in range(kl + ku + 1):
+        off = d - ku  # A(j+off, j) = band[j, d]
+        j0, j1 = max(0, -off), min(n, n - off)
+        if j1 <= j0:
+            continue
+        if trans == "N":
+            Y[:, j0 + off:j1 + off] += band[j0:j1, d] * X[:, j0:j1]
+        else:
+            Y[:, j0:j1] += band[j0:j1, d] * X[:, j0 + off:j1 + off]
+    return Y

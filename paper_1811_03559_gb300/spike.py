@@ -35,15 +35,25 @@ class SpikeInfo(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("K_measured", ctypes.c_double), ("best_p", ctypes.c_int32), ("best_mode", ctypes.c_int32),
+                ("best_R13", ctypes.c_double), ("best_ms", ctypes.c_double), ("default_ms", ctypes.c_double),
+                ("tried", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
 class SpikeOptions(ctypes.Structure):
     _fields_ = [("K", ctypes.c_double), ("nrhs_hint", ctypes.c_int32), ("flags", ctypes.c_int32),
-                ("stream", ctypes.c_void_p), ("reserved", ctypes.c_int64 * 4)]
+                ("stream", ctypes.c_void_p), ("R13", ctypes.c_double), ("reserved", ctypes.c_int64 * 3)]
 
 
 EXPORTS = ["spike_plan", "spike_factor", "spike_factor_ex", "spike_solve", "spike_solve_ex", "spike_set_stream",
            "spike_get_info", "spike_get_tips", "spike_backward_error", "spike_get_timings", "spike_kernel_launches",
            "spike_free", "spike_strerror", "spike_last_cuda_error", "spike_backward_error_noalloc",
-           "spike_measure_fp64_peak", "spike_factor_bytes", "spike_solve_workspace", "spike_solve_ws"]
+           "spike_measure_fp64_peak", "spike_factor_bytes", "spike_solve_workspace", "spike_solve_ws",
+           "spike_measure_K", "spike_tune"]
 SPIKE_ELIMIT = -1006
 NOALLOC_MAX_NRHS = 1024
 
@@ -90,6 +100,9 @@ def lib():
                                          ctypes.POINTER(i64), ctypes.POINTER(i64)]
         L.spike_solve_workspace.argtypes = [vp, i32, ctypes.c_char, i32, ctypes.POINTER(i64)]
         L.spike_solve_ws.argtypes = [vp, dp, i64, i32, ctypes.c_char, vp, i64]
+        L.spike_measure_K.argtypes = [dp, i64, i64, i32, i32, vp, ctypes.POINTER(ctypes.c_double)]
+        L.spike_tune.argtypes = [dp, i64, i64, i32, i32, i32, i32, vp, i32, vp, i32, vp, vp,
+                                 ctypes.POINTER(TuneResult)]
         L.spike_kernel_launches.argtypes = []
         L.spike_kernel_launches.restype = ctypes.c_int64
         L.spike_free.argtypes = [vp]
@@ -125,10 +138,10 @@ def _torch_stream(x):
     return ctypes.c_void_p(0)
 
 
-def plan(n, kl, ku, p, K=0.0, nrhs_hint=0, stage_balance=False):
+def plan(n, kl, ku, p, K=0.0, nrhs_hint=0, stage_balance=False, R13=0.0):
     """Partition plan (Sec. 3.1, 3.3) without a GPU: (info dict, block offsets, block flags)."""
     info = SpikeInfo()
-    opt = SpikeOptions(K=K, nrhs_hint=nrhs_hint, flags=FLAG_STAGE_BALANCE if stage_balance else 0)
+    opt = SpikeOptions(K=K, nrhs_hint=nrhs_hint, flags=FLAG_STAGE_BALANCE if stage_balance else 0, R13=R13)
     offs = np.zeros(p + 2, dtype=np.int64)
     flags = np.zeros(p + 2, dtype=np.int32)
     rc = lib().spike_plan(n, kl, ku, p, ctypes.byref(opt), ctypes.byref(info), offs.ctypes.data_as(ctypes.c_void_p),
@@ -143,14 +156,14 @@ class Factorization:
     """A SPIKE factorization handle (spike_factor_ex); free with .free() or by garbage collection."""
 
     def __init__(self, band, kl, ku, p, pivot=0, K=0.0, nrhs_hint=0, stream=None, timing=False, n=None,
-                 stage_balance=False, mixed=False, batch_invariant=False):
+                 stage_balance=False, mixed=False, batch_invariant=False, R13=0.0):
         rows, ldab = band.shape
         self.n, self.kl, self.ku = (rows if n is None else n), kl, ku
         n = self.n
         s = _torch_stream(band) if stream is None else ctypes.c_void_p(stream)
         flags = (FLAG_TIMING if timing else 0) | (FLAG_STAGE_BALANCE if stage_balance else 0) | \
             (FLAG_MIXED if mixed else 0) | (FLAG_BATCH_INVARIANT if batch_invariant else 0)
-        self._opt = SpikeOptions(K=K, nrhs_hint=nrhs_hint, flags=flags, stream=s)
+        self._opt = SpikeOptions(K=K, nrhs_hint=nrhs_hint, flags=flags, stream=s, R13=R13)
         h = ctypes.c_void_p()
         rc = lib().spike_factor_ex(_ptr(band), ldab, n, kl, ku, p, pivot, ctypes.byref(self._opt), ctypes.byref(h))
         self._h = h
@@ -250,6 +263,31 @@ def factor_bytes(n, kl, ku, p, pivot=0, mixed=False, host_band=False, K=0.0, nrh
     if rc != 0:
         raise SpikeError(rc, "spike_factor_bytes")
     return res.value, tr.value
+
+
+def measure_K(band, kl, ku):
+    """The load-balancing constant K (Sec. 3.3) measured on the leading block of a device band."""
+    n, ldab = band.shape
+    out = ctypes.c_double(0.0)
+    rc = lib().spike_measure_K(_ptr(band), ldab, n, kl, ku, _torch_stream(band), ctypes.byref(out))
+    if rc != 0:
+        raise SpikeError(rc, "spike_measure_K")
+    return out.value
+
+
+def tune(band, kl, ku, nrhs, p_candidates, r13_candidates=(), nsolves=2):
+    """spike_tune: (result dict, table ms array of shape (len(p_candidates), 2 + len(r13_candidates)))."""
+    n, ldab = band.shape
+    ps = np.asarray(p_candidates, dtype=np.int32)
+    rs = np.asarray(r13_candidates, dtype=np.float64)
+    table = np.zeros((len(ps), 2 + len(rs)))
+    res = TuneResult()
+    rc = lib().spike_tune(_ptr(band), ldab, n, kl, ku, nrhs, nsolves, ps.ctypes.data_as(ctypes.c_void_p), len(ps),
+                          rs.ctypes.data_as(ctypes.c_void_p) if len(rs) else None, len(rs), _torch_stream(band),
+                          table.ctypes.data_as(ctypes.c_void_p), ctypes.byref(res))
+    if rc != 0:
+        raise SpikeError(rc, "spike_tune")
+    return res.as_dict(), table
 
 
 def factor(band, kl, ku, p, pivot=0, **kw):

@@ -307,3 +307,19 @@ def test_full_size_k128(p):
         be = metrics.backward_error(pr["band"], k, k, Xh, F, trans)
         assert be <= BERR
         assert np.all(np.isfinite(Xh[:, rows]))
+
+
+def test_gpu_measure_K_and_tune():
+    """The machine constant K (Sec. 3.3) measured on one block, and the timed search: the best
+    configuration is the minimum of the returned table and the table is complete."""
+    n, k = 200_000, 32
+    pr = inputs.make_problem(n, k, k, 1, seed=9, dd=1.1)
+    bd = _dev(pr["band"])
+    K = spike.measure_K(bd, k, k)
+    assert 0.2 < K < 20.0
+    res, table = spike.tune(bd, k, k, 8, [16, 64], r13_candidates=[1.5, 3.0], nsolves=1)
+    assert res["tried"] == table.size == 8 and np.all(table > 0)
+    assert res["best_ms"] == pytest.approx(table.min())
+    assert res["best_p"] in (16, 64) and res["K_measured"] > 0
+    i, c = np.unravel_index(np.argmin(table), table.shape)
+    assert res["best_p"] == [16, 64][i] and res["best_mode"] == min(c, 2)

@@ -89,3 +89,28 @@ def test_pivoting_workload(k):
         bo = metrics.backward_error(pr["band"], k, k, xo, F, trans)
         # forward error is governed by the conditioning: compare with the oracle's own
         assert metrics.forward_error(X, xo) <= max(1e-9, 1e3 * cond * max(be, bo)), (trans, cond)
+
+
+@pytest.mark.parametrize("k,p,mixed", [(64, 152, False), (64, 148, True), (256, 148, False), (256, 152, True)])
+def test_mixed_precision_workload(k, p, mixed):
+    """n = 2^20, DD 1.05, k in {64, 256}, p = SM count (152) or 148, nrhs in {1, 32, 256}, N and T,
+    FP64 and mixed (FP32 blocks + FP64 refinement): backward error <= 1e-13 and forward error
+    <= 1e-9 against the manufactured solution, both evaluated on the device."""
+    n, dd = 1 << 20, 1.05
+    band, rng = inputs.make_band(n, k, k, seed=3, dd=dd)
+    bd = _dev(band)
+    fac = spike.factor(bd, k, k, p, 0, nrhs_hint=32, mixed=mixed, stage_balance=True)
+    assert fac.info()["boosts"] == 0
+    for m in (1, 32, 256):
+        xs = torch.from_numpy(rng.uniform(-1.0, 1.0, size=(m, n))).cuda()
+        for trans in ("N", "T"):
+            F = inputs.band_matvec_torch(bd, k, k, xs, trans)
+            X = F.clone()
+            fac.solve(X, trans)
+            be = spike.backward_error(bd, k, k, X, F, trans)
+            assert be.max() <= BERR, (m, trans, be.max())
+            fe = ((X - xs).abs().amax(dim=1) / xs.abs().amax(dim=1)).max().item()
+            assert fe <= FERR_DD, (m, trans, fe)
+            if mixed:
+                assert fac.info()["refine_steps"] <= 4
+    fac.free()

@@ -117,3 +117,15 @@ def test_stage_balance_uses_paper_limits(built):
     assert abs(sizes[0] - 2 * info["n3"]) <= 1 and abs(sizes[1] + sizes[2] - 2 * info["n3"]) <= 2
     f, _, _ = spike.plan(1_048_576, 128, 128, 148, K=4 / 3, nrhs_hint=0, stage_balance=True)
     assert f["R13"] == pytest.approx(3.0)
+
+
+@pytest.mark.parametrize("r13", [1.0, 1.7, 3.0])
+def test_explicit_ratio_override(built, r13):
+    """options.R13 > 0 replaces both the formula and the stage-balance choice (Sec. 3.3 sizing
+    with a given ratio): n1 / n3 = R13 and n2 = 2 n3 up to the integer rounding."""
+    for sb in (False, True):
+        info, offs, flags = spike.plan(1 << 20, 16, 16, 148, nrhs_hint=64, stage_balance=sb, R13=r13)
+        assert info["R13"] == r13 and info["R12"] == pytest.approx(r13 / 2)
+        assert abs(info["n1"] / info["n3"] - r13) < 1e-3
+        assert abs(info["n2"] - 2 * info["n3"]) <= 1
+        assert offs[-1] == 1 << 20
