@@ -72,6 +72,11 @@ extern "C" {
  * mixed-precision refinement stops per column.  Lets independent requests be merged
  * into one solve without changing any result (the serving engine sets it). */
 #define SPIKE_FLAG_BATCH_INVARIANT 8
+/* Mixed-precision handles of a DEVICE band: read the caller's band for the FP64
+ * residuals instead of keeping a copy (saves 8 n (kl+ku+1) bytes per handle).  The
+ * band must then stay valid and unchanged until spike_free.  Ignored for host bands
+ * and FP64 handles. */
+#define SPIKE_FLAG_BORROW_BAND 16
 #define SPIKE_MIXED_TOL 1e-14
 #define SPIKE_MIXED_MAX_STEPS 10
 
@@ -117,7 +122,10 @@ typedef struct {
   /* > 0: use this partition ratio R13 = n1/n3 (R12 = R13/2) instead of the formula or
    * SPIKE_FLAG_STAGE_BALANCE -- for ratio sweeps and tuned configurations (Sec. 3.3). */
   double R13;
-  int64_t reserved[3];
+  /* SPIKE_FLAG_MIXED: stop refining a column once its FP64 backward error is <= this
+   * (<= 0 selects SPIKE_MIXED_TOL). */
+  double refine_tol;
+  int64_t reserved[2];
 } spike_options;
 
 /* Description of a partition plan / factorization. */

@@ -22,7 +22,9 @@
  * Memory accounting: the budget covers resident factorizations (spike_factor_bytes'
  * resident figure, then the handle's actual device_bytes), the factorization scratch
  * while a factorization runs, and every worker's solve workspace and batch buffer.
- * Catalogue bands are the caller's memory and are not counted.
+ * Catalogue bands are the caller's memory and are not counted; mixed-precision
+ * factorizations of device-resident bands read them for their FP64 residuals
+ * (SPIKE_FLAG_BORROW_BAND) instead of keeping copies.
  *
  * Threading: all entry points may be called from any host thread.
  */
@@ -48,7 +50,7 @@ typedef struct {
   int64_t budget_bytes;    /* device bytes for factorizations, their scratch and the workspaces (> 0) */
   int32_t streams;         /* workers (one host thread + one CUDA stream each), >= 1 */
   int32_t max_batch_rhs;   /* most right-hand sides merged into one solve, >= 1 */
-  int32_t p;               /* worker count t of each factorization; 0: min(148, max(1, n / (8k))) */
+  int32_t p;               /* worker count t of each factorization; 0: min(max(4, 2 SMs / streams), max(1, n / (16k))) */
   int32_t nrhs_hint;       /* expected columns per solve, for partition sizing (0: 16) */
   double K;                /* balance constant (<= 0: library default) */
   int32_t flags;           /* SPIKE_SERVE_* */
@@ -97,6 +99,10 @@ int64_t spike_server_submit(spike_server s, int64_t matrix_id, const double *F, 
  * the factorization or solve that served it); *latency_ms (may be NULL) receives
  * submit-to-completion time.  -2 for an unknown request id. */
 int spike_server_wait(spike_server s, int64_t req, double *latency_ms);
+
+/* Non-blocking: 0 and *latency_ms when request `req` has completed, 1 while it has not,
+ * -2 for an unknown id. */
+int spike_server_request_latency(spike_server s, int64_t req, double *latency_ms);
 
 /* Block until every submitted request has completed. */
 int spike_server_drain(spike_server s);

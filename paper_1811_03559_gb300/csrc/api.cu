@@ -139,6 +139,7 @@ struct spike_ctx {
   size_t es = sizeof(double);
   double *band64 = nullptr;                // mixed: FP64 copy of the band for the refinement residuals
   int64_t ldab64 = 0;
+  double refine_tol = SPIKE_MIXED_TOL;     // mixed: per-column stopping backward error
   int last_iters = 0;                      // mixed: refinement steps of the last solve
   double last_berr = 0.0;                  //        and its final backward error
   int *ipiv = nullptr, *mpiv = nullptr;
@@ -371,7 +372,10 @@ struct FactorLayout {
   std::vector<int64_t> zoff;
 };
 
-static void factor_layout(const Plan &pl, int pivot, int f32, int64_t ldab, bool band_dev, FactorLayout &L) {
+// borrow: a mixed-precision handle reads the caller's device band for its residuals
+// (SPIKE_FLAG_BORROW_BAND) instead of keeping a copy.
+static void factor_layout(const Plan &pl, int pivot, int f32, int64_t ldab, bool band_dev, bool borrow,
+                          FactorLayout &L) {
   const int64_t n = pl.n;
   const int k = pl.k, nlv = pl.nleaves;
   const size_t es = f32 ? sizeof(float) : sizeof(double);
@@ -402,7 +406,7 @@ static void factor_layout(const Plan &pl, int pivot, int f32, int64_t ldab, bool
   };
   L.o_fb = carve(es * (size_t)n * L.ldf);
   L.o_dinv = carve(es * (size_t)n);
-  L.o_b64 = f32 ? carve(sizeof(double) * (size_t)n * ldab) : 0;
+  L.o_b64 = (f32 && !(borrow && band_dev)) ? carve(sizeof(double) * (size_t)n * ldab) : 0;
   L.o_ipiv = pivot ? carve(sizeof(int) * (size_t)n) : 0;
   L.o_cpl = carve(sizeof(double) * (size_t)nlv * 2 * kk);
   L.o_spk = carve(sizeof(double) * (size_t)nspk * 2 * nlv * 2 * kk);
@@ -433,7 +437,8 @@ extern "C" int spike_factor_bytes(int64_t n, int kl, int ku, int p, int pivot, c
   const int f32 = (opt && (opt->flags & SPIKE_FLAG_MIXED)) ? 1 : 0;
   if (f32 && pivot) return SPIKE_ENOTSUP;
   FactorLayout L;
-  factor_layout(pl, pivot, f32, (int64_t)kl + ku + 1, host_band == 0, L);
+  factor_layout(pl, pivot, f32, (int64_t)kl + ku + 1, host_band == 0,
+                (opt && (opt->flags & SPIKE_FLAG_BORROW_BAND)) != 0, L);
   *resident = (int64_t)L.mem;
   *transient = (int64_t)L.scr;
   return 0;
@@ -471,6 +476,7 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
   c->timing = opt && (opt->flags & SPIKE_FLAG_TIMING);
   c->f32 = (opt && (opt->flags & SPIKE_FLAG_MIXED)) ? 1 : 0;
   c->invariant = (opt && (opt->flags & SPIKE_FLAG_BATCH_INVARIANT)) ? 1 : 0;
+  if (opt && opt->refine_tol > 0.0) c->refine_tol = opt->refine_tol;
   c->es = c->f32 ? sizeof(float) : sizeof(double);
   if (c->f32 && pivot) {
     delete c;
@@ -492,7 +498,8 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
 
   const bool band_dev = is_device_ptr(band);
   FactorLayout FL;
-  factor_layout(pl, pivot, c->f32, ldab, band_dev, FL);
+  const bool borrow = c->f32 && band_dev && opt && (opt->flags & SPIKE_FLAG_BORROW_BAND);
+  factor_layout(pl, pivot, c->f32, ldab, band_dev, borrow, FL);
   c->dofs = FL.dofs;
   c->ldf = FL.ldf;
   const std::vector<int64_t> &zoff = FL.zoff;
@@ -536,7 +543,7 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
   c->fbc = c->mem + o_fb;
   c->dinvc = c->mem + o_dinv;
   if (c->f32) {
-    c->band64 = (double *)(c->mem + o_b64);
+    c->band64 = borrow ? const_cast<double *>(band) : (double *)(c->mem + o_b64);
     c->ldab64 = ldab;
   }
   c->ipiv = pivot ? (int *)(c->mem + o_ipiv) : nullptr;
@@ -593,7 +600,8 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
   }
   if (c->timing) cudaEventRecord(c->fev[0], s);
   // 1. repack the band into per-leaf LU storage; couplings; Z right-hand sides
-  if (c->f32 && cudaMemcpyAsync(c->band64, dband, sizeof(double) * (size_t)n * ldab, cudaMemcpyDeviceToDevice, s) !=
+  if (c->f32 && !borrow &&
+      cudaMemcpyAsync(c->band64, dband, sizeof(double) * (size_t)n * ldab, cudaMemcpyDeviceToDevice, s) !=
                     cudaSuccess) {
     g_cuda_err = "band copy";
     return fail2(SPIKE_ECUDA);
@@ -1270,7 +1278,7 @@ static int solve_impl(spike_handle h, double *F, int64_t ldf, int nrhs, char tra
         const double be = (an > 0 && x > 0) ? r / (an * x) : (r == 0 ? 0.0 : INFINITY);
         worst = std::max(worst, be);
         if (!act[col]) continue;
-        if (be > SPIKE_MIXED_TOL) {
+        if (be > c->refine_tol) {
           any = true;
         } else {
           act[col] = 0;

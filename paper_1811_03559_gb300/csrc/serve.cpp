@@ -75,6 +75,7 @@ struct WorkerBuf {
 struct spike_server_s {
   spike_server_config cfg;
   int dev = 0;
+  int sms = 152;
   bool dry = false;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -237,7 +238,8 @@ void worker(spike_server_s *S, int w) {
       memset(&o, 0, sizeof(o));
       o.K = S->cfg.K;
       o.nrhs_hint = S->cfg.nrhs_hint > 0 ? S->cfg.nrhs_hint : 16;
-      o.flags = SPIKE_FLAG_STAGE_BALANCE | SPIKE_FLAG_BATCH_INVARIANT | (prec ? SPIKE_FLAG_MIXED : 0);
+      o.flags = SPIKE_FLAG_STAGE_BALANCE | SPIKE_FLAG_BATCH_INVARIANT | (prec ? SPIKE_FLAG_MIXED : 0) |
+                (M.host ? 0 : SPIKE_FLAG_BORROW_BAND);
       o.stream = st;
       int64_t res = 0, tr = 0;
       rc = spike_factor_bytes(M.n, M.kl, M.ku, M.p, M.pivot, &o, M.host ? 1 : 0, &res, &tr);
@@ -373,6 +375,10 @@ extern "C" int spike_server_create(const spike_server_config *cfg, spike_server 
       return SPIKE_ENOGPU;
     }
     cudaGetDevice(&S->dev);
+    if (cudaDeviceGetAttribute(&S->sms, cudaDevAttrMultiProcessorCount, S->dev) != cudaSuccess) {
+      cudaGetLastError();
+      S->sms = 152;
+    }
     // keep freed blocks of the stream-ordered allocator cached up to the budget, so
     // evictions and re-factorizations reuse memory instead of remapping it
     if (cudaDeviceGetDefaultMemPool(&S->pool, S->dev) == cudaSuccess) {
@@ -415,8 +421,13 @@ extern "C" int spike_server_add_matrix(spike_server S, int64_t id, const double 
   M.kl = kl;
   M.ku = ku;
   M.pivot = pivot;
+  // Default worker count: blocks of at least 16k rows, and no more blocks than about two
+  // per SM for each stream (concurrent requests share the GPU).  Fewer blocks also mean
+  // fewer merge levels, whose spike tips (4k^2 per block per level) dominate the
+  // footprint of small-n/k factorizations.
   const int64_t k = std::max(1, std::max(kl, ku));
-  M.p = S->cfg.p > 0 ? S->cfg.p : (int)std::min<int64_t>(148, std::max<int64_t>(1, n / (8 * k)));
+  const int64_t cap = std::max<int64_t>(4, 2 * (int64_t)S->sms / S->cfg.streams);
+  M.p = S->cfg.p > 0 ? S->cfg.p : (int)std::min<int64_t>(cap, std::max<int64_t>(1, n / (16 * k)));
   if (S->dry) {
     M.host = true;
   } else {
@@ -472,6 +483,16 @@ extern "C" int spike_server_wait(spike_server S, int64_t req, double *latency_ms
   const Req &r = S->reqs[req];
   if (latency_ms) *latency_ms = 1e3 * (r.t_done - r.t_submit);
   return r.status;
+}
+
+extern "C" int spike_server_request_latency(spike_server S, int64_t req, double *latency_ms) {
+  if (!S) return -1;
+  Lock lk(S->mu);
+  if (req < 0 || req >= (int64_t)S->reqs.size()) return -2;
+  const Req &r = S->reqs[req];
+  if (!r.done) return 1;
+  if (latency_ms) *latency_ms = 1e3 * (r.t_done - r.t_submit);
+  return 0;
 }
 
 extern "C" int spike_server_drain(spike_server S) {

@@ -51,6 +51,8 @@ def _lib():
         L.spike_server_submit.restype = i64
         L.spike_server_wait.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_double)]
         L.spike_server_wait.restype = i32
+        L.spike_server_request_latency.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_double)]
+        L.spike_server_request_latency.restype = i32
         L.spike_server_drain.argtypes = [vp]
         L.spike_server_drain.restype = i32
         L.spike_server_stats_get.argtypes = [vp, ctypes.POINTER(ServerStats)]
@@ -111,6 +113,14 @@ class Server:
         if rc != 0:
             raise spike.SpikeError(rc, "request %d (%s)" % (rid, _lib().spike_server_last_error(self._h).decode()))
         return lat.value
+
+    def latency(self, rid):
+        """Latency (ms) of request rid if it has completed, else None (does not block)."""
+        lat = ctypes.c_double(0.0)
+        rc = _lib().spike_server_request_latency(self._h, rid, ctypes.byref(lat))
+        if rc < 0:
+            raise spike.SpikeError(rc, "spike_server_request_latency")
+        return lat.value if rc == 0 else None
 
     def drain(self):
         rc = _lib().spike_server_drain(self._h)

@@ -46,7 +46,8 @@ class TuneResult(ctypes.Structure):
 
 class SpikeOptions(ctypes.Structure):
     _fields_ = [("K", ctypes.c_double), ("nrhs_hint", ctypes.c_int32), ("flags", ctypes.c_int32),
-                ("stream", ctypes.c_void_p), ("R13", ctypes.c_double), ("reserved", ctypes.c_int64 * 3)]
+                ("stream", ctypes.c_void_p), ("R13", ctypes.c_double), ("refine_tol", ctypes.c_double),
+                ("reserved", ctypes.c_int64 * 2)]
 
 
 EXPORTS = ["spike_plan", "spike_factor", "spike_factor_ex", "spike_solve", "spike_solve_ex", "spike_set_stream",
@@ -61,6 +62,7 @@ FLAG_TIMING = 1
 FLAG_STAGE_BALANCE = 2
 FLAG_MIXED = 4
 FLAG_BATCH_INVARIANT = 8
+FLAG_BORROW_BAND = 16
 MIXED_TOL = 1e-14
 STAGES = ["factor", "setup", "block_lu", "spikes", "reduced", "solve_n", "solve_n_d", "solve_n_reduced",
           "solve_n_retrieval", "solve_t", "solve_t_s", "solve_t_reduced", "solve_t_d"]
@@ -156,14 +158,16 @@ class Factorization:
     """A SPIKE factorization handle (spike_factor_ex); free with .free() or by garbage collection."""
 
     def __init__(self, band, kl, ku, p, pivot=0, K=0.0, nrhs_hint=0, stream=None, timing=False, n=None,
-                 stage_balance=False, mixed=False, batch_invariant=False, R13=0.0):
+                 stage_balance=False, mixed=False, batch_invariant=False, R13=0.0, borrow_band=False,
+                 refine_tol=0.0):
         rows, ldab = band.shape
         self.n, self.kl, self.ku = (rows if n is None else n), kl, ku
         n = self.n
         s = _torch_stream(band) if stream is None else ctypes.c_void_p(stream)
         flags = (FLAG_TIMING if timing else 0) | (FLAG_STAGE_BALANCE if stage_balance else 0) | \
-            (FLAG_MIXED if mixed else 0) | (FLAG_BATCH_INVARIANT if batch_invariant else 0)
-        self._opt = SpikeOptions(K=K, nrhs_hint=nrhs_hint, flags=flags, stream=s, R13=R13)
+            (FLAG_MIXED if mixed else 0) | (FLAG_BATCH_INVARIANT if batch_invariant else 0) | \
+            (FLAG_BORROW_BAND if borrow_band else 0)
+        self._opt = SpikeOptions(K=K, nrhs_hint=nrhs_hint, flags=flags, stream=s, R13=R13, refine_tol=refine_tol)
         h = ctypes.c_void_p()
         rc = lib().spike_factor_ex(_ptr(band), ldab, n, kl, ku, p, pivot, ctypes.byref(self._opt), ctypes.byref(h))
         self._h = h
@@ -253,9 +257,11 @@ def kernel_launches():
     return int(lib().spike_kernel_launches())
 
 
-def factor_bytes(n, kl, ku, p, pivot=0, mixed=False, host_band=False, K=0.0, nrhs_hint=0, stage_balance=False):
+def factor_bytes(n, kl, ku, p, pivot=0, mixed=False, host_band=False, K=0.0, nrhs_hint=0, stage_balance=False,
+                 borrow_band=False):
     """(resident, transient) device bytes of a factorization, computed without a GPU."""
-    flags = (FLAG_STAGE_BALANCE if stage_balance else 0) | (FLAG_MIXED if mixed else 0)
+    flags = (FLAG_STAGE_BALANCE if stage_balance else 0) | (FLAG_MIXED if mixed else 0) | \
+        (FLAG_BORROW_BAND if borrow_band else 0)
     opt = SpikeOptions(K=K, nrhs_hint=nrhs_hint, flags=flags)
     res, tr = ctypes.c_int64(0), ctypes.c_int64(0)
     rc = lib().spike_factor_bytes(n, kl, ku, p, pivot, ctypes.byref(opt), 1 if host_band else 0, ctypes.byref(res),

@@ -108,7 +108,8 @@ def test_eviction_refactors_identically():
     round-robin requests evict and re-factor; every result is still right, and
     re-factoring reproduces the same bits."""
     n, k = 20_000, 32
-    p = min(148, max(1, n // (8 * k)))
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    p = min(max(4, 2 * sms // 1), max(1, n // (16 * k)))  # the engine's rule for one stream
     res, tr = spike.factor_bytes(n, k, k, p, 0, host_band=True, nrhs_hint=16, stage_balance=True)
     reserve, keep = res + tr + (1 << 20), res + (2 << 20)
     budget = reserve + keep + (8 << 20)  # + workspace and batch buffer for 2 columns

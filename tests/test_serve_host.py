@@ -191,3 +191,16 @@ def test_workers_run_concurrently():
             S.wait(r)
         dt = time.perf_counter() - t0
         assert dt < 3.5 * solve_us * 1e-6  # four solves overlapped, not serialised (4x)
+
+
+def test_request_latency_query_does_not_block():
+    with serve.Server(1 << 30, streams=1, dryrun=True, dryrun_solve_us=150_000) as S:
+        S.add_matrix(0, _band(300, 2), 2, 2)
+        rid, _ = S.submit(0, np.ones((1, 300)))
+        t0 = time.perf_counter()
+        assert S.latency(rid) is None  # still running
+        assert time.perf_counter() - t0 < 0.05
+        lat = S.wait(rid)
+        assert S.latency(rid) == lat
+        with pytest.raises(spike.SpikeError):
+            S.latency(12345)
