@@ -317,6 +317,21 @@ def serving_leg(dev, requests, streams, max_batch, passes=2, seed=None):
     scale = max(1.0, (requests / arrivals[-1]) / (0.6 * cap_rate))
     out["sustainable"] = dict(replay(scale), phase="60 % of measured capacity")
     out["gpu_launches"] = int(spike.kernel_launches() - launches0)
+    # baseline: the same requests one at a time with no resident factorizations and no
+    # merging (FP64 factor + solve + free per request, whole GPU per request), on a sample
+    nb = min(300, requests)
+    t0 = time.perf_counter()
+    for i in range(nb):
+        n, kk, m = int(ns[mids[i]]), int(ks[mids[i]]), int(nrhs[i])
+        fac = spike.Factorization(bands[int(mids[i])], kk, kk, min(148, max(1, n // (8 * kk))), nrhs_hint=m,
+                                  stage_balance=True, stream=0)
+        X = np.array(fbuf[: n * m].reshape(m, n))
+        fac.solve(X, str(trans[i]))
+        fac.free()
+    naive = nb / (time.perf_counter() - t0)
+    out["unbatched_fp64_baseline"] = {"solves_per_s": naive, "sample_requests": nb,
+                                      "method": "per request: FP64 spike_factor + spike_solve (host F/X) + spike_free, "
+                                                "one stream, t = min(148, n/(8k)), first %d requests of the trace" % nb}
     # accuracy of served results: one request per (trans, precision) on the largest used matrix
     big = max(used, key=lambda i: ns[i] * ks[i])
     n, k = int(ns[big]), int(ks[big])
@@ -335,6 +350,7 @@ def serving_leg(dev, requests, streams, max_batch, passes=2, seed=None):
     w = out["passes"][-1]
     out.update({"p50_ms": w["p50_ms"], "p99_ms": w["p99_ms"], "solves_per_s": w["solves_per_s"],
                 "rhs_per_s": w["rhs_per_s"], "capacity_solves_per_s": cap_rate,
+                "capacity_vs_unbatched_fp64": cap_rate / naive,
                 "p50_ms_at_60pct_capacity": out["sustainable"]["p50_ms"],
                 "p99_ms_at_60pct_capacity": out["sustainable"]["p99_ms"]})
     return out
