@@ -59,16 +59,29 @@ struct Arena {
   }
 };
 
-// A batch of GEMM descriptors with tile bookkeeping.
+// A batch of GEMM descriptors with tile bookkeeping.  The tile size is chosen when the
+// batch is launched: 64 x 64 when that gives at least one tile per SM, else 32 x 32 or
+// 16 x 16 (an SM retires ~2 FP64 FMAs per clock, so a few large tiles leave the GPU idle).
 struct GemmBatch {
   std::vector<GemmDesc> d;
-  int tiles = 0;
+  int tiles = 0, tsz = 64;
   void add(GemmDesc g) {
     if (g.M <= 0 || g.N <= 0) return;
-    g.tiles_n = (g.N + GEMM_TILE - 1) / GEMM_TILE;
-    g.tile0 = tiles;
-    tiles += ((g.M + GEMM_TILE - 1) / GEMM_TILE) * g.tiles_n;
     d.push_back(g);
+  }
+  void finalize(int sms) {
+    auto count = [&](int t) {
+      long long c = 0;
+      for (auto &g : d) c += (long long)((g.M + t - 1) / t) * ((g.N + t - 1) / t);
+      return c;
+    };
+    tsz = count(64) >= sms ? 64 : (count(32) >= sms ? 32 : 16);
+    tiles = 0;
+    for (auto &g : d) {
+      g.tiles_n = (g.N + tsz - 1) / tsz;
+      g.tile0 = tiles;
+      tiles += ((g.M + tsz - 1) / tsz) * g.tiles_n;
+    }
   }
 };
 
@@ -114,10 +127,20 @@ struct TrsBatch {
     t.ncols = ncols;
     t.trans = trans;
     t.alpha = alpha;
-    t.tile0 = tiles;
-    tiles += (ncols + 15) / 16;
     maxn = std::max(maxn, n);
     d.push_back(t);
+  }
+  // right-hand-side columns per CTA: 16, or 4 when 16-column tiles would not fill the GPU
+  int cols = 16;
+  void finalize(int sms) {
+    long long c16 = 0;
+    for (auto &t : d) c16 += (t.ncols + 15) / 16;
+    cols = c16 >= sms ? 16 : 4;
+    tiles = 0;
+    for (auto &t : d) {
+      t.tile0 = tiles;
+      tiles += (t.ncols + cols - 1) / cols;
+    }
   }
 };
 
@@ -307,10 +330,11 @@ struct Pipeline {
   }
   void gemm(GemmBatch &b) {
     if (b.d.empty()) return;
+    b.finalize(device_sms());
     const size_t off = ar.put(b.d);
-    const int nd = (int)b.d.size(), tiles = b.tiles;
+    const int nd = (int)b.d.size(), tiles = b.tiles, tsz = b.tsz;
     cudaStream_t s = st;
-    ops.push_back([=](char *base) { return launch_gemm((GemmDesc *)(base + off), nd, tiles, s); });
+    ops.push_back([=](char *base) { return launch_gemm((GemmDesc *)(base + off), nd, tiles, tsz, s); });
   }
   // One stage = per leaf a first and a second sweep (a[i], b[i]; empty slots have
   // ncols == 0), run by the leaf's CTA back to back in a single launch.  Pivoted
@@ -350,10 +374,11 @@ struct Pipeline {
   }
   void trs(TrsBatch &b) {
     if (b.d.empty()) return;
+    b.finalize(device_sms());
     const size_t off = ar.put(b.d);
-    const int nd = (int)b.d.size(), tiles = b.tiles, maxn = b.maxn;
+    const int nd = (int)b.d.size(), tiles = b.tiles, maxn = b.maxn, cols = b.cols;
     cudaStream_t s = st;
-    ops.push_back([=](char *base) { return launch_getrs((TrsDesc *)(base + off), nd, tiles, maxn, s); });
+    ops.push_back([=](char *base) { return launch_getrs((TrsDesc *)(base + off), nd, tiles, maxn, cols, s); });
   }
 };
 

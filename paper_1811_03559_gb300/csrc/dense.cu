@@ -17,6 +17,23 @@ namespace spk {
 
 #define FULLMASK 0xffffffffu
 
+int device_sms() {
+  static std::atomic<int> cache[16];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) {
+    cudaGetLastError();
+    dev = 0;
+  }
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+    cudaGetLastError();
+    v = 152;
+  }
+  cache[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
+
 int smem_at_least(const void *func, size_t bytes) {
   static std::mutex mu;
   static std::unordered_map<const void *, size_t> cur;
@@ -29,13 +46,17 @@ int smem_at_least(const void *func, size_t bytes) {
 }
 
 // --------------------------------------------------------------- GEMM
-// 64 x 64 output tile per CTA, 256 threads, each a 4 x 4 sub-tile (rows ty+16u,
-// columns tx+16v), K staged through shared memory 16 at a time.  Each output is
-// accumulated in a fixed order, so a row of C gets the same bits whatever batch
-// it is computed in.
+// TS x TS output tile per CTA (TS = 64, 32 or 16), 256 threads, each a (TS/16)^2
+// sub-tile (rows ty+16u, columns tx+16v), K staged through shared memory 16 at a time.
+// One SM retires only ~2 FP64 FMAs per clock, so a 64 x 64 x 128 tile is ~0.1 ms of
+// work; batches with too few 64-tiles to fill the GPU use smaller tiles (host choice).
+// Each output is accumulated in the same fixed order for every TS, so a row of C gets
+// the same bits whatever batch or tile size it is computed in.
+template <int TS>
 __global__ void __launch_bounds__(256) k_gemm(const GemmDesc *descs, int ndesc) {
-  __shared__ double As[16][GEMM_TILE + 1];
-  __shared__ double Bs[16][GEMM_TILE + 1];
+  constexpr int R = TS / 16;
+  __shared__ double As[16][TS + 1];
+  __shared__ double Bs[16][TS + 1];
   const int tile = blockIdx.x;
   int lo = 0, hi = ndesc - 1;
   while (lo < hi) {
@@ -45,24 +66,24 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmDesc *descs, int ndesc) 
   }
   const GemmDesc D = descs[lo];
   const int t = tile - D.tile0;
-  const int i0 = (t / D.tiles_n) * GEMM_TILE, j0 = (t % D.tiles_n) * GEMM_TILE;
+  const int i0 = (t / D.tiles_n) * TS, j0 = (t % D.tiles_n) * TS;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  double acc[4][4];
+  double acc[R][R];
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+  for (int u = 0; u < R; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+    for (int v = 0; v < R; ++v) acc[u][v] = 0.0;
   const bool a_kfast = (D.a_cs == 1 || D.a_cs == -1);
   const bool b_jfast = (D.b_cs == 1 || D.b_cs == -1);
   for (int kk = 0; kk < D.K; kk += 16) {
-    for (int idx = tid; idx < 16 * GEMM_TILE; idx += 256) {
+    for (int idx = tid; idx < 16 * TS; idx += 256) {
       int i, kq;
       if (a_kfast) {
         kq = idx & 15;
         i = idx >> 4;
       } else {
-        i = idx & (GEMM_TILE - 1);
-        kq = idx >> 6;
+        i = idx % TS;
+        kq = idx / TS;
       }
       double v = 0.0;
       if (i0 + i < D.M && kk + kq < D.K) {
@@ -72,8 +93,8 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmDesc *descs, int ndesc) 
       As[kq][i] = v;
       int j, kb;
       if (b_jfast) {
-        j = idx & (GEMM_TILE - 1);
-        kb = idx >> 6;
+        j = idx % TS;
+        kb = idx / TS;
       } else {
         kb = idx & 15;
         j = idx >> 4;
@@ -88,24 +109,24 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmDesc *descs, int ndesc) 
     __syncthreads();
 #pragma unroll
     for (int kq = 0; kq < 16; ++kq) {
-      double a[4], b[4];
+      double a[R], b[R];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) a[u] = As[kq][ty + 16 * u];
+      for (int u = 0; u < R; ++u) a[u] = As[kq][ty + 16 * u];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) b[v] = Bs[kq][tx + 16 * v];
+      for (int v = 0; v < R; ++v) b[v] = Bs[kq][tx + 16 * v];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < R; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+        for (int v = 0; v < R; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
+  for (int u = 0; u < R; ++u) {
     const int i = i0 + ty + 16 * u;
     if (i >= D.M) continue;
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
+    for (int v = 0; v < R; ++v) {
       const int j = j0 + tx + 16 * v;
       if (j >= D.N) continue;
       double r = D.alpha * acc[u][v];
@@ -120,9 +141,12 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmDesc *descs, int ndesc) 
   }
 }
 
-int launch_gemm(const GemmDesc *d, int ndesc, int total_tiles, void *stream) {
+int launch_gemm(const GemmDesc *d, int ndesc, int total_tiles, int tile_size, void *stream) {
   if (ndesc <= 0 || total_tiles <= 0) return 0;
-  k_gemm<<<total_tiles, 256, 0, (cudaStream_t)stream>>>(d, ndesc);
+  const cudaStream_t st = (cudaStream_t)stream;
+  if (tile_size == 16) k_gemm<16><<<total_tiles, 256, 0, st>>>(d, ndesc);
+  else if (tile_size == 32) k_gemm<32><<<total_tiles, 256, 0, st>>>(d, ndesc);
+  else k_gemm<64><<<total_tiles, 256, 0, st>>>(d, ndesc);
   count_launch();
   return (int)cudaGetLastError();
 }
@@ -133,20 +157,22 @@ int launch_gemm(const GemmDesc *d, int ndesc, int total_tiles, void *stream) {
 // holding the largest |entry| of the column.  In shared memory when it fits.
 constexpr int GETRF_SMEM_BYTES = 160 * 1024;
 
-__global__ void __launch_bounds__(256) k_getrf(const LuDesc *descs, unsigned long long *status) {
+// smem_bytes: the dynamic shared memory this launch has; a matrix is factored there
+// only when it fits in it (the launch sizes it for the batch's largest matrix, or 0).
+__global__ void __launch_bounds__(256) k_getrf(const LuDesc *descs, unsigned long long *status, size_t smem_bytes) {
   extern __shared__ double sh[];
   const LuDesc D = descs[blockIdx.x];
   if (!D.active) return;
   const int n = D.n;
-  const bool insm = (int64_t)n * n * (int64_t)sizeof(double) <= GETRF_SMEM_BYTES;
+  const bool insm = (size_t)n * (n + 1) * sizeof(double) <= smem_bytes;
   double *A = insm ? sh : D.a;
-  const int lda = insm ? n : D.lda;
+  const int lda = insm ? n + 1 : D.lda;  // padded rows: the 16 x 16 update grid spreads over banks
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   __shared__ double s_v[8];
   __shared__ int s_i[8];
   __shared__ int s_p;
   if (insm) {
-    for (int idx = tid; idx < n * n; idx += 256) sh[idx] = D.a[(int64_t)(idx / n) * D.lda + idx % n];
+    for (int idx = tid; idx < n * n; idx += 256) sh[(idx / n) * lda + idx % n] = D.a[(int64_t)(idx / n) * D.lda + idx % n];
     __syncthreads();
   }
   for (int j = 0; j < n; ++j) {
@@ -202,41 +228,45 @@ __global__ void __launch_bounds__(256) k_getrf(const LuDesc *descs, unsigned lon
       const double rinv = 1.0 / piv;
       for (int i = j + 1 + tid; i < n; i += 256) A[(int64_t)i * lda + j] *= rinv;
       __syncthreads();
-      const int m = n - j - 1;
-      for (int idx = tid; idx < m * m; idx += 256) {
-        const int i = j + 1 + idx / m, c = j + 1 + idx % m;
-        A[(int64_t)i * lda + c] = fma(-A[(int64_t)i * lda + j], A[(int64_t)j * lda + c], A[(int64_t)i * lda + c]);
+      // rank-1 update of the trailing block: thread (ty, tx) of a 16 x 16 grid owns rows
+      // j+1+ty (+16 ...) and columns j+1+tx (+16 ...)
+      const int ty = tid >> 4, tx = tid & 15;
+      const double *urow = A + (int64_t)j * lda;
+      for (int i = j + 1 + ty; i < n; i += 16) {
+        double *row = A + (int64_t)i * lda;
+        const double l = row[j];
+        for (int c = j + 1 + tx; c < n; c += 16) row[c] = fma(-l, urow[c], row[c]);
       }
     }
     __syncthreads();
   }
   if (insm) {
-    for (int idx = tid; idx < n * n; idx += 256) D.a[(int64_t)(idx / n) * D.lda + idx % n] = sh[idx];
+    for (int idx = tid; idx < n * n; idx += 256) D.a[(int64_t)(idx / n) * D.lda + idx % n] = sh[(idx / n) * lda + idx % n];
   }
 }
 
 int launch_getrf(const LuDesc *d, int ndesc, int maxn, unsigned long long *status, void *stream) {
   if (ndesc <= 0) return 0;
-  size_t smem = (size_t)maxn * maxn * sizeof(double);
-  if (smem > (size_t)GETRF_SMEM_BYTES) smem = 0;
+  size_t smem = (size_t)maxn * (maxn + 1) * sizeof(double);
+  if (smem > (size_t)GETRF_SMEM_BYTES) smem = GETRF_SMEM_BYTES;  // the matrices that fit still use it
   if (smem > 48 * 1024) {
     cudaError_t e = (cudaError_t)smem_at_least((const void *)k_getrf, smem);
     if (e != cudaSuccess) return (int)e;
   }
-  k_getrf<<<ndesc, 256, smem, (cudaStream_t)stream>>>(d, status);
+  k_getrf<<<ndesc, 256, smem, (cudaStream_t)stream>>>(d, status, smem);
   count_launch();
   return (int)cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- GETRS
-// One CTA per (matrix, 16-column tile of B).  trans 0: M x = b with P M = L U;
+// One CTA per (matrix, TRS_COLS-column tile of B): 16 columns, or 4 when 16-column tiles
+// would leave most SMs idle (each solve is 2 n^2 FMAs per column on one SM).  trans 0: M x = b with P M = L U;
 // trans 1: M^T x = b (U^T forward, L^T backward, swaps undone in reverse).
-constexpr int TRS_COLS = 16;
 
 // SMEM_LU: the n x n factor is first copied to shared memory (row stride n + 1), so the
 // column reads of every elimination step are shared-memory broadcasts instead of strided
 // global loads; the arithmetic and its order are the same in both forms.
-template <bool SMEM_LU>
+template <bool SMEM_LU, int TRS_COLS>
 __global__ void __launch_bounds__(256) k_getrs(const TrsDesc *descs, int ndesc) {
   extern __shared__ double trs_sm[];  // [LU n x (n+1)] when SMEM_LU, then B n x TRS_COLS
   const int tile = blockIdx.x;
@@ -330,21 +360,36 @@ __global__ void __launch_bounds__(256) k_getrs(const TrsDesc *descs, int ndesc) 
   }
 }
 
-int launch_getrs(const TrsDesc *d, int ndesc, int total_tiles, int maxn, void *stream) {
+int launch_getrs(const TrsDesc *d, int ndesc, int total_tiles, int maxn, int cols, void *stream) {
   if (ndesc <= 0 || total_tiles <= 0) return 0;
-  const size_t bsm = (size_t)maxn * TRS_COLS * sizeof(double);
+  const size_t bsm = (size_t)maxn * cols * sizeof(double);
   const size_t lsm = (size_t)maxn * (maxn + 1) * sizeof(double);
+  const cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e;
   if (bsm + lsm <= 200 * 1024) {
-    e = (cudaError_t)smem_at_least((const void *)k_getrs<true>, bsm + lsm);
-    if (e != cudaSuccess) return (int)e;
-    k_getrs<true><<<total_tiles, 256, bsm + lsm, (cudaStream_t)stream>>>(d, ndesc);
-  } else {
-    if (bsm > 48 * 1024) {
-      e = (cudaError_t)smem_at_least((const void *)k_getrs<false>, bsm);
+    if (cols == 4) {
+      e = (cudaError_t)smem_at_least((const void *)k_getrs<true, 4>, bsm + lsm);
       if (e != cudaSuccess) return (int)e;
+      k_getrs<true, 4><<<total_tiles, 256, bsm + lsm, st>>>(d, ndesc);
+    } else {
+      e = (cudaError_t)smem_at_least((const void *)k_getrs<true, 16>, bsm + lsm);
+      if (e != cudaSuccess) return (int)e;
+      k_getrs<true, 16><<<total_tiles, 256, bsm + lsm, st>>>(d, ndesc);
     }
-    k_getrs<false><<<total_tiles, 256, bsm, (cudaStream_t)stream>>>(d, ndesc);
+  } else {
+    if (cols == 4) {
+      if (bsm > 48 * 1024) {
+        e = (cudaError_t)smem_at_least((const void *)k_getrs<false, 4>, bsm);
+        if (e != cudaSuccess) return (int)e;
+      }
+      k_getrs<false, 4><<<total_tiles, 256, bsm, st>>>(d, ndesc);
+    } else {
+      if (bsm > 48 * 1024) {
+        e = (cudaError_t)smem_at_least((const void *)k_getrs<false, 16>, bsm);
+        if (e != cudaSuccess) return (int)e;
+      }
+      k_getrs<false, 16><<<total_tiles, 256, bsm, st>>>(d, ndesc);
+    }
   }
   count_launch();
   return (int)cudaGetLastError();

@@ -154,10 +154,13 @@ int launch_sweeps(const SweepDesc *descs, int ncta, int per_cta, int ldf, int do
 int launch_piv_sweep(int kind, const SweepDesc *descs, int ndesc, int k, int ldf, int dofs, void *stream);
 int launch_tips0(const LeafDev *leaves, int nleaves, int k, const void *zbuf, const int64_t *zoff, double *spk,
                  void *stream, int f32);
-int launch_gemm(const GemmDesc *d, int ndesc, int total_tiles, void *stream);
-constexpr int GEMM_TILE = 64;
+// tile_size: 64, 32 or 16 (GemmDesc.tiles_n / tile0 computed for that size)
+int launch_gemm(const GemmDesc *d, int ndesc, int total_tiles, int tile_size, void *stream);
 int launch_getrf(const LuDesc *d, int ndesc, int maxn, unsigned long long *status, void *stream);
-int launch_getrs(const TrsDesc *d, int ndesc, int total_tiles, int maxn, void *stream);
+// cols: right-hand-side columns per CTA, 16 or 4 (TrsDesc.tile0 computed for that width)
+int launch_getrs(const TrsDesc *d, int ndesc, int total_tiles, int maxn, int cols, void *stream);
+// SMs of the current device (cached after the first call)
+int device_sms();
 int launch_noswap_flags(const double *const *w, int k, int nm, int *flags, void *stream);
 int launch_assemble_M(const double *const *v, const double *const *w, int k, int nm, const int *flags, double *mbuf,
                       int64_t mstride, void *stream);

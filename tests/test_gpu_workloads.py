@@ -114,3 +114,21 @@ def test_mixed_precision_workload(k, p, mixed):
             if mixed:
                 assert fac.info()["refine_steps"] <= 4
     fac.free()
+
+
+def test_pivoting_wide_interfaces():
+    """k = 80 with pivoting on N(0,1) entries: interface blocks whose W tip has entries above 1
+    take the full 2k x 2k LU (160 x 160, factored in global memory) while the others take the
+    k x k Schur complement (in shared memory), often within one merge level."""
+    n, k, p, nrhs = 40_000, 80, 8, 3
+    seed = 5
+    while True:
+        pr = inputs.make_problem(n, k, k, nrhs, seed=seed, dist="normal", dd=0.3, keep_sign=True)
+        if oracle.BandLU(pr["band"], k, k).info == 0:
+            break
+        seed += 1
+    fac, out = _run(pr, k, p, nrhs, pivot=1)
+    assert fac.status == 0
+    for trans, (X, F, be_gpu) in out.items():
+        be = metrics.backward_error(pr["band"], k, k, X, F, trans)
+        assert be <= BERR, (trans, be)
