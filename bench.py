@@ -307,7 +307,8 @@ def serving_leg(dev, requests, streams, max_batch, passes=2, seed=None):
                 "failed": st["failed"] - prev["failed"], "batches": nb, "mean_requests_per_batch": done / max(1, nb),
                 "factorizations": st["factorizations"] - prev["factorizations"],
                 "evictions": st["evictions"] - prev["evictions"], "peak_gb": st["peak_bytes"] / 1e9,
-                "max_submit_lag_ms": 1e3 * float(lag.max())}
+                "solves_over_several_matrices": st["multi_solves"] - prev["multi_solves"],
+                "max_matrices_per_solve": st["max_systems"], "max_submit_lag_ms": 1e3 * float(lag.max())}
 
     # the workload's own rate (cold, then warm), then the same trace slowed to 60 % of the
     # measured capacity, where the queue stays bounded

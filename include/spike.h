@@ -204,6 +204,26 @@ int spike_solve_workspace(spike_handle h, int nrhs, char trans, int host_f, int6
  * handle's stream has completed.  Results are those of spike_solve_ex. */
 int spike_solve_ws(spike_handle h, double *F, int64_t ldf, int nrhs, char trans, void *workspace, int64_t ws_bytes);
 
+/* Solve `count` independent systems together (batching across matrices).  The same
+ * stage of every system runs as one launch: all their blocks' sweeps in one grid, and
+ * each merge level's reduced-system products, LU solves and sums as one batched launch
+ * (levels aligned from the bottom for N, from the top for T).  Many systems of uneven
+ * n, k and nrhs then fill the GPU together with a few dozen launches in all.
+ *   hs[i]   FP64, non-pivoting handles (SPIKE_ENOTSUP for mixed-precision or pivoting
+ *           ones); a handle may appear more than once.
+ *   F[i]    device pointer, n_i x nrhs[i] with leading dimension n_i, overwritten by X_i.
+ *   trans   one of 'N' / 'T' for all systems.
+ *   workspace  device scratch of at least spike_solve_batch_workspace bytes (-8
+ *           otherwise); it must not be reused until the work on `stream` is done.
+ * Asynchronous on `stream`.  Every X_i is bitwise the result of spike_solve_ex on that
+ * system alone (the merged launches keep each output's operation order).  The handles
+ * must not be used by other threads during the call. */
+int spike_solve_batch(const spike_handle *hs, double *const *F, const int *nrhs, int count, char trans,
+                      void *stream, void *workspace, int64_t ws_bytes);
+
+/* Device scratch bytes spike_solve_batch needs for these handles and column counts. */
+int spike_solve_batch_workspace(const spike_handle *hs, const int *nrhs, int count, char trans, int64_t *bytes);
+
 /* Set the cudaStream_t used by the handle (NULL = legacy default stream). */
 int spike_set_stream(spike_handle h, void *stream);
 

@@ -11,8 +11,10 @@
  * same time are merged into one multi-column solve (continuous batching: whenever a
  * worker becomes free it takes the oldest waiting request whose matrix is not being
  * solved by another worker, plus every other waiting request with the same key, up
- * to max_batch_rhs columns).  Each worker is one host thread driving one CUDA
- * stream, so solves of different matrices run concurrently.
+ * to max_batch_rhs columns).  FP64 requests of up to batch_systems different matrices
+ * whose factorizations are resident are solved together with spike_solve_batch (every
+ * stage of all of them in shared launches).  Each worker is one host thread driving
+ * one CUDA stream, so solves run concurrently.
  *
  * A request's result does not depend on what it was batched with: the solve kernels
  * give every right-hand side the same bits whatever the batch width or position
@@ -56,7 +58,8 @@ typedef struct {
   int32_t flags;           /* SPIKE_SERVE_* */
   int32_t dryrun_factor_us;  /* SPIKE_SERVE_DRYRUN: simulated factorization time */
   int32_t dryrun_solve_us;   /* SPIKE_SERVE_DRYRUN: simulated time per solve */
-  int32_t reserved[7];
+  int32_t batch_systems;     /* most matrices whose FP64 requests share one solve (0: 16, 1: one matrix) */
+  int32_t reserved[6];
 } spike_server_config;
 
 typedef struct {
@@ -70,6 +73,9 @@ typedef struct {
   int64_t peak_bytes;       /* maximum of used_bytes */
   int32_t resident;         /* factorizations currently resident */
   int32_t max_batch;        /* most requests merged into one solve */
+  int64_t multi_solves;     /* solves that covered more than one matrix (spike_solve_batch) */
+  int32_t max_systems;      /* most matrices in one solve */
+  int32_t pad;
   double p50_ms, p99_ms, max_ms, mean_ms;  /* latency: submit -> result in X */
   double span_s;            /* first submit -> last completion */
   double solves_per_s;      /* completed requests / span_s */

@@ -12,6 +12,7 @@
 #include <climits>
 #include <cstring>
 #include <functional>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -287,6 +288,8 @@ static SweepDesc sdesc(spike_ctx *c, int i, int kind, int r0, int r1, int ncols,
   d.kind = kind;
   d.kw = (kind == UN || kind == UT) ? c->dofs : c->k;  // U has 2k superdiagonals when pivoting
   d.fixed_split = (c->invariant && c->in_solve) ? 1 : 0;
+  d.ldf = c->ldf;
+  d.dofs = c->dofs;
   d.ga = g.p;
   d.ga_rs = g.rs;
   d.ga_cs = g.cs;
@@ -308,19 +311,67 @@ static SweepDesc empty_sweep() {
 
 static std::vector<SweepDesc> e0_dummy(int n) { return std::vector<SweepDesc>(n, empty_sweep()); }
 
-// Upload an arena and run the recorded launches.
+// A step of a solve, recorded instead of launched when several systems are solved
+// together (spike_solve_batch): steps with the same key from different systems are
+// merged into one launch.  Keys are (section, level, step), increasing in each system's
+// own order, so merging in key order keeps every system's order.
+struct PhaseKey {
+  int a, b, c;
+  bool operator<(const PhaseKey &o) const {
+    if (a != o.a) return a < o.a;
+    if (b != o.b) return b < o.b;
+    return c < o.c;
+  }
+};
+struct Phase {
+  int kind = 0;  // 0 plain ops (no descriptors), 1 sweep stage, 2 GEMM, 3 LU solve, 4 block sums
+  std::vector<std::function<int(char *)>> ops;
+  std::vector<SweepDesc> a, b;
+  int a_piv = -1, b_piv = -1, k = 0;
+  GemmBatch g;
+  TrsBatch t;
+  std::vector<SumDesc> sums;
+  int64_t maxe = 0;
+};
+
+// Upload an arena and run the recorded launches.  With rec != nullptr every call is
+// instead appended to *rec as a Phase under the current key (empty ones too, so that
+// systems of the same kind record the same key sequence).
 struct Pipeline {
   cudaStream_t st = nullptr;
   int f32 = 0;  // sweep storage precision
   Arena ar;
   std::vector<std::function<int(char *)>> ops;
+  std::map<PhaseKey, Phase> *rec = nullptr;
+  int ka = 0, kb = 0, kc = 0;
+  // Zeroed-per-launch device counters for sweep stages with more blocks than SMs (merged
+  // batches): their tasks are sorted largest first and taken by persistent CTAs.
+  unsigned int *queue_base = nullptr;
+  int nqueue = 0, max_queue = 0;
+  void key(int a, int b) {
+    ka = a;
+    kb = b;
+    kc = 0;
+  }
+  Phase &next(int kind) {
+    Phase &ph = (*rec)[PhaseKey{ka, kb, kc++}];
+    ph.kind = kind;
+    return ph;
+  }
+  void op(std::function<int(char *)> f) {
+    if (rec) next(0).ops.push_back(f);
+    else ops.push_back(f);
+  }
   int run(spike_ctx *c) {
     if (!ar.h.empty()) {
       SP_TRY(ensure(&c->dargs, &c->dargs_bytes, ar.h.size(), c->stream));
       SP_CUDA(cudaMemcpyAsync(c->dargs, ar.h.data(), ar.h.size(), cudaMemcpyHostToDevice, c->stream));
     }
-    for (auto &op : ops) {
-      const int rc = op(c->dargs);
+    return run_ops(c->dargs);
+  }
+  int run_ops(char *base) {
+    for (auto &o : ops) {
+      const int rc = o(base);
       if (rc != 0) {
         g_cuda_err = std::string("kernel launch: ") + cudaGetErrorString((cudaError_t)rc);
         return SPIKE_ECUDA;
@@ -329,6 +380,10 @@ struct Pipeline {
     return 0;
   }
   void gemm(GemmBatch &b) {
+    if (rec) {
+      next(2).g = b;
+      return;
+    }
     if (b.d.empty()) return;
     b.finalize(device_sms());
     const size_t off = ar.put(b.d);
@@ -339,9 +394,19 @@ struct Pipeline {
   // One stage = per leaf a first and a second sweep (a[i], b[i]; empty slots have
   // ncols == 0), run by the leaf's CTA back to back in a single launch.  Pivoted
   // L / L^T sweeps (interleaved row swaps, a_piv / b_piv = LN or LT, -1 = none) use
-  // their own kernel and launch.
+  // their own kernel and launch.  Descriptors carry their leaf's ldf / dofs; the
+  // arguments are those of the pivoted kernel.
   void stage(std::vector<SweepDesc> &a, std::vector<SweepDesc> &b, int a_piv, int b_piv, int ldf, int dofs,
              int k) {
+    if (rec) {
+      Phase &ph = next(1);
+      ph.a = a;
+      ph.b = b;
+      ph.a_piv = a_piv;
+      ph.b_piv = b_piv;
+      ph.k = k;
+      return;
+    }
     cudaStream_t s = st;
     const int nl = (int)a.size();
     auto used = [](const std::vector<SweepDesc> &v) {
@@ -351,14 +416,29 @@ struct Pipeline {
     };
     const bool ua = used(a), ub = used(b);
     const int fp = f32;
+    const int sms = device_sms();
     if (a_piv < 0 && b_piv < 0 && ua && ub) {
+      std::vector<int> order(nl);
+      for (int i = 0; i < nl; ++i) order[i] = i;
+      unsigned int *q = nullptr;
+      if (queue_base && nl > sms && nqueue < max_queue) {
+        q = queue_base + nqueue++;
+        auto cost = [](const SweepDesc &d) {
+          return d.ncols > 0 ? (double)(d.r1 - d.r0) * d.ncols * (d.kw + NB) : 0.0;
+        };
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int x, int y) { return cost(a[x]) + cost(b[x]) > cost(a[y]) + cost(b[y]); });
+        ops.push_back([=](char *) { return (int)cudaMemsetAsync(q, 0, sizeof(unsigned int), s); });
+      }
       std::vector<SweepDesc> ab;
-      for (int i = 0; i < nl; ++i) {
+      for (int i : order) {
         ab.push_back(a[i]);
         ab.push_back(b[i]);
       }
       const size_t off = ar.put(ab);
-      ops.push_back([=](char *base) { return launch_sweeps((SweepDesc *)(base + off), nl, 2, ldf, dofs, s, fp); });
+      ops.push_back([=](char *base) {
+        return launch_sweeps((SweepDesc *)(base + off), nl, 2, ldf, dofs, s, fp, q, sms);
+      });
       return;
     }
     for (int pass = 0; pass < 2; ++pass) {
@@ -373,6 +453,10 @@ struct Pipeline {
     }
   }
   void trs(TrsBatch &b) {
+    if (rec) {
+      next(3).t = b;
+      return;
+    }
     if (b.d.empty()) return;
     b.finalize(device_sms());
     const size_t off = ar.put(b.d);
@@ -380,7 +464,60 @@ struct Pipeline {
     cudaStream_t s = st;
     ops.push_back([=](char *base) { return launch_getrs((TrsDesc *)(base + off), nd, tiles, maxn, cols, s); });
   }
+  void sums(const std::vector<SumDesc> &v, int64_t maxe) {
+    if (rec) {
+      Phase &ph = next(4);
+      ph.sums = v;
+      ph.maxe = maxe;
+      return;
+    }
+    if (v.empty()) return;
+    const size_t so = ar.put(v);
+    const int nd = (int)v.size();
+    cudaStream_t s = st;
+    ops.push_back([=](char *base) { return launch_sum_blocks((SumDesc *)(base + so), nd, maxe, s); });
+  }
+  // Add a recorded phase (possibly merged from several systems) as launches.
+  void emit(Phase &ph) {
+    switch (ph.kind) {
+      case 0:
+        for (auto &o : ph.ops) ops.push_back(o);
+        break;
+      case 1: {
+        bool any = false;
+        for (auto &d : ph.a) any = any || d.ncols > 0;
+        for (auto &d : ph.b) any = any || d.ncols > 0;
+        if (any) stage(ph.a, ph.b, ph.a_piv, ph.b_piv, 0, 0, ph.k);
+        break;
+      }
+      case 2:
+        gemm(ph.g);
+        break;
+      case 3:
+        trs(ph.t);
+        break;
+      case 4:
+        sums(ph.sums, ph.maxe);
+        break;
+    }
+  }
 };
+
+// Merge phase `src` of one system into the phase with the same key of the batch.
+static void merge_phase(Phase &dst, const Phase &src) {
+  dst.kind = src.kind;
+  for (auto &o : src.ops) dst.ops.push_back(o);
+  dst.a.insert(dst.a.end(), src.a.begin(), src.a.end());
+  dst.b.insert(dst.b.end(), src.b.begin(), src.b.end());
+  dst.a_piv = src.a_piv;
+  dst.b_piv = src.b_piv;
+  dst.k = std::max(dst.k, src.k);
+  for (auto &d : src.g.d) dst.g.d.push_back(d);
+  for (auto &d : src.t.d) dst.t.d.push_back(d);
+  dst.t.maxn = std::max(dst.t.maxn, src.t.maxn);
+  dst.sums.insert(dst.sums.end(), src.sums.begin(), src.sums.end());
+  dst.maxe = std::max(dst.maxe, src.maxe);
+}
 
 // ============================================================== factor
 static int factor_reduced_level(spike_ctx *c, int lv, char *tmp, size_t tmp_bytes);
@@ -905,18 +1042,20 @@ static void build_solve_body(spike_ctx *c, Pipeline &pp, const SolveBufs &B, int
   View none{nullptr, 0, 0};
   const bool piv = c->pivot != 0;
   auto memset_op = [&](void *p, size_t bytes) {
-    pp.ops.push_back([=](char *) { return (int)cudaMemsetAsync(p, 0, bytes, s); });
+    pp.op([=](char *) { return (int)cudaMemsetAsync(p, 0, bytes, s); });
   };
   cudaEvent_t *evs = tr ? c->tev : c->nev;
   auto mark = [&](int i) {
     if (!marks || !c->timing) return;
     cudaEvent_t e = evs[i];
-    pp.ops.push_back([=](char *) { return (int)cudaEventRecord(e, s); });
+    pp.op([=](char *) { return (int)cudaEventRecord(e, s); });
   };
+  pp.key(0, 0);
   memset_op(H, es * (size_t)n * m);
   memset_op(Y, sizeof(double) * (size_t)nlv * 2 * km);
 
   if (tr == 0) {
+    pp.key(1, 0);
     // ---------------- D stage (Eq. Dstage) with the sweep savings of Sec. 2.3
     std::vector<SweepDesc> sa(nlv, empty_sweep()), sb(nlv, empty_sweep());
     for (int i = 0; i < nlv; ++i) {
@@ -943,6 +1082,7 @@ static void build_solve_body(spike_ctx *c, Pipeline &pp, const SolveBufs &B, int
     mark(1);
     // ---------------- reduced system, levels ascending: D^[1]^-1 ... (Eqs. D1Inverse, S2Inverse)
     for (int lv = 0; lv < c->NL; ++lv) {
+      pp.key(2, lv);
       const auto &ms = c->pl.levels[lv];
       GemmBatch g1, g2, g3;
       TrsBatch ts;
@@ -977,6 +1117,7 @@ static void build_solve_body(spike_ctx *c, Pipeline &pp, const SolveBufs &B, int
     }
     mark(2);
     // ---------------- retrieval (Eqs. one/two/three): X_i = U^{-1}(L^{-1}F - L^{-1}[R_top x_top; 0; R_bot x_bot])
+    pp.key(3, 0);
     memset_op(H, es * (size_t)n * m);
     GemmBatch gc;
     std::vector<SweepDesc> sc(nlv, empty_sweep()), sd(nlv, empty_sweep());
@@ -1003,6 +1144,7 @@ static void build_solve_body(spike_ctx *c, Pipeline &pp, const SolveBufs &B, int
     pp.stage(sc, sd, piv ? LN : -1, -1, c->ldf, c->dofs, k);
   } else {
     // ---------------- transpose: S^T Y = F then D^T X = Y (Sec. 4.1, 4.2)
+    pp.key(1, 0);
     GemmBatch g0, gz;
     for (int i = 0; i < nlv; ++i) {
       const LeafDev &L = c->hl[i];
@@ -1032,7 +1174,7 @@ static void build_solve_body(spike_ctx *c, Pipeline &pp, const SolveBufs &B, int
       // the pivoted L^T sweep runs in place: copy w into H first
       pp.stage(sa, e0, -1, -1, c->ldf, c->dofs, k);
       const size_t bytes = es * (size_t)n * m;
-      pp.ops.push_back([=](char *) { return (int)cudaMemcpyAsync(H, W, bytes, cudaMemcpyDeviceToDevice, s); });
+      pp.op([=](char *) { return (int)cudaMemcpyAsync(H, W, bytes, cudaMemcpyDeviceToDevice, s); });
       pp.stage(sb, e0, LT, -1, c->ldf, c->dofs, k);
     } else {
       pp.stage(sa, sb, -1, -1, c->ldf, c->dofs, k);
@@ -1059,6 +1201,7 @@ static void build_solve_body(spike_ctx *c, Pipeline &pp, const SolveBufs &B, int
     mark(1);
     // ---------------- transposed reduced system, levels descending (Sec. 4.3)
     for (int lv = c->NL - 1; lv >= 0; --lv) {
+      pp.key(2, -lv);  // levels descending: higher levels first in every system
       const auto &ms = c->pl.levels[lv];
       GemmBatch gpart, g2, g3, g4;
       std::vector<SumDesc> sums;
@@ -1096,11 +1239,7 @@ static void build_solve_body(spike_ctx *c, Pipeline &pp, const SolveBufs &B, int
         g4.add(gd(c->ident, k, 1, s2, m, 1, YB(mg.b - 1, 1), m, 1, YB(mg.b - 1, 1), m, 1, k, m, k, -1.0, 1.0));
       }
       pp.gemm(gpart);
-      {
-        const size_t so = pp.ar.put(sums);
-        const int nd = (int)sums.size();
-        pp.ops.push_back([=](char *base) { return launch_sum_blocks((SumDesc *)(base + so), nd, maxe, s); });
-      }
+      pp.sums(sums, maxe);
       pp.gemm(g2);
       pp.trs(ts);
       pp.gemm(g3);
@@ -1108,6 +1247,7 @@ static void build_solve_body(spike_ctx *c, Pipeline &pp, const SolveBufs &B, int
     }
     mark(2);
     // ---------------- D^T stage (Eq. sweeps_in_D): X_i = L^{-T}(w + U^{-T}[y_top; 0; y_bot])
+    pp.key(3, 0);
     memset_op(H, es * (size_t)n * m);
     GemmBatch gp;
     std::vector<SweepDesc> sc(nlv, empty_sweep()), sd(nlv, empty_sweep());
@@ -1139,7 +1279,7 @@ static void build_solve_body(spike_ctx *c, Pipeline &pp, const SolveBufs &B, int
       pp.stage(sc, e0, -1, -1, c->ldf, c->dofs, k);
       const int64_t cnt = n * (int64_t)m;
       double *Wd = (double *)W, *Hd = (double *)H;
-      pp.ops.push_back([=](char *) { return launch_axpy(Wd, Hd, 1.0, cnt, s); });
+      pp.op([=](char *) { return launch_axpy(Wd, Hd, 1.0, cnt, s); });
       std::vector<SweepDesc> e1 = e0_dummy(nlv);
       pp.stage(sd, e1, LT, -1, c->ldf, c->dofs, k);
     } else {
@@ -1348,6 +1488,112 @@ extern "C" int spike_solve_ws(spike_handle h, double *F, int64_t ldf, int nrhs, 
                               int64_t ws_bytes) {
   if (!workspace) return -6;
   return solve_impl(h, F, ldf, nrhs, trans, (char *)workspace, ws_bytes, nullptr, false);
+}
+
+// ============================================================== batched solve
+// Several systems solved together: each system's solve is recorded as keyed phases
+// (Pipeline::rec), the phases with equal keys are merged, and every merged phase is one
+// launch.  Scratch per system as in solve_impl (FP64, device F); the merged descriptor
+// arena follows the systems' scratch in the workspace.
+static int solve_batch_impl(const spike_handle *hs, double *const *F, const int *nrhs, int count, char trans,
+                            cudaStream_t s, char *ws, int64_t ws_bytes, int64_t *need) {
+  if (need) *need = 0;
+  if (!hs) return -1;
+  if (!F && !need) return -2;
+  if (!nrhs) return -3;
+  if (count < 0) return -4;
+  const int tr = (trans == 'N' || trans == 'n') ? 0 : ((trans == 'T' || trans == 't' || trans == 'C' || trans == 'c') ? 1 : -1);
+  if (tr < 0) return -5;
+  auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
+  struct Sys {
+    size_t off, o_w, o_h, o_y, o_t, o_p;
+  };
+  std::vector<Sys> sys((size_t)count);
+  size_t total = 0;
+  for (int i = 0; i < count; ++i) {
+    spike_ctx *c = hs[i];
+    if (!valid(c)) return SPIKE_EHANDLE;
+    if (c->f32 || c->pivot) return SPIKE_ENOTSUP;
+    if (nrhs[i] < 0) return -3;
+    const int64_t n = c->pl.n, m = nrhs[i], km = (int64_t)c->k * m;
+    size_t maxm = 1;
+    for (auto &lvv : c->pl.levels) maxm = std::max(maxm, lvv.size());
+    Sys &S = sys[i];
+    S.off = total;
+    size_t o = 0;
+    auto carve = [&](size_t bytes) {
+      size_t r = o;
+      o = align(o + bytes);
+      return r;
+    };
+    S.o_w = m > 1 ? carve(sizeof(double) * (size_t)n * m) : 0;
+    S.o_h = carve(sizeof(double) * (size_t)n * m);
+    S.o_y = carve(sizeof(double) * (size_t)c->nleaves * 2 * km);
+    S.o_t = carve(sizeof(double) * maxm * 2 * km);
+    S.o_p = carve(sizeof(double) * (size_t)c->nleaves * km);
+    total += m > 0 ? o : 0;
+  }
+  std::map<PhaseKey, Phase> merged;
+  for (int i = 0; i < count; ++i) {
+    spike_ctx *c = hs[i];
+    const int m = nrhs[i];
+    if (m == 0) continue;
+    const int64_t n = c->pl.n;
+    char *base = (ws ? ws : (char *)nullptr) + sys[i].off;  // sizing pass: pointers are never used
+    double *Fi = F ? F[i] : nullptr;
+    if (!need && !Fi) return -2;
+    SolveBufs B;
+    B.W = m > 1 ? (void *)(base + sys[i].o_w) : (void *)Fi;
+    B.H = base + sys[i].o_h;
+    B.Y = (double *)(base + sys[i].o_y);
+    B.TM = (double *)(base + sys[i].o_t);
+    B.PP = (double *)(base + sys[i].o_p);
+    std::map<PhaseKey, Phase> ph;
+    Pipeline pr;
+    pr.st = s;
+    pr.rec = &ph;
+    if (m > 1) {
+      double *src = Fi, *dst = (double *)B.W;
+      pr.key(-1, 0);
+      pr.op([=](char *) { return launch_transpose(src, dst, n, m, n, 1, s); });
+    }
+    build_solve(c, pr, B, m, tr, false);
+    if (m > 1) {
+      double *src = (double *)B.W, *dst = Fi;
+      pr.key(9, 0);
+      pr.op([=](char *) { return launch_transpose(src, dst, n, m, n, 0, s); });
+    }
+    for (auto &kv : ph) merge_phase(merged[kv.first], kv.second);
+  }
+  const size_t q_off = align(total), q_bytes = 4096;  // work-queue counters of the sweep stages
+  const size_t args_off = q_off + q_bytes;
+  Pipeline pp;
+  pp.st = s;
+  pp.queue_base = (unsigned int *)((ws ? ws : (char *)nullptr) + q_off);
+  pp.max_queue = (int)(q_bytes / sizeof(unsigned int));
+  for (auto &kv : merged) pp.emit(kv.second);
+  const int64_t want = (int64_t)(args_off + pp.ar.h.size());
+  if (need) {
+    *need = want;
+    return 0;
+  }
+  if (!ws) return -7;
+  if (ws_bytes < want) return -8;
+  char *args = ws + args_off;
+  if (!pp.ar.h.empty()) SP_CUDA(cudaMemcpyAsync(args, pp.ar.h.data(), pp.ar.h.size(), cudaMemcpyHostToDevice, s));
+  return pp.run_ops(args);
+}
+
+extern "C" int spike_solve_batch_workspace(const spike_handle *hs, const int *nrhs, int count, char trans,
+                                           int64_t *bytes) {
+  if (!bytes) return -5;
+  const int rc = solve_batch_impl(hs, nullptr, nrhs, count, trans, nullptr, nullptr, 0, bytes);
+  return rc == -3 ? -2 : (rc == -4 ? -3 : (rc == -5 ? -4 : rc));  // argument positions of this entry point
+}
+
+extern "C" int spike_solve_batch(const spike_handle *hs, double *const *F, const int *nrhs, int count, char trans,
+                                 void *stream, void *workspace, int64_t ws_bytes) {
+  return solve_batch_impl(hs, F, nrhs, count, trans, (cudaStream_t)stream, (char *)workspace, ws_bytes, nullptr);
 }
 
 extern "C" int spike_solve(spike_handle h, double *F, int nrhs, char trans) {

@@ -75,6 +75,7 @@ struct SweepDesc {
   int kind;            // SweepKind
   int kw;              // off-diagonal width of the triangle (k, or 2k for U in pivoting mode)
   int fixed_split;     // 1: batch-invariant summation order of the window products
+  int ldf, dofs;       // the leaf's factor storage: column stride and diagonal offset (leaf.cu)
   const double *ga;
   int64_t ga_rs, ga_cs;
   const double *gb;
@@ -149,8 +150,11 @@ int launch_factor_nopiv(const LeafDev *leaves, int nleaves, int k, int ldf, void
                         unsigned long long *status, const SweepDesc *sweeps, void *stream, int f32);
 int launch_factor_piv(const LeafDev *leaves, int nleaves, int k, int ldf, double *fb, double *dinv, int *ipiv,
                       unsigned long long *status, void *stream);
-// Runs per_cta consecutive descriptors per CTA (a leaf's sweep sequence), ncta CTAs.
-int launch_sweeps(const SweepDesc *descs, int ncta, int per_cta, int ldf, int dofs, void *stream, int f32 = 0);
+// Runs per_cta consecutive descriptors per task (a leaf's sweep sequence), ncta tasks: one
+// CTA per task, or, with queue (a zeroed device counter), `grid` persistent CTAs taking
+// tasks in order.
+int launch_sweeps(const SweepDesc *descs, int ncta, int per_cta, int ldf, int dofs, void *stream, int f32 = 0,
+                  unsigned int *queue = nullptr, int grid = 0);
 int launch_piv_sweep(int kind, const SweepDesc *descs, int ndesc, int k, int ldf, int dofs, void *stream);
 int launch_tips0(const LeafDev *leaves, int nleaves, int k, const void *zbuf, const int64_t *zoff, double *spk,
                  void *stream, int f32);

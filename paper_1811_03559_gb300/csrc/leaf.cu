@@ -17,6 +17,7 @@
 //          columns [k, 2k) = [0; R_bot] (coupling through the local bottom rows).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "internal.h"
@@ -479,6 +480,8 @@ __device__ __forceinline__ void window_fma(T *acc, const T *tw, const T *xrow, i
 template <typename T>
 __device__ void sweep_run(const SweepDesc &D, int ldf, int dofs, T *sm) {
   if (D.ncols <= 0 || D.r1 <= D.r0) return;
+  ldf = D.ldf;  // the descriptor carries its leaf's storage (several systems may share a launch)
+  dofs = D.dofs;
   // descriptor pointers carry the leaf's storage type T
   const T *dfb = (const T *)D.fb;
   const T *ddinv = (const T *)D.dinv;
@@ -712,26 +715,44 @@ __device__ void sweep_run(const SweepDesc &D, int ldf, int dofs, T *sm) {
   }
 }
 
+// Task t = descriptors [t*per_cta, (t+1)*per_cta), run back to back by one CTA.  Without a
+// queue CTA b runs task b; with one (a zeroed counter) a grid of persistent CTAs takes
+// tasks in index order (tasks are listed largest first) until all ntasks are taken.
 template <typename T>
-__global__ void __launch_bounds__(NTHREADS, 1) k_sweeps(const SweepDesc *descs, int per_cta, int ldf, int dofs) {
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_sweeps(const SweepDesc *descs, int per_cta, int ldf, int dofs, int ntasks, unsigned int *queue) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  for (int s = 0; s < per_cta; ++s) {
-    sweep_run<T>(descs[(int64_t)blockIdx.x * per_cta + s], ldf, dofs, (T *)sm_raw);
-    __syncthreads();
+  __shared__ int s_task;
+  int task = blockIdx.x;
+  for (;;) {
+    if (queue) {
+      __syncthreads();
+      if (threadIdx.x == 0) s_task = (int)atomicAdd(queue, 1u);
+      __syncthreads();
+      task = s_task;
+    }
+    if (task >= ntasks) break;
+    for (int s = 0; s < per_cta; ++s) {
+      sweep_run<T>(descs[(int64_t)task * per_cta + s], ldf, dofs, (T *)sm_raw);
+      __syncthreads();
+    }
+    if (!queue) break;
   }
 }
 
-int launch_sweeps(const SweepDesc *descs, int ncta, int per_cta, int ldf, int dofs, void *stream, int f32) {
+int launch_sweeps(const SweepDesc *descs, int ncta, int per_cta, int ldf, int dofs, void *stream, int f32,
+                  unsigned int *queue, int grid) {
   if (ncta <= 0 || per_cta <= 0) return 0;
+  const int g = queue ? std::max(1, std::min(grid, ncta)) : ncta;
   cudaError_t e;
   if (f32) {
     e = (cudaError_t)smem_at_least((const void *)k_sweeps<float>, SWEEP_SMEM);
     if (e != cudaSuccess) return (int)e;
-    k_sweeps<float><<<ncta, NTHREADS, SWEEP_SMEM, (cudaStream_t)stream>>>(descs, per_cta, ldf, dofs);
+    k_sweeps<float><<<g, NTHREADS, SWEEP_SMEM, (cudaStream_t)stream>>>(descs, per_cta, ldf, dofs, ncta, queue);
   } else {
     e = (cudaError_t)smem_at_least((const void *)k_sweeps<double>, SWEEP_SMEM);
     if (e != cudaSuccess) return (int)e;
-    k_sweeps<double><<<ncta, NTHREADS, SWEEP_SMEM, (cudaStream_t)stream>>>(descs, per_cta, ldf, dofs);
+    k_sweeps<double><<<g, NTHREADS, SWEEP_SMEM, (cudaStream_t)stream>>>(descs, per_cta, ldf, dofs, ncta, queue);
   }
   count_launch();
   return (int)cudaGetLastError();

@@ -76,6 +76,7 @@ struct spike_server_s {
   spike_server_config cfg;
   int dev = 0;
   int sms = 152;
+  int batch_systems = 16;  // most matrices per solve
   bool dry = false;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -90,8 +91,8 @@ struct spike_server_s {
   uint64_t tick = 0;
   int running = 0;  // workers between taking a batch and finishing it
   int waiting = 0;  // of those, workers blocked in admit()
-  int64_t batches = 0, rhs = 0, nfact = 0, nevict = 0, nwait = 0, failed = 0, completed = 0;
-  int max_batch = 0;
+  int64_t batches = 0, rhs = 0, nfact = 0, nevict = 0, nwait = 0, failed = 0, completed = 0, multi = 0;
+  int max_batch = 0, max_systems = 0;
   double t_first = -1.0, t_last = 0.0;
   std::vector<double> lat;
   cudaMemPool_t pool = nullptr;
@@ -181,6 +182,45 @@ void release(Lock &lk, std::vector<spike_handle> &victims, cudaStream_t st) {
   }
   victims.clear();
   lk.lock();
+}
+
+// Requests of one matrix merged into a solve.
+struct Group {
+  Mat *M;
+  Fac *F;
+  std::vector<int64_t> ids;
+  int cols;
+};
+
+// Add up to `limit` more groups to a solve: waiting FP64 requests with the given trans on
+// other matrices whose (non-pivoting) factorization is resident and idle, each with the
+// other waiting requests on its matrix, up to max_batch_rhs columns per matrix.
+void pick_more(spike_server_s *S, char trans, int64_t mid0, int limit, std::vector<Group> &out) {
+  std::unordered_map<int64_t, size_t> gi;
+  std::deque<int64_t> rest;
+  for (int64_t id : S->pending) {
+    const Req &r = S->reqs[id];
+    bool take = false;
+    if (r.prec == 0 && r.trans == trans && r.mid != mid0) {
+      Mat &M = S->mats[r.mid];
+      auto it = gi.find(r.mid);
+      if (it != gi.end()) {
+        Group &g = out[it->second];
+        if (g.cols + r.nrhs <= S->cfg.max_batch_rhs) {
+          g.ids.push_back(id);
+          g.cols += r.nrhs;
+          take = true;
+        }
+      } else if ((int)gi.size() < limit && !M.pivot && M.fac[0].resident && !M.fac[0].busy) {
+        gi[r.mid] = out.size();
+        out.push_back(Group{&M, &M.fac[0], {id}, r.nrhs});
+        M.fac[0].busy = true;
+        take = true;
+      }
+    }
+    if (!take) rest.push_back(id);
+  }
+  S->pending.swap(rest);
 }
 
 int grow(spike_server_s *S, Lock &lk, char **p, int64_t *have, int64_t need, cudaStream_t st) {
@@ -280,47 +320,84 @@ void worker(spike_server_s *S, int w) {
       }
     }
 
-    // 2. buffers: merged right-hand sides and solve workspace of this worker
+    // 2. other resident FP64 matrices with waiting requests of the same trans join the
+    // solve (one spike_solve_batch: every stage of all of them in shared launches)
+    std::vector<Group> groups;
+    groups.push_back(Group{&M, &F, batch, cols});
+    if (rc == 0 && prec == 0 && !M.pivot && S->batch_systems > 1)
+      pick_more(S, trans, r0.mid, S->batch_systems - 1, groups);
+    const bool multi = groups.size() > 1;
+
+    // 3. buffers: merged right-hand sides and solve workspace of this worker
+    std::vector<int64_t> fb_off(groups.size(), 0);
+    int64_t fb_need = 0;
+    for (size_t g = 0; g < groups.size(); ++g) {
+      fb_off[g] = fb_need;
+      fb_need += ((int64_t)sizeof(double) * groups[g].M->n * groups[g].cols + 255) & ~int64_t(255);
+    }
+    std::vector<spike_handle> hs;
+    std::vector<int> gcols;
+    for (auto &g : groups) {
+      hs.push_back(g.F->h);
+      gcols.push_back(g.cols);
+    }
     if (rc == 0) {
       int64_t ws_need = 0;
       if (S->dry) {
-        ws_need = (int64_t)sizeof(double) * M.n * cols * 2;
+        ws_need = 2 * fb_need;
+      } else if (multi) {
+        rc = spike_solve_batch_workspace(hs.data(), gcols.data(), (int)hs.size(), trans, &ws_need);
       } else {
         rc = spike_solve_workspace(F.h, cols, trans, 0, &ws_need);
       }
       if (rc == 0) rc = grow(S, lk, &B.ws, &B.ws_bytes, ws_need, st);
-      if (rc == 0) rc = grow(S, lk, (char **)&B.fb, &B.fb_bytes, (int64_t)sizeof(double) * M.n * cols, st);
+      if (rc == 0) rc = grow(S, lk, (char **)&B.fb, &B.fb_bytes, fb_need, st);
     }
 
-    // 3. the merged solve
+    // 4. the merged solve
     if (rc == 0) {
-      std::vector<Req *> rs;
-      for (int64_t id : batch) rs.push_back(&S->reqs[id]);
-      spike_handle h = F.h;
+      std::vector<std::vector<Req *>> rs(groups.size());
+      for (size_t g = 0; g < groups.size(); ++g)
+        for (int64_t id : groups[g].ids) rs[g].push_back(&S->reqs[id]);
       lk.unlock();
-      const size_t col_bytes = sizeof(double) * (size_t)M.n;
       if (S->dry) {
         sleep_us(S->cfg.dryrun_solve_us);
-        for (Req *r : rs) memmove(r->X, r->F, col_bytes * r->nrhs);
+        for (size_t g = 0; g < groups.size(); ++g)
+          for (Req *r : rs[g]) memmove(r->X, r->F, sizeof(double) * (size_t)groups[g].M->n * r->nrhs);
       } else {
-        int64_t off = 0;
-        for (Req *r : rs) {
-          if (!rc && cudaMemcpyAsync(B.fb + off * M.n, r->F, col_bytes * r->nrhs, cudaMemcpyDefault, st) != cudaSuccess)
-            rc = SPIKE_ECUDA;
-          off += r->nrhs;
+        std::vector<double *> fptr(groups.size());
+        for (size_t g = 0; g < groups.size(); ++g) {
+          const int64_t n = groups[g].M->n;
+          double *base = (double *)((char *)B.fb + fb_off[g]);
+          fptr[g] = base;
+          int64_t off = 0;
+          for (Req *r : rs[g]) {
+            if (!rc && cudaMemcpyAsync(base + off * n, r->F, sizeof(double) * n * r->nrhs, cudaMemcpyDefault, st) !=
+                           cudaSuccess)
+              rc = SPIKE_ECUDA;
+            off += r->nrhs;
+          }
         }
-        if (!rc) rc = spike_set_stream(h, st);
-        if (!rc) rc = spike_solve_ws(h, B.fb, M.n, cols, trans, B.ws, B.ws_bytes);
-        off = 0;
-        for (Req *r : rs) {
-          if (!rc && cudaMemcpyAsync(r->X, B.fb + off * M.n, col_bytes * r->nrhs, cudaMemcpyDefault, st) != cudaSuccess)
-            rc = SPIKE_ECUDA;
-          off += r->nrhs;
+        if (!rc && multi) {
+          rc = spike_solve_batch(hs.data(), fptr.data(), gcols.data(), (int)hs.size(), trans, st, B.ws, B.ws_bytes);
+        } else if (!rc) {
+          rc = spike_set_stream(F.h, st);
+          if (!rc) rc = spike_solve_ws(F.h, fptr[0], M.n, cols, trans, B.ws, B.ws_bytes);
+        }
+        for (size_t g = 0; g < groups.size(); ++g) {
+          const int64_t n = groups[g].M->n;
+          int64_t off = 0;
+          for (Req *r : rs[g]) {
+            if (!rc && cudaMemcpyAsync(r->X, fptr[g] + off * n, sizeof(double) * n * r->nrhs, cudaMemcpyDefault, st) !=
+                           cudaSuccess)
+              rc = SPIKE_ECUDA;
+            off += r->nrhs;
+          }
         }
         if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = SPIKE_ECUDA;
       }
       lk.lock();
-      if (!S->dry && F.h) {
+      if (!S->dry && !multi && F.h) {
         spike_info info;  // the descriptor buffer may have grown
         if (spike_get_info(F.h, &info) == 0) {
           account(S, info.device_bytes - F.bytes);
@@ -329,27 +406,33 @@ void worker(spike_server_s *S, int w) {
       }
     }
 
-    // 4. completion
+    // 5. completion
     if (rc != 0) {
       const char *msg = spike_last_cuda_error();
       S->last_error = std::string(spike_strerror(rc)) + (msg && *msg ? std::string(": ") + msg : std::string());
     }
     const double t = now_s();
-    for (int64_t id : batch) {
-      Req &r = S->reqs[id];
-      r.status = rc;
-      r.t_done = t;
-      r.done = true;
-      S->lat.push_back(1e3 * (t - r.t_submit));
-      if (rc == 0) ++S->completed;
-      else ++S->failed;
+    int nreq = 0;
+    for (auto &g : groups) {
+      for (int64_t id : g.ids) {
+        Req &r = S->reqs[id];
+        r.status = rc;
+        r.t_done = t;
+        r.done = true;
+        S->lat.push_back(1e3 * (t - r.t_submit));
+        if (rc == 0) ++S->completed;
+        else ++S->failed;
+      }
+      nreq += (int)g.ids.size();
+      S->rhs += g.cols;
+      g.F->last_use = ++S->tick;
+      g.F->busy = false;
     }
     ++S->batches;
-    S->rhs += cols;
-    S->max_batch = std::max(S->max_batch, (int)batch.size());
+    if (multi) ++S->multi;
+    S->max_batch = std::max(S->max_batch, nreq);
+    S->max_systems = std::max(S->max_systems, (int)groups.size());
     S->t_last = t;
-    F.last_use = ++S->tick;
-    F.busy = false;
     --S->running;
     S->cv_done.notify_all();
     S->cv_work.notify_all();
@@ -367,6 +450,7 @@ extern "C" int spike_server_create(const spike_server_config *cfg, spike_server 
   spike_server_s *S = new spike_server_s();
   S->cfg = *cfg;
   S->dry = (cfg->flags & SPIKE_SERVE_DRYRUN) != 0;
+  if (cfg->batch_systems > 0) S->batch_systems = cfg->batch_systems;
   if (!S->dry) {
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -520,6 +604,8 @@ extern "C" int spike_server_stats_get(spike_server S, spike_server_stats *o) {
   for (auto &kv : S->mats)
     for (auto &f : kv.second.fac) o->resident += f.resident ? 1 : 0;
   o->max_batch = S->max_batch;
+  o->multi_solves = S->multi;
+  o->max_systems = S->max_systems;
   if (!S->lat.empty()) {
     std::vector<double> v = S->lat;
     std::sort(v.begin(), v.end());

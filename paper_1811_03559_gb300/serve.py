@@ -19,7 +19,8 @@ class ServerConfig(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_int64), ("streams", ctypes.c_int32), ("max_batch_rhs", ctypes.c_int32),
                 ("p", ctypes.c_int32), ("nrhs_hint", ctypes.c_int32), ("K", ctypes.c_double),
                 ("flags", ctypes.c_int32), ("dryrun_factor_us", ctypes.c_int32),
-                ("dryrun_solve_us", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("dryrun_solve_us", ctypes.c_int32), ("batch_systems", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 class ServerStats(ctypes.Structure):
@@ -27,12 +28,13 @@ class ServerStats(ctypes.Structure):
                 ("batches", ctypes.c_int64), ("rhs", ctypes.c_int64), ("factorizations", ctypes.c_int64),
                 ("evictions", ctypes.c_int64), ("admission_waits", ctypes.c_int64),
                 ("used_bytes", ctypes.c_int64), ("peak_bytes", ctypes.c_int64), ("resident", ctypes.c_int32),
-                ("max_batch", ctypes.c_int32), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("max_batch", ctypes.c_int32), ("multi_solves", ctypes.c_int64), ("max_systems", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
                 ("max_ms", ctypes.c_double), ("mean_ms", ctypes.c_double), ("span_s", ctypes.c_double),
                 ("solves_per_s", ctypes.c_double), ("rhs_per_s", ctypes.c_double)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad"}
 
 
 _bound = False
@@ -72,11 +74,12 @@ class Server:
     up to `max_batch_rhs` right-hand sides merged per solve."""
 
     def __init__(self, budget_bytes, streams=4, max_batch_rhs=64, p=0, nrhs_hint=0, K=0.0, dryrun=False,
-                 dryrun_factor_us=0, dryrun_solve_us=0):
+                 dryrun_factor_us=0, dryrun_solve_us=0, batch_systems=0):
         self._keep = {}
         cfg = ServerConfig(budget_bytes=int(budget_bytes), streams=streams, max_batch_rhs=max_batch_rhs, p=p,
                            nrhs_hint=nrhs_hint, K=K, flags=DRYRUN if dryrun else 0,
-                           dryrun_factor_us=dryrun_factor_us, dryrun_solve_us=dryrun_solve_us)
+                           dryrun_factor_us=dryrun_factor_us, dryrun_solve_us=dryrun_solve_us,
+                           batch_systems=batch_systems)
         h = ctypes.c_void_p()
         rc = _lib().spike_server_create(ctypes.byref(cfg), ctypes.byref(h))
         if rc != 0:

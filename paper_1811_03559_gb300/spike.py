@@ -54,7 +54,7 @@ EXPORTS = ["spike_plan", "spike_factor", "spike_factor_ex", "spike_solve", "spik
            "spike_get_info", "spike_get_tips", "spike_backward_error", "spike_get_timings", "spike_kernel_launches",
            "spike_free", "spike_strerror", "spike_last_cuda_error", "spike_backward_error_noalloc",
            "spike_measure_fp64_peak", "spike_factor_bytes", "spike_solve_workspace", "spike_solve_ws",
-           "spike_measure_K", "spike_tune"]
+           "spike_measure_K", "spike_tune", "spike_solve_batch", "spike_solve_batch_workspace"]
 SPIKE_ELIMIT = -1006
 NOALLOC_MAX_NRHS = 1024
 
@@ -103,6 +103,8 @@ def lib():
         L.spike_solve_workspace.argtypes = [vp, i32, ctypes.c_char, i32, ctypes.POINTER(i64)]
         L.spike_solve_ws.argtypes = [vp, dp, i64, i32, ctypes.c_char, vp, i64]
         L.spike_measure_K.argtypes = [dp, i64, i64, i32, i32, vp, ctypes.POINTER(ctypes.c_double)]
+        L.spike_solve_batch.argtypes = [vp, vp, vp, i32, ctypes.c_char, vp, vp, i64]
+        L.spike_solve_batch_workspace.argtypes = [vp, vp, i32, ctypes.c_char, ctypes.POINTER(i64)]
         L.spike_tune.argtypes = [dp, i64, i64, i32, i32, i32, i32, vp, i32, vp, i32, vp, vp,
                                  ctypes.POINTER(TuneResult)]
         L.spike_kernel_launches.argtypes = []
@@ -294,6 +296,30 @@ def tune(band, kl, ku, nrhs, p_candidates, r13_candidates=(), nsolves=2):
     if rc != 0:
         raise SpikeError(rc, "spike_tune")
     return res.as_dict(), table
+
+
+def solve_batch(facs, Fs, trans="N", workspace=None):
+    """spike_solve_batch: overwrite every device tensor Fs[i] (shape (nrhs_i, n_i)) with
+    op(A_i)^{-1} Fs[i], all systems stage by stage in shared launches.  Returns the
+    workspace tensor (reusable for the same shapes)."""
+    import torch
+    cnt = len(facs)
+    hs = (ctypes.c_void_p * cnt)(*[f._h.value for f in facs])
+    ptrs = (ctypes.c_void_p * cnt)(*[F.data_ptr() for F in Fs])
+    nr = (ctypes.c_int * cnt)(*[1 if F.ndim == 1 else F.shape[0] for F in Fs])
+    for f, F in zip(facs, Fs):
+        assert F.is_cuda and F.is_contiguous() and F.shape[-1] == f.n
+    need = ctypes.c_int64(0)
+    rc = lib().spike_solve_batch_workspace(hs, nr, cnt, trans.encode(), ctypes.byref(need))
+    if rc != 0:
+        raise SpikeError(rc, "spike_solve_batch_workspace")
+    if workspace is None or workspace.numel() < need.value:
+        workspace = torch.empty(max(need.value, 1), dtype=torch.uint8, device=Fs[0].device)
+    rc = lib().spike_solve_batch(hs, ptrs, nr, cnt, trans.encode(), _torch_stream(Fs[0]),
+                                 ctypes.c_void_p(workspace.data_ptr()), workspace.numel())
+    if rc != 0:
+        raise SpikeError(rc, "spike_solve_batch")
+    return workspace
 
 
 def factor(band, kl, ku, p, pivot=0, **kw):

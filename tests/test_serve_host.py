@@ -204,3 +204,35 @@ def test_request_latency_query_does_not_block():
         assert S.latency(rid) == lat
         with pytest.raises(spike.SpikeError):
             S.latency(12345)
+
+
+def test_resident_fp64_requests_of_several_matrices_share_a_solve():
+    """With factorizations resident, waiting FP64 requests of the same trans on different
+    matrices are solved together (one spike_solve_batch); mixed-precision ones and the
+    other trans are not merged with them."""
+    with serve.Server(1 << 30, streams=1, max_batch_rhs=64, dryrun=True, dryrun_solve_us=150_000) as S:
+        for mid in range(6):
+            S.add_matrix(mid, _band(400, 2), 2, 2)
+        for mid in range(5):  # factor (and keep) matrices 0..4
+            S.wait(S.submit(mid, np.ones((1, 400)))[0])
+        base = S.stats()
+        busy, _ = S.submit(5, np.ones((1, 400)))  # keeps the single worker busy
+        time.sleep(0.05)
+        ids = [S.submit(mid, np.full((2, 400), float(mid)))[0] for mid in range(4)]    # FP64 N on 0..3
+        ids.append(S.submit(4, np.ones((1, 400)), mixed=True)[0])                     # mixed: own solve
+        ids.append(S.submit(0, np.ones((1, 400)), trans="T")[0])                      # T: own solve
+        for r in [busy] + ids:
+            S.wait(r)
+        st = S.stats()
+        assert st["batches"] - base["batches"] == 1 + 1 + 1 + 1  # busy, 4-matrix N solve, mixed, T
+        assert st["multi_solves"] == 1 and st["max_systems"] == 4
+    with serve.Server(1 << 30, streams=1, dryrun=True, dryrun_solve_us=100_000, batch_systems=1) as S:
+        for mid in range(3):
+            S.add_matrix(mid, _band(300, 2), 2, 2)
+            S.wait(S.submit(mid, np.ones((1, 300)))[0])
+        busy, _ = S.submit(2, np.ones((1, 300)))
+        time.sleep(0.05)
+        ids = [S.submit(mid, np.ones((1, 300)))[0] for mid in range(2)]
+        for r in [busy] + ids:
+            S.wait(r)
+        assert S.stats()["multi_solves"] == 0
