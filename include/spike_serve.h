@@ -11,10 +11,11 @@
  * same time are merged into one multi-column solve (continuous batching: whenever a
  * worker becomes free it takes the oldest waiting request whose matrix is not being
  * solved by another worker, plus every other waiting request with the same key, up
- * to max_batch_rhs columns).  FP64 requests of up to batch_systems different matrices
- * whose factorizations are resident are solved together with spike_solve_batch (every
- * stage of all of them in shared launches).  Each worker is one host thread driving
- * one CUDA stream, so solves run concurrently.
+ * to max_batch_rhs columns).  With batch_systems > 1, FP64 requests of up to that many
+ * matrices whose factorizations are resident are solved together with spike_solve_batch
+ * (every stage of all of them in shared launches); this pays for many small systems, but
+ * it keeps all those factorizations busy (not evictable) until the slowest finishes.
+ * Each worker is one host thread driving one CUDA stream, so solves run concurrently.
  *
  * A request's result does not depend on what it was batched with: the solve kernels
  * give every right-hand side the same bits whatever the batch width or position
@@ -58,7 +59,7 @@ typedef struct {
   int32_t flags;           /* SPIKE_SERVE_* */
   int32_t dryrun_factor_us;  /* SPIKE_SERVE_DRYRUN: simulated factorization time */
   int32_t dryrun_solve_us;   /* SPIKE_SERVE_DRYRUN: simulated time per solve */
-  int32_t batch_systems;     /* most matrices whose FP64 requests share one solve (0: 16, 1: one matrix) */
+  int32_t batch_systems;     /* most matrices whose FP64 requests share one solve (0 or 1: one matrix) */
   int32_t reserved[6];
 } spike_server_config;
 

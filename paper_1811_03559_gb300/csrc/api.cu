@@ -70,18 +70,30 @@ struct GemmBatch {
     if (g.M <= 0 || g.N <= 0) return;
     d.push_back(g);
   }
+  // Batches whose products all have N <= 8 columns (few right-hand sides) use 256-row
+  // tiles of 1, 4 or 8 columns instead (tsz = -columns).
   void finalize(int sms) {
     auto count = [&](int t) {
       long long c = 0;
       for (auto &g : d) c += (long long)((g.M + t - 1) / t) * ((g.N + t - 1) / t);
       return c;
     };
-    tsz = count(64) >= sms ? 64 : (count(32) >= sms ? 32 : 16);
+    int maxn = 0;
+    for (auto &g : d) maxn = std::max(maxn, g.N);
+    int tm, tn;
+    if (maxn <= 8) {
+      tn = maxn <= 1 ? 1 : (maxn <= 4 ? 4 : 8);
+      tm = 256;
+      tsz = -tn;
+    } else {
+      tsz = count(64) >= sms ? 64 : (count(32) >= sms ? 32 : 16);
+      tm = tn = tsz;
+    }
     tiles = 0;
     for (auto &g : d) {
-      g.tiles_n = (g.N + tsz - 1) / tsz;
+      g.tiles_n = (g.N + tn - 1) / tn;
       g.tile0 = tiles;
-      tiles += ((g.M + tsz - 1) / tsz) * g.tiles_n;
+      tiles += ((g.M + tm - 1) / tm) * g.tiles_n;
     }
   }
 };

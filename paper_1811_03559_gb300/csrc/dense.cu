@@ -141,10 +141,87 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmDesc *descs, int ndesc) 
   }
 }
 
+// Few columns (N <= 8, e.g. single right-hand sides): 256 rows x TN columns per CTA, one row
+// per thread.  Same per-output K order as k_gemm, so the same bits.
+template <int TN>
+__global__ void __launch_bounds__(256) k_gemm_skinny(const GemmDesc *descs, int ndesc) {
+  __shared__ double As[16][256 + 1];
+  __shared__ double Bs[16][TN];
+  const int tile = blockIdx.x;
+  int lo = 0, hi = ndesc - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (descs[mid].tile0 <= tile) lo = mid;
+    else hi = mid - 1;
+  }
+  const GemmDesc D = descs[lo];
+  const int t = tile - D.tile0;
+  const int i0 = (t / D.tiles_n) * 256, j0 = (t % D.tiles_n) * TN;
+  const int tid = threadIdx.x;
+  double acc[TN];
+#pragma unroll
+  for (int v = 0; v < TN; ++v) acc[v] = 0.0;
+  const bool a_kfast = (D.a_cs == 1 || D.a_cs == -1);
+  for (int kk = 0; kk < D.K; kk += 16) {
+    for (int idx = tid; idx < 16 * 256; idx += 256) {
+      int i, kq;
+      if (a_kfast) {
+        kq = idx & 15;
+        i = idx >> 4;
+      } else {
+        i = idx & 255;
+        kq = idx >> 8;
+      }
+      double v = 0.0;
+      if (i0 + i < D.M && kk + kq < D.K) {
+        const int64_t o = (int64_t)(i0 + i) * D.a_rs + (int64_t)(kk + kq) * D.a_cs;
+        v = (D.types & G_A32) ? (double)((const float *)D.A)[o] : D.A[o];
+      }
+      As[kq][i] = v;
+    }
+    if (tid < 16 * TN) {
+      const int kb = tid / TN, j = tid % TN;
+      double w = 0.0;
+      if (j0 + j < D.N && kk + kb < D.K) {
+        const int64_t o = (int64_t)(kk + kb) * D.b_rs + (int64_t)(j0 + j) * D.b_cs;
+        w = (D.types & G_B32) ? (double)((const float *)D.B)[o] : D.B[o];
+      }
+      Bs[kb][j] = w;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kq = 0; kq < 16; ++kq) {
+      const double a = As[kq][tid];
+#pragma unroll
+      for (int v = 0; v < TN; ++v) acc[v] = fma(a, Bs[kq][v], acc[v]);
+    }
+    __syncthreads();
+  }
+  const int i = i0 + tid;
+  if (i >= D.M) return;
+#pragma unroll
+  for (int v = 0; v < TN; ++v) {
+    const int j = j0 + v;
+    if (j >= D.N) continue;
+    double r = D.alpha * acc[v];
+    if (D.beta != 0.0) {
+      const int64_t o = (int64_t)i * D.c0_rs + (int64_t)j * D.c0_cs;
+      r = fma(D.beta, (D.types & G_C032) ? (double)((const float *)D.C0)[o] : D.C0[o], r);
+    }
+    const int64_t oc = (int64_t)i * D.c_rs + (int64_t)j * D.c_cs;
+    if (D.types & G_C32) ((float *)D.C)[oc] = (float)r;
+    else D.C[oc] = r;
+  }
+}
+
 int launch_gemm(const GemmDesc *d, int ndesc, int total_tiles, int tile_size, void *stream) {
   if (ndesc <= 0 || total_tiles <= 0) return 0;
   const cudaStream_t st = (cudaStream_t)stream;
-  if (tile_size == 16) k_gemm<16><<<total_tiles, 256, 0, st>>>(d, ndesc);
+  if (tile_size < 0) {  // skinny: 256 rows x (-tile_size) columns
+    if (tile_size == -1) k_gemm_skinny<1><<<total_tiles, 256, 0, st>>>(d, ndesc);
+    else if (tile_size == -4) k_gemm_skinny<4><<<total_tiles, 256, 0, st>>>(d, ndesc);
+    else k_gemm_skinny<8><<<total_tiles, 256, 0, st>>>(d, ndesc);
+  } else if (tile_size == 16) k_gemm<16><<<total_tiles, 256, 0, st>>>(d, ndesc);
   else if (tile_size == 32) k_gemm<32><<<total_tiles, 256, 0, st>>>(d, ndesc);
   else k_gemm<64><<<total_tiles, 256, 0, st>>>(d, ndesc);
   count_launch();

@@ -158,7 +158,8 @@ int launch_sweeps(const SweepDesc *descs, int ncta, int per_cta, int ldf, int do
 int launch_piv_sweep(int kind, const SweepDesc *descs, int ndesc, int k, int ldf, int dofs, void *stream);
 int launch_tips0(const LeafDev *leaves, int nleaves, int k, const void *zbuf, const int64_t *zoff, double *spk,
                  void *stream, int f32);
-// tile_size: 64, 32 or 16 (GemmDesc.tiles_n / tile0 computed for that size)
+// tile_size: 64, 32 or 16 (square tiles), or -1 / -4 / -8 (256 rows x that many columns);
+// GemmDesc.tiles_n / tile0 computed for that shape
 int launch_gemm(const GemmDesc *d, int ndesc, int total_tiles, int tile_size, void *stream);
 int launch_getrf(const LuDesc *d, int ndesc, int maxn, unsigned long long *status, void *stream);
 // cols: right-hand-side columns per CTA, 16 or 4 (TrsDesc.tile0 computed for that width)

@@ -671,31 +671,53 @@ __device__ void sweep_run(const SweepDesc &D, int ldf, int dofs, T *sm) {
           __syncthreads();
         }
       }
-      // in-block triangular solve
-      if (cw >= 64) {
-        for (int cc = tid; cc < cw; cc += NTHREADS) {
-          T xv[NB];
+      // in-block triangular solve: X(a) = d(a) s(a), s(a) = G(a) - sum_{ap<a} T'(a, ap) s(ap)
+      // with T'(a, ap) = T(a, ap) d(ap) and the sum taken in ascending ap.  Both schedules
+      // below apply the same FMAs in the same order to every column, so a column's bits do
+      // not depend on how many columns share the pass.
+      for (int idx = tid; idx < NB * NB; idx += NTHREADS) Td[idx] *= dsm[idx / NB];  // Td[ap*NB + a] *= d(ap)
+      __syncthreads();
+      if (cw >= 32) {
+        // blocked: sub-blocks of 8 rows; a thread per column solves the sub-block, then all
+        // threads apply its 8 columns of T' to the rows below ((row, column) pairs in parallel)
+        for (int q0 = 0; q0 < NB; q0 += 8) {
+          for (int cc = tid; cc < cw; cc += NTHREADS) {
+            T sv[8];
 #pragma unroll
-          for (int a = 0; a < NB; ++a) {
-            T s = Gs[a * GLD + cc];
+            for (int a = 0; a < 8; ++a) {
+              T v = Gs[(q0 + a) * GLD + cc];
 #pragma unroll
-            for (int ap = 0; ap < a; ++ap) s = fma(-Td[ap * NB + a], xv[ap], s);
-            xv[a] = s * dsm[a];
+              for (int ap = 0; ap < a; ++ap) v = fma(-Td[(q0 + ap) * NB + q0 + a], sv[ap], v);
+              sv[a] = v;
+            }
+#pragma unroll
+            for (int a = 0; a < 8; ++a) Gs[(q0 + a) * GLD + cc] = sv[a];
           }
+          __syncthreads();
+          const int below = NB - q0 - 8;
+          for (int idx = tid; idx < below * cw; idx += NTHREADS) {
+            const int r = q0 + 8 + idx / cw, cc = idx - (idx / cw) * cw;
+            T v = Gs[r * GLD + cc];
 #pragma unroll
-          for (int a = 0; a < NB; ++a) Gs[a * GLD + cc] = xv[a];
+            for (int ap = 0; ap < 8; ++ap) v = fma(-Td[(q0 + ap) * NB + r], Gs[(q0 + ap) * GLD + cc], v);
+            Gs[r * GLD + cc] = v;
+          }
+          __syncthreads();
+        }
+        for (int idx = tid; idx < NB * cw; idx += NTHREADS) {
+          const int a = idx / cw, cc = idx - a * cw;
+          Gs[a * GLD + cc] *= dsm[a];
         }
       } else {
+        // a warp per column, lanes <-> rows: step ap broadcasts the finished s(ap)
         for (int cc = warp; cc < cw; cc += nwarps) {
-          T s = Gs[lane * GLD + cc];
-          T xf = (T)0;
+          T v = Gs[lane * GLD + cc];
 #pragma unroll
           for (int ap = 0; ap < NB; ++ap) {
-            const T xa = __shfl_sync(FULLMASK, s, ap) * dsm[ap];
-            if (lane == ap) xf = xa;
-            if (lane > ap) s = fma(-Td[ap * NB + lane], xa, s);
+            const T sa = __shfl_sync(FULLMASK, v, ap);
+            if (lane > ap) v = fma(-Td[ap * NB + lane], sa, v);
           }
-          Gs[lane * GLD + cc] = xf;
+          Gs[lane * GLD + cc] = v * dsm[lane];
         }
       }
       __syncthreads();

@@ -76,7 +76,7 @@ struct spike_server_s {
   spike_server_config cfg;
   int dev = 0;
   int sms = 152;
-  int batch_systems = 16;  // most matrices per solve
+  int batch_systems = 1;  // most matrices per solve (1: one matrix per solve)
   bool dry = false;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;

@@ -210,7 +210,8 @@ def test_resident_fp64_requests_of_several_matrices_share_a_solve():
     """With factorizations resident, waiting FP64 requests of the same trans on different
     matrices are solved together (one spike_solve_batch); mixed-precision ones and the
     other trans are not merged with them."""
-    with serve.Server(1 << 30, streams=1, max_batch_rhs=64, dryrun=True, dryrun_solve_us=150_000) as S:
+    with serve.Server(1 << 30, streams=1, max_batch_rhs=64, dryrun=True, dryrun_solve_us=150_000,
+                      batch_systems=16) as S:
         for mid in range(6):
             S.add_matrix(mid, _band(400, 2), 2, 2)
         for mid in range(5):  # factor (and keep) matrices 0..4
