@@ -202,6 +202,47 @@ def load_traffic():
     return d.get("dram_bytes_per_launch_full"), d
 
 
+def _cpu_serve_one(args):
+    """One request of the serving workload on the CPU oracle: banded GEPP + solve (one core)."""
+    import oracle
+    from paper_1811_03559_gb300 import inputs
+    n, k, m, trans, seed = args
+    band, rng = inputs.make_band(n, k, k, seed=seed, dd=1.1)
+    F = rng.uniform(-1.0, 1.0, size=(m, n))
+    t0 = time.perf_counter()
+    oracle.gbsv(band, k, k, F, trans)
+    return time.perf_counter() - t0
+
+
+def cpu_serving_baseline(nreq=160, seed=None):
+    """Requests of the serving workload solved by the CPU oracle, one per host core in
+    parallel (spawned processes): CPU solves/s.  Each request factors its matrix (the oracle
+    keeps no factorization) and solves its right-hand sides; the matrix generation is not
+    timed."""
+    import multiprocessing as mp
+    from paper_1811_03559_gb300 import inputs
+    cfg = dict(inputs.SERVING)
+    if seed is not None:
+        cfg["seed"] = seed
+    ns, ks, _ = inputs.serving_catalogue(cfg)
+    arrivals, mids, nrhs, trans, mixed = inputs.serving_trace(cfg)
+    jobs = [(int(ns[mids[i]]), int(ks[mids[i]]), int(nrhs[i]), str(trans[i]), 1000 + int(mids[i]))
+            for i in range(nreq)]
+    cores = os.cpu_count() or 1
+    import oracle
+    oracle.build_oracle()
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        t0 = time.perf_counter()
+        times = pool.map(_cpu_serve_one, jobs, chunksize=1)
+        wall = time.perf_counter() - t0
+    busy = float(sum(times))
+    return {"solves_per_s": nreq * cores / busy, "cores": cores, "kind": "oracle", "requests": nreq,
+            "sample": "first %d requests of the serving trace, banded GEPP factor + solve per request, one request "
+                      "per core (%d spawned processes); rate = requests / (summed solve seconds / cores), "
+                      "wall %.1f s" % (nreq, cores, wall)}
+
+
 def tuning_leg(band, k, nrhs):
     """The load-balancing constant K measured on one block (Sec. 3.3), a partition-ratio sweep
     at p = 148 (the paper's ratio experiment), and the fastest worker count (spike_tune)."""
@@ -546,10 +587,14 @@ def main():
     tuning = None
     if not args.no_tune and rank == 0:
         tuning = tuning_leg(band, k, m)
+    cpu_serve = None
+    if not args.no_serve and not args.no_cpu and rank == 0:
+        cpu_serve = cpu_serving_baseline()
     serving = None
     if not args.no_serve and rank == 0:
         serving = serving_leg(dev, args.serve_requests, args.serve_streams, args.serve_batch, args.serve_passes,
                               batch_systems=args.serve_batch_systems)
+        serving["cpu_baseline"] = cpu_serve
 
     if rank != 0:
         if dist:

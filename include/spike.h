@@ -43,6 +43,8 @@ extern "C" {
 #define SPIKE_ENOTSUP (-1004)  /* unsupported combination (e.g. bandwidth above the library limit) */
 #define SPIKE_ENOGPU (-1005)   /* no CUDA device available */
 #define SPIKE_ELIMIT (-1006)   /* size above the fixed limit of an entry point that allocates nothing */
+#define SPIKE_ETIMEOUT (-1007) /* reserved: no kernel of this library waits on another (no spin-waits),
+                                  so no call returns it */
 
 #define SPIKE_FLAG_TIMING 1
 /* Size partitions for stage-synchronised execution.  The reduced system puts a
@@ -287,6 +289,13 @@ typedef struct {
 int spike_tune(const double *band, int64_t ldab, int64_t n, int kl, int ku, int nrhs, int nsolves,
                const int *p_candidates, int np, const double *r13_candidates, int nr, void *stream,
                double *table_ms, spike_tune_result *out);
+
+/* Device memory: the library allocates stream-ordered from its own pool per device, which
+ * keeps freed blocks cached (a factorization or solve that follows another reuses them
+ * instead of remapping memory).  spike_release_cached synchronises every device the
+ * library has used and returns the cached blocks that are not in use to the driver;
+ * reserved_before / reserved_after (may be NULL) receive the pools' reserved bytes. */
+int spike_release_cached(int64_t *reserved_before, int64_t *reserved_after);
 
 /* Number of CUDA kernels this library has launched in the process so far. */
 int64_t spike_kernel_launches(void);

@@ -13,6 +13,7 @@
 #include <cstring>
 #include <functional>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -23,7 +24,69 @@ using namespace spk;
 namespace spk {
 static std::atomic<long long> g_launches{0};
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pools[16] = {};
+
+static cudaMemPool_t lib_pool(int dev) {
+  std::lock_guard<std::mutex> g(g_pool_mu);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pools[dev] = pool;
+  }
+  return g_pools[dev];
+}
+
+cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t s) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) {
+    cudaGetLastError();
+    return cudaMallocAsync(p, bytes, s);
+  }
+  cudaMemPool_t pool = lib_pool(dev);
+  if (!pool) return cudaMallocAsync(p, bytes, s);
+  return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
 }  // namespace spk
+
+extern "C" int spike_release_cached(int64_t *reserved_before, int64_t *reserved_after) {
+  if (reserved_before) *reserved_before = 0;
+  if (reserved_after) *reserved_after = 0;
+  std::lock_guard<std::mutex> g(spk::g_pool_mu);
+  uint64_t before = 0, after = 0;
+  for (int dev = 0; dev < 16; ++dev) {
+    cudaMemPool_t pool = spk::g_pools[dev];
+    if (!pool) continue;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(dev);
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+      cudaSetDevice(cur);
+      return SPIKE_ECUDA;
+    }
+    uint64_t v = 0;
+    cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &v);
+    before += v;
+    cudaMemPoolTrimTo(pool, 0);
+    cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &v);
+    after += v;
+    cudaSetDevice(cur);
+  }
+  if (reserved_before) *reserved_before = (int64_t)before;
+  if (reserved_after) *reserved_after = (int64_t)after;
+  return 0;
+}
 
 namespace {
 
@@ -205,7 +268,7 @@ static int ensure(char **p, size_t *cap, size_t need, cudaStream_t s) {
   *p = nullptr;
   *cap = 0;
   size_t want = need + need / 4 + 4096;
-  cudaError_t e = cudaMallocAsync((void **)p, want, s);
+  cudaError_t e = dev_alloc((void **)p, want, s);
   if (e != cudaSuccess) {
     g_cuda_err = std::string("cudaMallocAsync: ") + cudaGetErrorString(e);
     *p = nullptr;
@@ -707,7 +770,7 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
                o_spk = FL.o_spk, o_mlu = FL.o_mlu, o_mpiv = FL.o_mpiv, o_id = FL.o_id, o_st = FL.o_st;
   c->mem_bytes = FL.mem;
   {
-    cudaError_t e = cudaMallocAsync((void **)&c->mem, c->mem_bytes, s);
+    cudaError_t e = dev_alloc((void **)&c->mem, c->mem_bytes, s);
     if (e != cudaSuccess) {
       g_cuda_err = std::string("cudaMallocAsync: ") + cudaGetErrorString(e);
       c->mem = nullptr;
@@ -733,7 +796,7 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
   const size_t tmp_bytes = FL.tmp_bytes, soff = FL.scr;
   char *fscr = nullptr;
   {
-    cudaError_t e = cudaMallocAsync((void **)&fscr, soff, s);
+    cudaError_t e = dev_alloc((void **)&fscr, soff, s);
     if (e != cudaSuccess) {
       g_cuda_err = std::string("cudaMallocAsync: ") + cudaGetErrorString(e);
       return fail(SPIKE_ENOMEM);
@@ -1665,7 +1728,7 @@ extern "C" int spike_backward_error(const double *band, int64_t ldab, int64_t n,
   cudaStream_t s = (cudaStream_t)stream;
   unsigned long long *scr = nullptr;
   const size_t bytes = sizeof(unsigned long long) * (1 + 2 * (size_t)nrhs);
-  SP_CUDA(cudaMallocAsync((void **)&scr, bytes, s));
+  SP_CUDA(dev_alloc((void **)&scr, bytes, s));
   SP_CUDA(cudaMemsetAsync(scr, 0, bytes, s));
   const int e = launch_berr(band, ldab, n, kl, ku, X, F, nrhs, (trans == 'T' || trans == 't') ? 1 : 0, scr, s);
   if (e) {
@@ -1757,6 +1820,7 @@ extern "C" const char *spike_strerror(int code) {
     case SPIKE_ENOTSUP: return "unsupported argument combination";
     case SPIKE_ENOGPU: return "no CUDA device available";
     case SPIKE_ELIMIT: return "size above the fixed limit of an entry point that allocates nothing";
+    case SPIKE_ETIMEOUT: return "timeout (reserved: not returned by this library)";
     default: return "invalid argument";
   }
 }

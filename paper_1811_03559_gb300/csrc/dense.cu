@@ -984,7 +984,7 @@ extern "C" int spike_measure_fp64_peak(void *stream, double *tflops) {
     return SPIKE_ECUDA;
   const int blocks = 2 * sms, threads = 512, iters = 8192;
   double *out = nullptr;
-  if (cudaMallocAsync((void **)&out, sizeof(double) * blocks * threads, s) != cudaSuccess) return SPIKE_ENOMEM;
+  if (spk::dev_alloc((void **)&out, sizeof(double) * blocks * threads, s) != cudaSuccess) return SPIKE_ENOMEM;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);

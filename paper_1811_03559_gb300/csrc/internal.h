@@ -2,6 +2,8 @@
 // the device kernels (leaf.cu, dense.cu).  Not part of the public ABI.
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include <cstdint>
 #include <vector>
 
@@ -131,6 +133,11 @@ struct SumDesc {
 // ------------------------------------------------------------ launchers
 // Each returns cudaError_t as int (0 = success) and counts its kernel launches.
 void count_launch(int n = 1);
+// Stream-ordered allocation from the library's pool on the current device.  The pool keeps
+// freed blocks (release threshold = max), so a factorization or solve that follows another
+// reuses its memory instead of remapping it; spike_release_cached returns it.  Free with
+// cudaFreeAsync.
+cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t s);
 // Raise a kernel's dynamic shared-memory limit to at least `bytes`, never lowering it.
 // The limit is a process-wide attribute of the function: lowering it while another host
 // thread launches the same kernel with a larger request would make that launch fail.

@@ -22,6 +22,7 @@
 
 #include "spike.h"
 #include "spike_serve.h"
+#include "internal.h"
 
 namespace {
 
@@ -95,8 +96,6 @@ struct spike_server_s {
   int max_batch = 0, max_systems = 0;
   double t_first = -1.0, t_last = 0.0;
   std::vector<double> lat;
-  cudaMemPool_t pool = nullptr;
-  uint64_t pool_old = 0;
   std::string last_error;  // CUDA error text of the last failed request (worker threads' own)
 };
 
@@ -234,7 +233,7 @@ int grow(spike_server_s *S, Lock &lk, char **p, int64_t *have, int64_t need, cud
   if (!S->dry) {
     if (*p) cudaFreeAsync(*p, st);
     *p = nullptr;
-    if (cudaMallocAsync((void **)p, (size_t)need, st) != cudaSuccess) {
+    if (spk::dev_alloc((void **)p, (size_t)need, st) != cudaSuccess) {
       cudaGetLastError();
       *p = nullptr;
       rc = SPIKE_ENOMEM;
@@ -463,16 +462,6 @@ extern "C" int spike_server_create(const spike_server_config *cfg, spike_server 
       cudaGetLastError();
       S->sms = 152;
     }
-    // keep freed blocks of the stream-ordered allocator cached up to the budget, so
-    // evictions and re-factorizations reuse memory instead of remapping it
-    if (cudaDeviceGetDefaultMemPool(&S->pool, S->dev) == cudaSuccess) {
-      cudaMemPoolGetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &S->pool_old);
-      uint64_t thr = (uint64_t)cfg->budget_bytes;
-      cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &thr);
-    } else {
-      cudaGetLastError();
-      S->pool = nullptr;
-    }
     S->st.resize(cfg->streams);
     for (auto &s : S->st)
       if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
@@ -670,7 +659,6 @@ extern "C" void spike_server_destroy(spike_server S) {
         cudaStreamSynchronize(s);
         cudaStreamDestroy(s);
       }
-    if (S->pool) cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &S->pool_old);
   }
   delete S;
 }

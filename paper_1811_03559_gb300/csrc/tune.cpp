@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "spike.h"
+#include "internal.h"
 
 namespace {
 
@@ -63,7 +64,7 @@ extern "C" int spike_measure_K(const double *band, int64_t ldab, int64_t n, int 
   const int64_t n0 = std::min<int64_t>(n, 1 << 16);  // leading block: a band matrix with the same layout
   double *F = nullptr;
   const size_t fb = sizeof(double) * (size_t)n0 * k;
-  if (cudaMallocAsync((void **)&F, fb, st) != cudaSuccess || cudaMemsetAsync(F, 0, fb, st) != cudaSuccess) {
+  if (spk::dev_alloc((void **)&F, fb, st) != cudaSuccess || cudaMemsetAsync(F, 0, fb, st) != cudaSuccess) {
     cudaGetLastError();
     if (F) cudaFreeAsync(F, st);
     return SPIKE_ENOMEM;
@@ -112,7 +113,7 @@ extern "C" int spike_tune(const double *band, int64_t ldab, int64_t n, int kl, i
   out->K_measured = K;
   double *F = nullptr;
   const size_t fb = sizeof(double) * (size_t)n * nrhs;
-  if (cudaMallocAsync((void **)&F, fb, st) != cudaSuccess || cudaMemsetAsync(F, 0, fb, st) != cudaSuccess) {
+  if (spk::dev_alloc((void **)&F, fb, st) != cudaSuccess || cudaMemsetAsync(F, 0, fb, st) != cudaSuccess) {
     cudaGetLastError();
     if (F) cudaFreeAsync(F, st);
     return SPIKE_ENOMEM;

@@ -54,7 +54,8 @@ EXPORTS = ["spike_plan", "spike_factor", "spike_factor_ex", "spike_solve", "spik
            "spike_get_info", "spike_get_tips", "spike_backward_error", "spike_get_timings", "spike_kernel_launches",
            "spike_free", "spike_strerror", "spike_last_cuda_error", "spike_backward_error_noalloc",
            "spike_measure_fp64_peak", "spike_factor_bytes", "spike_solve_workspace", "spike_solve_ws",
-           "spike_measure_K", "spike_tune", "spike_solve_batch", "spike_solve_batch_workspace"]
+           "spike_measure_K", "spike_tune", "spike_solve_batch", "spike_solve_batch_workspace",
+           "spike_release_cached"]
 SPIKE_ELIMIT = -1006
 NOALLOC_MAX_NRHS = 1024
 
@@ -104,6 +105,7 @@ def lib():
         L.spike_solve_ws.argtypes = [vp, dp, i64, i32, ctypes.c_char, vp, i64]
         L.spike_measure_K.argtypes = [dp, i64, i64, i32, i32, vp, ctypes.POINTER(ctypes.c_double)]
         L.spike_solve_batch.argtypes = [vp, vp, vp, i32, ctypes.c_char, vp, vp, i64]
+        L.spike_release_cached.argtypes = [ctypes.POINTER(i64), ctypes.POINTER(i64)]
         L.spike_solve_batch_workspace.argtypes = [vp, vp, i32, ctypes.c_char, ctypes.POINTER(i64)]
         L.spike_tune.argtypes = [dp, i64, i64, i32, i32, i32, i32, vp, i32, vp, i32, vp, vp,
                                  ctypes.POINTER(TuneResult)]
@@ -271,6 +273,15 @@ def factor_bytes(n, kl, ku, p, pivot=0, mixed=False, host_band=False, K=0.0, nrh
     if rc != 0:
         raise SpikeError(rc, "spike_factor_bytes")
     return res.value, tr.value
+
+
+def release_cached():
+    """Return the library pools' cached device memory to the driver: (reserved before, after)."""
+    a, b = ctypes.c_int64(0), ctypes.c_int64(0)
+    rc = lib().spike_release_cached(ctypes.byref(a), ctypes.byref(b))
+    if rc != 0:
+        raise SpikeError(rc, "spike_release_cached")
+    return a.value, b.value
 
 
 def measure_K(band, kl, ku):

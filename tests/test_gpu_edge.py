@@ -72,3 +72,14 @@ def test_zero_pivot_without_pivoting_is_boosted():
     Xp = _dev(F)
     piv.solve(Xp, "N")
     assert metrics.backward_error(band, k, k, Xp.cpu().numpy(), F, "N") <= 1e-13
+
+
+def test_library_pool_keeps_and_releases_memory():
+    """Freed factorizations stay in the library's pool (reused by the next one) until
+    spike_release_cached hands them back to the driver."""
+    band, _ = inputs.make_band(200_000, 16, 16, seed=2)
+    fac = spike.factor(_dev(band), 16, 16, 32)
+    fac.free()
+    before, after = spike.release_cached()
+    assert before >= 8 * 200_000 * 33  # at least the freed factor storage was still held
+    assert after < before

@@ -150,7 +150,11 @@ def test_gpu_backward_error_kernel_matches_oracle():
         be_gpu = spike.backward_error(_dev(pr["band"]), 12, 9, _dev(X), _dev(F), trans)
         for c in range(3):
             be_cpu = metrics.backward_error(pr["band"], 12, 9, X[c:c + 1], F[c:c + 1], trans)
-            assert be_gpu[c] == pytest.approx(be_cpu, rel=1e-6, abs=1e-30)
+            # two evaluations of the same residual in different summation orders differ by at
+            # most ~(kl+ku+1) u ||A|| ||x||, i.e. (kl+ku+1) u in backward-error units
+            assert abs(be_gpu[c] - be_cpu) <= 4 * (12 + 9 + 1) * np.finfo(float).eps, (trans, c)
+            if trans == "T" or c == 1:
+                assert be_cpu > 1e-12  # the planted residual is visible
 
 
 @pytest.mark.parametrize("n,kl,ku,m", [(1000, 12, 9, 8), (20_011, 5, 17, 40), (50, 3, 2, 16),
