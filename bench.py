@@ -202,6 +202,47 @@ def load_traffic():
     return d.get("dram_bytes_per_launch_full"), d
 
 
+def mixed_workload_leg(dev, reps=2):
+    """The mixed-precision workload (n = 2^20, DD 1.05, k in {64, 256}, nrhs in {1, 32, 256}):
+    factor + one N solve, FP64 against SPIKE_FLAG_MIXED (FP32 blocks + FP64 refinement), with the
+    backward error of each.  Inputs are drawn on the device (inputs.make_band_torch)."""
+    import torch
+    from paper_1811_03559_gb300 import inputs, spike
+    n, dd, p = 1 << 20, 1.05, 148
+    out = {"workload": "n=%d DD=%g p=%d: spike_factor + spike_solve N, FP64 vs mixed" % (n, dd, p), "cases": []}
+    for k in (64, 256):
+        band = inputs.make_band_torch(n, k, k, seed=3, dd=dd, device=dev)
+        for m in (1, 32, 256):
+            g = torch.Generator(device=dev)
+            g.manual_seed(7 + m)
+            xs = torch.rand((m, n), generator=g, dtype=torch.float64, device=dev) * 2.0 - 1.0
+            F = inputs.band_matvec_torch(band, k, k, xs, "N")
+            row = {"k": k, "nrhs": m}
+            for mixed in (False, True):
+                times = []
+                X = None
+                for _ in range(reps + 1):
+                    X = F.clone()
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    fac = spike.Factorization(band, k, k, p, nrhs_hint=m, stage_balance=True, mixed=mixed)
+                    fac.solve(X, "N")
+                    torch.cuda.synchronize()
+                    times.append(time.perf_counter() - t0)
+                    steps = fac.info()["refine_steps"]
+                    fac.free()
+                key = "mixed" if mixed else "fp64"
+                row[key + "_ms"] = 1e3 * float(np.median(times[1:]))
+                row[key + "_backward_error"] = float(spike.backward_error(band, k, k, X, F, "N").max())
+                if mixed:
+                    row["refine_steps"] = steps
+            row["speedup"] = row["fp64_ms"] / row["mixed_ms"]
+            out["cases"].append(row)
+            del xs, F
+        del band
+    return out
+
+
 def _cpu_serve_one(args):
     """One request of the serving workload on the CPU oracle: banded GEPP + solve (one core)."""
     import oracle
@@ -584,6 +625,9 @@ def main():
             e2e_s += dt
     e2e_step_s = e2e_s / args.e2e_steps if args.e2e_steps > 0 else float("nan")
 
+    mixed_workload = None
+    if not args.no_mixed and rank == 0:
+        mixed_workload = mixed_workload_leg(dev)
     tuning = None
     if not args.no_tune and rank == 0:
         tuning = tuning_leg(band, k, m)
@@ -629,7 +673,7 @@ def main():
                 "h2d_bytes_per_step": int(8 * n * (2 * k + 1) + 2 * 8 * n * m),
                 "d2h_bytes_per_step": int(2 * 8 * n * m), "steps": args.e2e_steps,
                 "ms_per_step": e2e_step_s * 1e3},
-        "variants": {"mixed_fp32_fp64_refinement": mixed},
+        "variants": {"mixed_fp32_fp64_refinement": mixed, "mixed_precision_workload": mixed_workload},
         "serving": serving,
         "tuning": tuning,
         "gpu_launches": int(launches),
