@@ -202,6 +202,40 @@ def load_traffic():
     return d.get("dram_bytes_per_launch_full"), d
 
 
+def graphs_leg(dev, solves=200):
+    """Repeated solves of small systems, direct launches against CUDA-graph replay
+    (SPIKE_FLAG_GRAPHS): wall microseconds per solve on a side stream (F re-copied into X each
+    time, in both variants)."""
+    import torch
+    from paper_1811_03559_gb300 import inputs, spike
+    s = torch.cuda.Stream()
+    out = {}
+    for n, k, p, m in [(20_000, 16, 16, 4), (200_000, 64, 64, 16)]:
+        band = inputs.make_band_torch(n, k, k, seed=9, dd=1.1, device=dev)
+        res = {}
+        with torch.cuda.stream(s):
+            for graphs in (False, True):
+                fac = spike.Factorization(band, k, k, p, graphs=graphs)
+                F = torch.rand((m, n), dtype=torch.float64, device=dev)
+                X = F.clone()
+                for _ in range(3):  # direct, captured, replayed
+                    X.copy_(F)
+                    fac.solve(X, "N")
+                s.synchronize()
+                t0 = time.perf_counter()
+                for _ in range(solves):
+                    X.copy_(F)
+                    fac.solve(X, "N")
+                s.synchronize()
+                res["graphs_us" if graphs else "direct_us"] = 1e6 * (time.perf_counter() - t0) / solves
+                if graphs:
+                    res["graph_replays"] = fac.info()["graph_replays"]
+                fac.free()
+        res["speedup"] = res["direct_us"] / res["graphs_us"]
+        out["n=%d k=%d p=%d nrhs=%d" % (n, k, p, m)] = res
+    return out
+
+
 def mixed_workload_leg(dev, reps=2):
     """The mixed-precision workload (n = 2^20, DD 1.05, k in {64, 256}, nrhs in {1, 32, 256}):
     factor + one N solve, FP64 against SPIKE_FLAG_MIXED (FP32 blocks + FP64 refinement), with the
@@ -628,6 +662,7 @@ def main():
     mixed_workload = None
     if not args.no_mixed and rank == 0:
         mixed_workload = mixed_workload_leg(dev)
+    graphs = graphs_leg(dev) if rank == 0 and not args.no_tune else None
     tuning = None
     if not args.no_tune and rank == 0:
         tuning = tuning_leg(band, k, m)
@@ -673,7 +708,8 @@ def main():
                 "h2d_bytes_per_step": int(8 * n * (2 * k + 1) + 2 * 8 * n * m),
                 "d2h_bytes_per_step": int(2 * 8 * n * m), "steps": args.e2e_steps,
                 "ms_per_step": e2e_step_s * 1e3},
-        "variants": {"mixed_fp32_fp64_refinement": mixed, "mixed_precision_workload": mixed_workload},
+        "variants": {"mixed_fp32_fp64_refinement": mixed, "mixed_precision_workload": mixed_workload,
+                     "cuda_graphs_repeated_solves": graphs},
         "serving": serving,
         "tuning": tuning,
         "gpu_launches": int(launches),

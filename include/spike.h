@@ -79,6 +79,15 @@ extern "C" {
  * band must then stay valid and unchanged until spike_free.  Ignored for host bands
  * and FP64 handles. */
 #define SPIKE_FLAG_BORROW_BAND 16
+/* CUDA graphs for repeated solves: an FP64 solve of device buffers is run directly the
+ * first time a call (nrhs, trans, F pointer, ldf, scratch) is seen, captured as a CUDA
+ * graph the second time, and replayed from then on (up to 8 graphs per handle, least
+ * recently used replaced).  A replay launches the whole solve at once instead of a few
+ * dozen separate launches; results are those of the direct launches.  The buffers a
+ * graph was captured with must not be freed while it may be replayed (F is the caller's;
+ * the scratch is the handle's own or the spike_solve_ws workspace).  Not used with
+ * SPIKE_FLAG_TIMING, mixed precision, host F or the legacy default stream (NULL). */
+#define SPIKE_FLAG_GRAPHS 32
 #define SPIKE_MIXED_TOL 1e-14
 #define SPIKE_MIXED_MAX_STEPS 10
 
@@ -152,6 +161,8 @@ typedef struct {
   int32_t mixed;            /* 1: SPIKE_FLAG_MIXED handle */
   int32_t refine_steps;     /* mixed: FP64 refinement steps of the last solve */
   double refine_berr;       /* mixed: max backward error over columns after the last solve */
+  int64_t graph_captures;   /* SPIKE_FLAG_GRAPHS: solves captured as CUDA graphs */
+  int64_t graph_replays;    /* SPIKE_FLAG_GRAPHS: solves replayed from a captured graph */
 } spike_info;
 
 /* Compute the partition plan for (n, kl, ku, p) without touching a GPU (Sec. 3.1, 3.3).

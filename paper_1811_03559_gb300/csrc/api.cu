@@ -222,6 +222,18 @@ struct TrsBatch {
 
 }  // namespace
 
+// A solve captured as a CUDA graph (SPIKE_FLAG_GRAPHS): replayed when the same call
+// (columns, trans, right-hand-side buffer, scratch) comes again.
+struct GraphEntry {
+  int m = 0, tr = 0;
+  const double *F = nullptr;
+  int64_t ld = 0;
+  const char *scratch = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  char *args = nullptr;  // the graph's own copy of the descriptor arena
+  uint64_t last = 0;
+};
+
 struct spike_ctx {
   uint32_t magic = kMagic;
   Plan pl;
@@ -234,6 +246,11 @@ struct spike_ctx {
   double *couple = nullptr, *spk = nullptr, *mlu = nullptr, *ident = nullptr;
   int f32 = 0;                             // SPIKE_FLAG_MIXED: FP32 leaf factors and sweeps
   int invariant = 0;                       // SPIKE_FLAG_BATCH_INVARIANT
+  int graphs = 0;                          // SPIKE_FLAG_GRAPHS
+  std::vector<GraphEntry> gcache;          // captured solves (at most kGraphCache)
+  std::vector<GraphEntry> gseen;           // calls seen once (captured on their second use)
+  uint64_t gtick = 0;
+  int64_t graph_captures = 0, graph_replays = 0;
   int in_solve = 0;                        // descriptors being built belong to a solve
   size_t es = sizeof(double);
   double *band64 = nullptr;                // mixed: FP64 copy of the band for the refinement residuals
@@ -713,6 +730,7 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
   c->timing = opt && (opt->flags & SPIKE_FLAG_TIMING);
   c->f32 = (opt && (opt->flags & SPIKE_FLAG_MIXED)) ? 1 : 0;
   c->invariant = (opt && (opt->flags & SPIKE_FLAG_BATCH_INVARIANT)) ? 1 : 0;
+  c->graphs = (opt && (opt->flags & SPIKE_FLAG_GRAPHS)) ? 1 : 0;
   if (opt && opt->refine_tol > 0.0) c->refine_tol = opt->refine_tol;
   c->es = c->f32 ? sizeof(float) : sizeof(double);
   if (c->f32 && pivot) {
@@ -1363,6 +1381,60 @@ static void build_solve_body(spike_ctx *c, Pipeline &pp, const SolveBufs &B, int
   }
 }
 
+constexpr size_t kGraphCache = 8;
+
+static void drop_graph(GraphEntry &g, cudaStream_t s) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (g.args) cudaFreeAsync(g.args, s);
+  g.exec = nullptr;
+  g.args = nullptr;
+}
+
+// Capture the recorded launches of a solve into a CUDA graph with its own descriptor
+// buffer, keep it in the handle's cache (least recently used one replaced) and launch it.
+static int capture_solve(spike_ctx *c, Pipeline &pp, cudaStream_t s, int m, int tr, const double *F, int64_t ld,
+                         const char *scratch) {
+  GraphEntry g;
+  g.m = m;
+  g.tr = tr;
+  g.F = F;
+  g.ld = ld;
+  g.scratch = scratch;
+  if (!pp.ar.h.empty()) {
+    SP_CUDA(dev_alloc((void **)&g.args, pp.ar.h.size(), s));
+    SP_CUDA(cudaMemcpyAsync(g.args, pp.ar.h.data(), pp.ar.h.size(), cudaMemcpyHostToDevice, s));
+  }
+  cudaGraph_t graph = nullptr;
+  SP_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  const int rc = pp.run_ops(g.args);
+  const cudaError_t ec = cudaStreamEndCapture(s, &graph);
+  if (rc != 0 || ec != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    if (g.args) cudaFreeAsync(g.args, s);
+    if (rc != 0) return rc;
+    g_cuda_err = std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ec);
+    return SPIKE_ECUDA;
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) {
+    if (g.args) cudaFreeAsync(g.args, s);
+    g_cuda_err = std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ei);
+    return SPIKE_ECUDA;
+  }
+  g.last = ++c->gtick;
+  ++c->graph_captures;
+  if (c->gcache.size() >= kGraphCache) {
+    auto lru = std::min_element(c->gcache.begin(), c->gcache.end(),
+                                [](const GraphEntry &a, const GraphEntry &b) { return a.last < b.last; });
+    drop_graph(*lru, s);
+    c->gcache.erase(lru);
+  }
+  c->gcache.push_back(g);
+  SP_CUDA(cudaGraphLaunch(g.exec, s));
+  return 0;
+}
+
 // The solve.  Scratch comes from `ws` (ws_bytes) when given, else from the handle's own
 // buffer (grown on demand).  With need != nullptr only the scratch size is computed
 // (F may then be null; host_f says whether F would be host memory).
@@ -1438,6 +1510,38 @@ static int solve_impl(spike_handle h, double *F, int64_t ldf, int nrhs, char tra
   B.PP = (double *)(base + o_p);
   cudaEvent_t *evs = tr ? c->tev : c->nev;
 
+  // SPIKE_FLAG_GRAPHS: FP64 solves of device buffers are replayed from a CUDA graph once the
+  // same call has been seen before (the first run also sets every kernel attribute, so the
+  // capture contains launches, memsets and device copies only)
+  // (stream capture needs a stream other than the legacy default one)
+  const bool use_graph = !mixed && c->graphs && fdev && !c->timing && s != nullptr && s != cudaStreamLegacy;
+  GraphEntry *hit = nullptr;
+  bool capture = false;
+  if (use_graph) {
+    auto same = [&](const GraphEntry &g) {
+      return g.m == m && g.tr == tr && g.F == Fd && g.ld == ld && g.scratch == base;
+    };
+    for (auto &g : c->gcache)
+      if (same(g)) hit = &g;
+    if (hit) {
+      hit->last = ++c->gtick;
+      ++c->graph_replays;
+      SP_CUDA(cudaGraphLaunch(hit->exec, s));
+      return 0;
+    }
+    for (auto &g : c->gseen)
+      if (same(g)) capture = true;
+    if (!capture) {
+      GraphEntry g;
+      g.m = m;
+      g.tr = tr;
+      g.F = Fd;
+      g.ld = ld;
+      g.scratch = base;
+      if (c->gseen.size() >= 16) c->gseen.erase(c->gseen.begin());
+      c->gseen.push_back(g);
+    }
+  }
   if (!mixed) {
     Pipeline pp;
     pp.st = s;
@@ -1459,6 +1563,10 @@ static int solve_impl(spike_handle h, double *F, int64_t ldf, int nrhs, char tra
     if (c->timing) {
       cudaEvent_t e = evs[3];
       pp.ops.push_back([=](char *) { return (int)cudaEventRecord(e, s); });
+    }
+    if (capture) {
+      SP_TRY(capture_solve(c, pp, s, m, tr, Fd, ld, base));
+      return 0;
     }
     SP_TRY(pp.run(c));
     if (c->timing) (tr ? c->tdone : c->ndone) = true;
@@ -1692,6 +1800,8 @@ extern "C" int spike_get_info(spike_handle h, spike_info *out) {
   out->mixed = h->f32;
   out->refine_steps = h->last_iters;
   out->refine_berr = h->last_berr;
+  out->graph_captures = h->graph_captures;
+  out->graph_replays = h->graph_replays;
   return 0;
 }
 
@@ -1797,6 +1907,9 @@ extern "C" int64_t spike_kernel_launches(void) { return (int64_t)g_launches.load
 extern "C" void spike_free(spike_handle h) {
   if (!valid(h)) return;
   cudaStream_t s = h->stream;
+  cudaStreamSynchronize(s);
+  for (auto &g : h->gcache) drop_graph(g, s);
+  h->gcache.clear();
   if (h->mem) cudaFreeAsync(h->mem, s);
   if (h->scr) cudaFreeAsync(h->scr, s);
   if (h->dargs) cudaFreeAsync(h->dargs, s);

@@ -29,7 +29,8 @@ class SpikeInfo(ctypes.Structure):
                 ("n2", ctypes.c_int64), ("n3", ctypes.c_int64), ("R12", ctypes.c_double), ("R13", ctypes.c_double),
                 ("K", ctypes.c_double), ("boosts", ctypes.c_int64), ("zero_pivot_col", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("mixed", ctypes.c_int32), ("refine_steps", ctypes.c_int32),
-                ("refine_berr", ctypes.c_double)]
+                ("refine_berr", ctypes.c_double), ("graph_captures", ctypes.c_int64),
+                ("graph_replays", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -64,6 +65,7 @@ FLAG_STAGE_BALANCE = 2
 FLAG_MIXED = 4
 FLAG_BATCH_INVARIANT = 8
 FLAG_BORROW_BAND = 16
+FLAG_GRAPHS = 32
 MIXED_TOL = 1e-14
 STAGES = ["factor", "setup", "block_lu", "spikes", "reduced", "solve_n", "solve_n_d", "solve_n_reduced",
           "solve_n_retrieval", "solve_t", "solve_t_s", "solve_t_reduced", "solve_t_d"]
@@ -163,14 +165,14 @@ class Factorization:
 
     def __init__(self, band, kl, ku, p, pivot=0, K=0.0, nrhs_hint=0, stream=None, timing=False, n=None,
                  stage_balance=False, mixed=False, batch_invariant=False, R13=0.0, borrow_band=False,
-                 refine_tol=0.0):
+                 refine_tol=0.0, graphs=False):
         rows, ldab = band.shape
         self.n, self.kl, self.ku = (rows if n is None else n), kl, ku
         n = self.n
         s = _torch_stream(band) if stream is None else ctypes.c_void_p(stream)
         flags = (FLAG_TIMING if timing else 0) | (FLAG_STAGE_BALANCE if stage_balance else 0) | \
             (FLAG_MIXED if mixed else 0) | (FLAG_BATCH_INVARIANT if batch_invariant else 0) | \
-            (FLAG_BORROW_BAND if borrow_band else 0)
+            (FLAG_BORROW_BAND if borrow_band else 0) | (FLAG_GRAPHS if graphs else 0)
         self._opt = SpikeOptions(K=K, nrhs_hint=nrhs_hint, flags=flags, stream=s, R13=R13, refine_tol=refine_tol)
         h = ctypes.c_void_p()
         rc = lib().spike_factor_ex(_ptr(band), ldab, n, kl, ku, p, pivot, ctypes.byref(self._opt), ctypes.byref(h))
