@@ -589,8 +589,11 @@ def main():
 
     # mixed-precision variant (SPIKE_FLAG_MIXED: FP32 blocks + FP64 refinement) against plain FP64,
     # on this step (nrhs = m) and with nrhs = 1, where the factorization dominates.
+    # the variant, tuning and serving legs run at N = 1 only (under torchrun they would run on
+    # rank 0 alone while the other ranks hold their GPUs)
+    extras = world == 1
     mixed = None
-    if not args.no_mixed:
+    if not args.no_mixed and extras:
         def variant(nr, use_mixed):
             A1, A2 = F1src[:nr], F2src[:nr]
             B1, B2 = torch.empty_like(A1), torch.empty_like(A2)
@@ -660,17 +663,17 @@ def main():
     e2e_step_s = e2e_s / args.e2e_steps if args.e2e_steps > 0 else float("nan")
 
     mixed_workload = None
-    if not args.no_mixed and rank == 0:
+    if not args.no_mixed and extras:
         mixed_workload = mixed_workload_leg(dev)
-    graphs = graphs_leg(dev) if rank == 0 and not args.no_tune else None
+    graphs = graphs_leg(dev) if extras and not args.no_tune else None
     tuning = None
-    if not args.no_tune and rank == 0:
+    if not args.no_tune and extras:
         tuning = tuning_leg(band, k, m)
     cpu_serve = None
-    if not args.no_serve and not args.no_cpu and rank == 0:
+    if not args.no_serve and not args.no_cpu and extras:
         cpu_serve = cpu_serving_baseline()
     serving = None
-    if not args.no_serve and rank == 0:
+    if not args.no_serve and extras:
         serving = serving_leg(dev, args.serve_requests, args.serve_streams, args.serve_batch, args.serve_passes,
                               batch_systems=args.serve_batch_systems)
         serving["cpu_baseline"] = cpu_serve
