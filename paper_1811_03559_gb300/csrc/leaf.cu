@@ -29,7 +29,9 @@ namespace spk {
 constexpr int WCH = 256;  // sweep window rows per staged chunk
 constexpr int SCW = 128;  // RHS columns per sweep pass: 8 warps x 16 accumulators
 constexpr int WSPLIT = NTHREADS / 32;  // fixed sub-ranges of each window chunk (one per warp)
-constexpr size_t SWEEP_SMEM = sizeof(double) * ((size_t)WCH * NB + NB * NB + NB + (size_t)NB * (SCW + 1));
+// two buffers of the block coefficients (window Tw, diagonal block Td, reciprocals) so the next
+// block's are copied in while the current one computes, plus the right-hand-side block Gs
+constexpr size_t SWEEP_SMEM = sizeof(double) * (2 * ((size_t)WCH * NB + NB * NB + NB) + (size_t)NB * (SCW + 1));
 
 // ------------------------------------------------------------------ repack
 // User band (LAPACK layout, global frame) -> per-leaf LU band (local frame),
@@ -461,6 +463,26 @@ __device__ __forceinline__ T coef(int kind, const T *fb, int ldf, int dofs, int6
   return fb[r * ldf + dofs + c - r];
 }
 
+template <typename T>
+__device__ __forceinline__ const T *coef_ptr(int kind, const T *fb, int ldf, int dofs, int64_t r, int64_t c) {
+  if (kind == LN || kind == UN) return fb + (c * ldf + dofs + r - c);
+  return fb + (r * ldf + dofs + c - r);
+}
+
+// Asynchronous copy of one element global -> shared (cp.async); with valid == false nothing
+// is read and the element is zero-filled.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T *dst, const T *src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = valid ? (int)sizeof(T) : 0;
+  if (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // acc[q] += sum_j Tw[j*NB] * X(row_j, col_base + q), rows row_j = row_0 + j (stride xstep),
 // for q < C.  Columns past `lastc` are clamped (their accumulators are never stored).
 template <typename T, int C>
@@ -493,12 +515,56 @@ __device__ void sweep_run(const SweepDesc &D, int ldf, int dofs, T *sm) {
   const bool FWD = (kind == LN || kind == UT);
   const bool UNIT = (kind == LN || kind == LT);
   const int GLD = SCW + 1;
-  T *Tw = sm;                 // WCH x NB   : Tw[j*NB + a] = T(row(a), wrow(j))
-  T *Td = Tw + WCH * NB;      // NB x NB    : Td[a'*NB + a] = T(row(a), row(a'))
-  T *dsm = Td + NB * NB;      // NB
-  T *Gs = dsm + NB;           // NB x GLD
+  // per buffer: WCH x NB Tw[j*NB + a] = T(row(a), wrow(j)); NB x NB Td[a'*NB + a] = T(row(a), row(a'));
+  // NB reciprocals (1 for unit triangles)
+  constexpr int BUF = WCH * NB + NB * NB + NB;
+  T *Gs = sm + 2 * BUF;       // NB x GLD
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nwarps = NTHREADS / 32;
+  // When a block's window fits one staged chunk (kw <= WCH), the coefficients of block
+  // bk+1 are copied asynchronously into the other buffer while block bk computes (they
+  // are factor entries, independent of the results).
+  const bool pre = kw <= WCH;
+  const int nblk = (D.r1 - D.r0 + NB - 1) / NB;
+  auto geom = [&](int bk, int64_t &b0, int64_t &b1, int &nbk, int &jlo, int &jhi) {
+    if (FWD) {
+      b0 = D.r0 + (int64_t)bk * NB;
+      nbk = (int)min((int64_t)NB, D.r1 - b0);
+      b1 = 0;
+      jlo = (int)max((int64_t)0, D.r0 - (b0 - kw));
+      jhi = kw;
+    } else {
+      b1 = D.r1 - (int64_t)bk * NB;
+      nbk = (int)min((int64_t)NB, b1 - D.r0);
+      b0 = 0;
+      jlo = 0;
+      jhi = (int)min((int64_t)kw, D.r1 - b1);
+    }
+  };
+  auto stage_async = [&](int bk, int buf) {
+    int64_t b0, b1;
+    int nbk, jlo, jhi;
+    geom(bk, b0, b1, nbk, jlo, jhi);
+    auto row = [&](int a) -> int64_t { return FWD ? (b0 + a) : (b1 - 1 - a); };
+    auto wrow = [&](int j) -> int64_t { return FWD ? (b0 - kw + j) : (b1 + j); };
+    T *Twb = sm + buf * BUF, *Tdb = Twb + WCH * NB, *dsb = Tdb + NB * NB;
+    for (int idx = tid; idx < NB * NB; idx += NTHREADS) {
+      const int ap = idx / NB, a = idx - ap * NB;
+      const bool v = ap < a && a < nbk && a - ap <= kw;
+      cp_async_elem(Tdb + idx, v ? coef_ptr<T>(kind, dfb, ldf, dofs, row(a), row(ap)) : dfb, v);
+    }
+    for (int a = tid; a < NB; a += NTHREADS) {
+      if (UNIT) dsb[a] = (a < nbk) ? (T)1 : (T)0;
+      else cp_async_elem(dsb + a, a < nbk ? ddinv + row(a) : ddinv, a < nbk);
+    }
+    const int tot = (jhi - jlo) * NB;
+    for (int idx = tid; idx < tot; idx += NTHREADS) {
+      const int jj = idx / NB, a = idx - jj * NB, j = jlo + jj;
+      const bool v = a < nbk && (FWD ? (j >= a) : (j <= kw - 1 - a));
+      cp_async_elem(Twb + idx, v ? coef_ptr<T>(kind, dfb, ldf, dofs, row(a), wrow(j)) : dfb, v);
+    }
+    cp_async_commit();
+  };
 
   for (int c0 = 0; c0 < D.ncols; c0 += SCW) {
     const int cw = min(SCW, D.ncols - c0);
@@ -530,31 +596,24 @@ __device__ void sweep_run(const SweepDesc &D, int ldf, int dofs, T *sm) {
     }
     const int lastc = c0 + cw - 1;
     const bool owns = col_base <= lastc;
-    const int nblk = (D.r1 - D.r0 + NB - 1) / NB;
+    if (pre) {
+      __syncthreads();  // the buffers may still be read by the previous pass / sweep
+      stage_async(0, 0);
+    }
     for (int bk = 0; bk < nblk; ++bk) {
       int64_t b0, b1;
-      int nbk;
-      if (FWD) {
-        b0 = D.r0 + (int64_t)bk * NB;
-        nbk = (int)min((int64_t)NB, D.r1 - b0);
-        b1 = 0;
-      } else {
-        b1 = D.r1 - (int64_t)bk * NB;
-        nbk = (int)min((int64_t)NB, b1 - D.r0);
-        b0 = 0;
-      }
+      int nbk, jlo, jhi;
+      geom(bk, b0, b1, nbk, jlo, jhi);
       auto row = [&](int a) -> int64_t { return FWD ? (b0 + a) : (b1 - 1 - a); };
       auto wrow = [&](int j) -> int64_t { return FWD ? (b0 - kw + j) : (b1 + j); };
-      int jlo, jhi;
-      if (FWD) {
-        jlo = (int)max((int64_t)0, D.r0 - (b0 - kw));
-        jhi = kw;
+      const int buf = pre ? (bk & 1) : 0;
+      T *Tw = sm + buf * BUF, *Td = Tw + WCH * NB, *dsm = Td + NB * NB;
+      if (pre) {
+        cp_async_wait_all();
+        __syncthreads();  // this block's coefficients are in; the other buffer is free
+        if (bk + 1 < nblk) stage_async(bk + 1, buf ^ 1);
       } else {
-        jlo = 0;
-        jhi = (int)min((int64_t)kw, D.r1 - b1);
-      }
-      __syncthreads();
-      {
+        __syncthreads();
         T v[NB * NB / NTHREADS];
 #pragma unroll
         for (int u = 0; u < NB * NB / NTHREADS; ++u) {
@@ -564,8 +623,8 @@ __device__ void sweep_run(const SweepDesc &D, int ldf, int dofs, T *sm) {
         }
 #pragma unroll
         for (int u = 0; u < NB * NB / NTHREADS; ++u) Td[tid + u * NTHREADS] = v[u];
+        for (int a = tid; a < NB; a += NTHREADS) dsm[a] = (a < nbk) ? (UNIT ? (T)1 : ddinv[row(a)]) : (T)0;
       }
-      for (int a = tid; a < NB; a += NTHREADS) dsm[a] = (a < nbk) ? (UNIT ? (T)1 : ddinv[row(a)]) : (T)0;
       if (fixed) {  // G block first (rows past the block end are zero)
         for (int idx = tid; idx < NB * cw; idx += NTHREADS) {
           const int a = idx % NB, cc = idx / NB, col = c0 + cc;
@@ -584,8 +643,8 @@ __device__ void sweep_run(const SweepDesc &D, int ldf, int dofs, T *sm) {
       for (int q = 0; q < 16; ++q) acc[q] = (T)0;
       for (int jc0 = jlo; jc0 < jhi; jc0 += WCH) {
         const int jce = min(jhi, jc0 + WCH);
-        __syncthreads();
-        const int tot = (jce - jc0) * NB;
+        const int tot = pre ? 0 : (jce - jc0) * NB;  // prefetched: the window is already staged
+        if (!pre) __syncthreads();
         for (int base = tid; base < tot; base += NTHREADS * 8) {
           T v[8];
 #pragma unroll
@@ -599,7 +658,7 @@ __device__ void sweep_run(const SweepDesc &D, int ldf, int dofs, T *sm) {
           for (int u = 0; u < 8; ++u)
             if (base + u * NTHREADS < tot) Tw[base + u * NTHREADS] = v[u];
         }
-        __syncthreads();
+        if (!pre) __syncthreads();
         const int per = (jce - jc0 + nsplit - 1) / nsplit;
         // A predicated-off DFMA still occupies the FP64 pipe, so the accumulation loop is
         // instantiated for the exact column count; edge columns are clamped, not predicated.
