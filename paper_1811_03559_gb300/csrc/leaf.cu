@@ -636,6 +636,9 @@ __device__ void sweep_run(const SweepDesc &D, int ldf, int dofs, T *sm) {
           }
           Gs[a * GLD + cc] = g;
         }
+        // the window products below are subtracted by other threads (lanes <-> rows); without
+        // the staging barriers of the synchronous path this one orders the two
+        if (pre) __syncthreads();
       }
 
       T acc[16];
