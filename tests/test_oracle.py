@@ -2,8 +2,8 @@
 
 Each check ties the oracle to something other than itself: exact rational
 arithmetic, LAPACK's own banded factorization (pivot sequence), an independent
-dense elimination, closed-form solutions, the transpose identity, and the
-identities between GEPP, non-pivoting LU and UL that the SPIKE partitions rely
+dense elimination, closed-form solutions, the transpose identity, the factors
+multiplied back into A, and the identities between GEPP, non-pivoting LU and UL that the SPIKE partitions rely
 on (Sec. 2.3, Sec. 5.2).
 """
 import numpy as np
@@ -242,6 +242,71 @@ def test_ul_is_reversed_lu():
         for d in range(2 * k + 1):
             back[j, d] = lu[n - 1 - j, 2 * k - d]
     np.testing.assert_array_equal(ul, back)
+
+
+# ------------------------------------------------------------- factor checks
+
+@pytest.mark.parametrize("seed", range(6))
+def test_gepp_factors_rebuild_the_matrix(seed):
+    """Multiplying the stored GEPP factors back together gives A: undo the elimination steps
+    from the last to the first (apply L_j, then the row swap j <-> ipiv[j]) starting from U,
+    and compare with the band's dense copy (Wilkinson's bound for GEPP: |A - P L U| is at
+    most a small multiple of n * eps * |L| |U|)."""
+    rng = np.random.default_rng(600 + seed)
+    n = int(rng.integers(20, 160))
+    kl, ku = int(rng.integers(1, 6)), int(rng.integers(1, 6))
+    band, _ = inputs.make_band(n, kl, ku, seed=seed, dist="normal", dd=0.3, keep_sign=True)
+    A = oracle.band_to_dense(band, kl, ku)
+    lu = oracle.BandLU(band, kl, ku)
+    assert lu.info == 0
+    kv = kl + ku  # row of the diagonal in the factor storage: fac[j, kv + i - j] holds entry (i, j)
+    U = np.zeros((n, n))
+    L = np.eye(n)
+    for j in range(n):
+        for i in range(max(0, j - kv), j + 1):
+            U[i, j] = lu.fac[j, kv + i - j]
+        for i in range(j + 1, min(n, j + kl + 1)):
+            L[i, j] = lu.fac[j, kv + i - j]
+    M = U.copy()
+    for j in range(n - 1, -1, -1):
+        M[j + 1:, :] += np.outer(L[j + 1:, j], M[j, :])
+        p = lu.ipiv[j]
+        assert j <= p <= min(n - 1, j + kl)  # a pivot comes from inside the band
+        M[[j, p], :] = M[[p, j], :]
+    assert np.all(np.abs(np.tril(L, -1)) <= 1.0)  # partial pivoting bounds the multipliers
+    bound = 4 * n * EPS * (np.abs(L) @ np.abs(U)).max()
+    assert np.abs(M - A).max() <= bound
+    # U fills to bandwidth kl + ku and no further
+    assert np.all(np.triu(U, kv + 1) == 0.0)
+
+
+@pytest.mark.parametrize("kind", ["LU", "UL"])
+@pytest.mark.parametrize("k", [(1, 1), (3, 2), (2, 5)])
+def test_nopiv_factors_rebuild_the_matrix(kind, k):
+    """A = L U (unit L) and A = U L (unit U) from the in-place non-pivoting band factors of
+    Sec. 2.3: the factors keep the band, L below and U above the diagonal."""
+    kl, ku = k
+    n = 90
+    band, _ = inputs.make_band(n, kl, ku, seed=31 + kl + 7 * ku, dd=1.2)
+    A = oracle.band_to_dense(band, kl, ku)
+    fac, info = oracle.nopiv_factor(band, kl, ku, kind)
+    assert info == 0
+    F = oracle.band_to_dense(fac, kl, ku)
+    lower, upper = np.tril(F, -1), np.triu(F, 1)
+    diag = np.diag(np.diag(F))
+    if kind == "LU":
+        L, U = np.eye(n) + lower, diag + upper
+        R = L @ U
+    else:
+        U, L = np.eye(n) + upper, diag + lower
+        R = U @ L
+    bound = 4 * n * EPS * (np.abs(L) @ np.abs(U) if kind == "LU" else np.abs(U) @ np.abs(L)).max()
+    assert np.abs(R - A).max() <= bound
+    if kind == "UL":
+        # the UL factorization eliminates from the bottom: its last diagonal entry is A(n-1, n-1)
+        assert F[n - 1, n - 1] == A[n - 1, n - 1]
+    else:
+        assert F[0, 0] == A[0, 0]
 
 
 def test_singular_reports_info():
