@@ -3,8 +3,8 @@
 Each check ties the oracle to something other than itself: exact rational
 arithmetic, LAPACK's own banded factorization (pivot sequence), an independent
 dense elimination, closed-form solutions, the transpose identity, the factors
-multiplied back into A, and the identities between GEPP, non-pivoting LU and UL that the SPIKE partitions rely
-on (Sec. 2.3, Sec. 5.2).
+multiplied back into A, and the identities between GEPP, non-pivoting LU and UL
+that the SPIKE partitions rely on (Sec. 2.3, Sec. 5.2).
 """
 import numpy as np
 import pytest
