@@ -99,8 +99,9 @@ class Server:
         """Queue op(A_mid) X = F; returns (request id, X).  X defaults to a new array like F."""
         if X is None:
             X = np.empty_like(F) if isinstance(F, np.ndarray) else F.clone()
-        nrhs = 1 if F.ndim == 1 else F.shape[0]
-        assert F.shape[-1] == self._n[mid] and X.shape == F.shape
+        nrhs = spike._check_rhs(F, self._n[mid])
+        if tuple(X.shape) != tuple(F.shape):
+            raise ValueError("X has shape %s, F has %s" % (tuple(X.shape), tuple(F.shape)))
         rid = _lib().spike_server_submit(self._h, mid, spike._ptr(F), spike._ptr(X), nrhs, trans.encode(),
                                          1 if mixed else 0)
         if rid < 0:
@@ -123,12 +124,19 @@ class Server:
         rc = _lib().spike_server_request_latency(self._h, rid, ctypes.byref(lat))
         if rc < 0:
             raise spike.SpikeError(rc, "spike_server_request_latency")
-        return lat.value if rc == 0 else None
+        if rc == 0:
+            self._keep.pop(rid, None)  # done: the engine no longer touches its buffers
+            return lat.value
+        return None
 
     def drain(self):
+        submitted = [key for key in list(self._keep) if not isinstance(key, tuple)]
         rc = _lib().spike_server_drain(self._h)
         if rc != 0:
             raise spike.SpikeError(rc, "spike_server_drain")
+        # the requests submitted before the drain have finished: release their F and X references
+        for key in submitted:
+            self._keep.pop(key, None)
 
     def stats(self):
         out = ServerStats()

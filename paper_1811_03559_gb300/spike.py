@@ -133,10 +133,18 @@ def _is_torch(x):
 
 def _ptr(x):
     if _is_torch(x):
-        assert x.is_contiguous() and str(x.dtype) == "torch.float64"
+        if not (x.is_contiguous() and str(x.dtype) == "torch.float64"):
+            raise ValueError("expected a contiguous float64 tensor, got %s %s" % (x.dtype, tuple(x.stride())))
         return ctypes.c_void_p(x.data_ptr())
-    assert isinstance(x, np.ndarray) and x.dtype == np.float64 and x.flags["C_CONTIGUOUS"]
+    if not (isinstance(x, np.ndarray) and x.dtype == np.float64 and x.flags["C_CONTIGUOUS"]):
+        raise ValueError("expected a C-contiguous float64 array or a CUDA float64 tensor")
     return x.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check_rhs(F, n):
+    if F.ndim not in (1, 2) or F.shape[-1] != n:
+        raise ValueError("right-hand sides must have shape (nrhs, %d) or (%d,), got %s" % (n, n, tuple(F.shape)))
+    return 1 if F.ndim == 1 else F.shape[0]
 
 
 def _torch_stream(x):
@@ -174,6 +182,8 @@ class Factorization:
             (FLAG_MIXED if mixed else 0) | (FLAG_BATCH_INVARIANT if batch_invariant else 0) | \
             (FLAG_BORROW_BAND if borrow_band else 0) | (FLAG_GRAPHS if graphs else 0)
         self._opt = SpikeOptions(K=K, nrhs_hint=nrhs_hint, flags=flags, stream=s, R13=R13, refine_tol=refine_tol)
+        # a borrowed device band is read by every mixed-precision solve until spike_free
+        self._borrowed = band if borrow_band else None
         h = ctypes.c_void_p()
         rc = lib().spike_factor_ex(_ptr(band), ldab, n, kl, ku, p, pivot, ctypes.byref(self._opt), ctypes.byref(h))
         self._h = h
@@ -183,8 +193,7 @@ class Factorization:
 
     def solve(self, F, trans="N"):
         """Overwrite F (shape (nrhs, n) or (n,)) with op(A)^{-1} F.  Returns F."""
-        nrhs = 1 if F.ndim == 1 else F.shape[0]
-        assert F.shape[-1] == self.n
+        nrhs = _check_rhs(F, self.n)
         rc = lib().spike_solve_ex(self._h, _ptr(F), self.n, nrhs, trans.encode())
         if rc != 0:
             raise SpikeError(rc, "spike_solve_ex")
@@ -200,8 +209,7 @@ class Factorization:
 
     def solve_ws(self, F, workspace, trans="N"):
         """solve() on caller-provided device scratch (a CUDA uint8 tensor of workspace_bytes)."""
-        nrhs = 1 if F.ndim == 1 else F.shape[0]
-        assert F.shape[-1] == self.n
+        nrhs = _check_rhs(F, self.n)
         rc = lib().spike_solve_ws(self._h, _ptr(F), self.n, nrhs, trans.encode(),
                                   ctypes.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size())
         if rc != 0:
@@ -241,6 +249,7 @@ class Factorization:
         if self._h:
             lib().spike_free(self._h)
             self._h = ctypes.c_void_p()
+        self._borrowed = None
 
     def __del__(self):
         try:
@@ -321,7 +330,9 @@ def solve_batch(facs, Fs, trans="N", workspace=None):
     ptrs = (ctypes.c_void_p * cnt)(*[F.data_ptr() for F in Fs])
     nr = (ctypes.c_int * cnt)(*[1 if F.ndim == 1 else F.shape[0] for F in Fs])
     for f, F in zip(facs, Fs):
-        assert F.is_cuda and F.is_contiguous() and F.shape[-1] == f.n
+        if not (F.is_cuda and F.is_contiguous()):
+            raise ValueError("solve_batch takes contiguous CUDA tensors")
+        _check_rhs(F, f.n)
     need = ctypes.c_int64(0)
     rc = lib().spike_solve_batch_workspace(hs, nr, cnt, trans.encode(), ctypes.byref(need))
     if rc != 0:

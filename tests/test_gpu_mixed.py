@@ -80,7 +80,9 @@ def test_mixed_borrowed_band_matches_copy():
     pr = inputs.make_problem(n, k, k, 3, seed=8, dd=1.05)
     bd = torch.from_numpy(pr["band"]).cuda()
     a = spike.factor(bd, k, k, p, mixed=True)
-    b = spike.factor(bd, k, k, p, mixed=True, borrow_band=True)
+    lent = bd.clone()
+    b = spike.factor(lent, k, k, p, mixed=True, borrow_band=True)
+    del lent  # the Factorization keeps the borrowed tensor alive until free()
     assert a.info()["device_bytes"] - b.info()["device_bytes"] >= 8 * n * (2 * k + 1)
     res_a, _ = spike.factor_bytes(n, k, k, p, mixed=True)
     res_b, _ = spike.factor_bytes(n, k, k, p, mixed=True, borrow_band=True)
@@ -92,3 +94,6 @@ def test_mixed_borrowed_band_matches_copy():
         b.solve(Xb, trans)
         assert torch.equal(Xa, Xb)
         assert metrics.backward_error(pr["band"], k, k, Xb.cpu().numpy(), F, trans) <= 1e-13
+    assert b._borrowed is not None
+    b.free()
+    assert b._borrowed is None

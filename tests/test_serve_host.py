@@ -237,3 +237,17 @@ def test_resident_fp64_requests_of_several_matrices_share_a_solve():
         for r in [busy] + ids:
             S.wait(r)
         assert S.stats()["multi_solves"] == 0
+
+
+def test_drain_releases_request_buffers_and_shapes_are_checked():
+    with serve.Server(1 << 30, streams=2, dryrun=True, dryrun_solve_us=1000) as S:
+        S.add_matrix(0, _band(300, 2), 2, 2)
+        for _ in range(20):
+            S.submit(0, np.ones((2, 300)))
+        S.drain()
+        assert [key for key in S._keep if not isinstance(key, tuple)] == []
+        assert S.stats()["completed"] == 20
+        with pytest.raises(ValueError):
+            S.submit(0, np.ones((2, 299)))
+        with pytest.raises(ValueError):
+            S.submit(0, np.ones((2, 300)), X=np.empty((1, 300)))
