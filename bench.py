@@ -485,7 +485,8 @@ def main():
     ap.add_argument("--nrhs", type=int, default=64)
     ap.add_argument("--dd", type=float, default=1.01)
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--cpu-sample", type=int, default=65536)
+    ap.add_argument("--cpu-sample", type=int, default=262144,
+                    help="rows of the workload the CPU oracle baseline solves (about 10 s on one Arm core)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer (e2e) leg, e.g. under a profiler")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision variant")
@@ -509,16 +510,17 @@ def main():
         # The reference arm is the CPU oracle, timed on this host; only rank 0 runs it.
         if rank != 0:
             return
+        ref_rows = max(4096, args.cpu_sample // 16)  # a short sample per step
         steps = []
         for _ in range(max(args.warmup, 0)):
-            cpu_oracle_sample(k, m, dd, max(4096, args.cpu_sample // 4), seed)
+            cpu_oracle_sample(k, m, dd, ref_rows, seed)
         for _ in range(args.steps):
-            steps.append(cpu_oracle_sample(k, m, dd, max(4096, args.cpu_sample // 4), seed))
+            steps.append(cpu_oracle_sample(k, m, dd, ref_rows, seed))
         v = float(np.mean([s["value"] for s in steps]))
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": 0,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean([s["seconds"] for s in steps])),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": workload, "sample_rows": max(4096, args.cpu_sample // 4)},
+                "config": {"workload": workload, "sample_rows": ref_rows},
                 "cpu_baseline": {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": steps[0]["sample"]},
                 "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
