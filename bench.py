@@ -720,7 +720,7 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
-    if not args.no_cpu and rank == 0:
+    if not args.no_cpu and rank == 0 and world == 1:  # the CPU baseline is a single-GPU figure
         line["cpu_baseline"] = cpu_oracle_sample(k, m, dd, args.cpu_sample, seed)
         line["cpu_baseline"].pop("seconds", None)
     print(json.dumps(line))

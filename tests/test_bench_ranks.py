@@ -53,3 +53,26 @@ def test_single_process_aggregation():
     import bench
     ms, value, w = bench.aggregate_over_ranks(200.0, 2e9, 5)
     assert (ms, w) == (200.0, 1) and value == pytest.approx(2e9 * 5 / 0.2 / 1e9)
+
+
+@pytest.mark.parametrize("rank", [0, 1])
+def test_reference_arm_contract(rank):
+    """`--impl reference` times the CPU oracle on rank 0 only; other ranks exit 0 silently."""
+    import json
+    import subprocess
+    env = dict(os.environ, RANK=str(rank), WORLD_SIZE="2", LOCAL_RANK=str(rank))
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+                          "--warmup", "1", "--cpu-sample", "65536"], env=env, capture_output=True, text=True,
+                         timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr
+    lines = [l for l in out.stdout.splitlines() if l.strip()]
+    if rank != 0:
+        assert lines == []
+        return
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "GB/s" and d["higher_is_better"] is True
+    assert d["steps"] == 2 and d["warmup"] == 1 and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["sample_rows"] == 4096
