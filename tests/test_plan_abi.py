@@ -129,3 +129,37 @@ def test_explicit_ratio_override(built, r13):
         assert abs(info["n1"] / info["n3"] - r13) < 1e-3
         assert abs(info["n2"] - 2 * info["n3"]) <= 1
         assert offs[-1] == 1 << 20
+
+
+@pytest.mark.parametrize("n,k,p", [(200_000, 16, 32), (1 << 20, 128, 148), (50_001, 7, 9)])
+def test_factor_bytes_accounting(built, n, k, p):
+    """spike_factor_bytes (computed without a GPU, used by the serving engine's budget) against the
+    storage the header documents: the FP64 band copy of mixed handles (8 n (kl+ku+1) bytes, none when
+    the band is borrowed), the staged copy of a host band in the transient figure, FP32 block factors
+    and reciprocals in mixed handles (ldf = 2k+2 values per row), and the pivoting layout (U fill to
+    2k above the diagonal: ldf = 3k+1 rounded up to even, plus one int pivot per row)."""
+    ldab = 2 * k + 1
+    band_bytes = 8 * n * ldab
+    slack = 256 * 16  # each carved buffer is rounded up to 256 bytes
+
+    def fb(**kw):
+        return spike.factor_bytes(n, k, k, p, **kw)
+
+    r64, t64 = fb()
+    r64h, t64h = fb(host_band=True)
+    assert r64h == r64 and r64 == fb(borrow_band=True)[0]  # FP64 handles keep no band
+    assert abs((t64h - t64) - band_bytes) <= slack           # staged host band
+    rmix, tmix = fb(mixed=True)
+    rbor, _ = fb(mixed=True, borrow_band=True)
+    assert abs((rmix - rbor) - band_bytes) <= slack           # the FP64 band copy, unless borrowed
+    assert fb(mixed=True, borrow_band=True, host_band=True)[0] == rmix  # borrowing needs a device band
+    ldf = 2 * k + 2
+    assert abs((r64 - rbor) - 4 * n * (ldf + 1)) <= slack     # factors and 1/u_jj: 8 -> 4 bytes
+    assert abs((t64 - tmix) - 4 * n * 2 * k) <= slack         # the spike right-hand sides Z in FP32
+    rpiv, _ = fb(pivot=1)
+    ldf_piv = (3 * k + 1 + 1) // 2 * 2
+    assert abs((rpiv - r64) - (8 * n * (ldf_piv - ldf) + 4 * n)) <= slack
+    assert r64 >= 8 * n * (ldf + 1)
+    with pytest.raises(spike.SpikeError) as e:
+        fb(pivot=1, mixed=True)
+    assert e.value.code == spike.SPIKE_ENOTSUP
