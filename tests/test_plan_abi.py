@@ -163,3 +163,23 @@ def test_factor_bytes_accounting(built, n, k, p):
     with pytest.raises(spike.SpikeError) as e:
         fb(pivot=1, mixed=True)
     assert e.value.code == spike.SPIKE_ENOTSUP
+
+
+def test_bandwidth_limit(built):
+    """max(kl, ku) up to SPIKE_MAX_K = 512 is planned (blocks of >= 2k rows); one more is refused
+    with SPIKE_ENOTSUP, by the planner, the factorization and the serving engine alike."""
+    import ctypes
+    info, offs, _ = spike.plan(1 << 20, 512, 200, 64)
+    assert info["k"] == 512 and np.all(np.diff(offs) >= 1024)
+    for kl, ku in ((513, 0), (0, 513)):
+        with pytest.raises(spike.SpikeError) as e:
+            spike.plan(1 << 20, kl, ku, 64)
+        assert e.value.code == spike.SPIKE_ENOTSUP
+        res, tr = ctypes.c_int64(0), ctypes.c_int64(0)
+        rc = built.spike_factor_bytes(1 << 20, kl, ku, 64, 0, None, 0, ctypes.byref(res), ctypes.byref(tr))
+        assert rc == spike.SPIKE_ENOTSUP
+    from paper_1811_03559_gb300 import serve
+    with serve.Server(1 << 30, dryrun=True) as S:
+        with pytest.raises(spike.SpikeError) as e:
+            S.add_matrix(0, np.zeros((5000, 1027)), 513, 513)
+        assert e.value.code == spike.SPIKE_ENOTSUP
