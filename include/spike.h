@@ -163,7 +163,16 @@ typedef struct {
   double refine_berr;       /* mixed: max backward error over columns after the last solve */
   int64_t graph_captures;   /* SPIKE_FLAG_GRAPHS: solves captured as CUDA graphs */
   int64_t graph_replays;    /* SPIKE_FLAG_GRAPHS: solves replayed from a captured graph */
+  int32_t numerics;         /* SPIKE_NUMERICS_* bits seen by the factorization (0: none).  As in
+                               LAPACK, a NaN in A is not an error: the call succeeds and the results
+                               carry NaN; this field says so without a pass over the output */
+  int32_t reserved0;
 } spike_info;
+
+/* Bits of spike_info.numerics. */
+#define SPIKE_NUMERICS_NAN_PIVOT 1         /* a block factorization met a NaN pivot (NaN or Inf in A) */
+#define SPIKE_NUMERICS_SINGULAR_INTERFACE 2 /* an interface block of the reduced system (Sec. 2.2) had no
+                                              nonzero pivot candidate: S is singular to working precision */
 
 /* Compute the partition plan for (n, kl, ku, p) without touching a GPU (Sec. 3.1, 3.3).
  * leaf_offsets (may be NULL) receives leaves+1 entries: block b covers global rows

@@ -265,7 +265,7 @@ struct spike_ctx {
   std::vector<std::vector<int>> schur;    // per level, per merge: 1 = Schur-complement path
   int total_merges = 0;
   int64_t boosts = 0, zero_col = 0;
-  int nan_flag = 0;
+  int nan_flag = 0;                        // SPIKE_NUMERICS_* bits of the factorization
   // solve scratch (grown on demand)
   char *scr = nullptr;
   size_t scr_bytes = 0;
@@ -1802,6 +1802,7 @@ extern "C" int spike_get_info(spike_handle h, spike_info *out) {
   out->refine_berr = h->last_berr;
   out->graph_captures = h->graph_captures;
   out->graph_replays = h->graph_replays;
+  out->numerics = h->nan_flag;
   return 0;
 }
 

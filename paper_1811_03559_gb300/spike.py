@@ -30,10 +30,10 @@ class SpikeInfo(ctypes.Structure):
                 ("K", ctypes.c_double), ("boosts", ctypes.c_int64), ("zero_pivot_col", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("mixed", ctypes.c_int32), ("refine_steps", ctypes.c_int32),
                 ("refine_berr", ctypes.c_double), ("graph_captures", ctypes.c_int64),
-                ("graph_replays", ctypes.c_int64)]
+                ("graph_replays", ctypes.c_int64), ("numerics", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved0"}
 
 
 class TuneResult(ctypes.Structure):
@@ -66,6 +66,8 @@ FLAG_MIXED = 4
 FLAG_BATCH_INVARIANT = 8
 FLAG_BORROW_BAND = 16
 FLAG_GRAPHS = 32
+NUMERICS_NAN_PIVOT = 1
+NUMERICS_SINGULAR_INTERFACE = 2
 MIXED_TOL = 1e-14
 STAGES = ["factor", "setup", "block_lu", "spikes", "reduced", "solve_n", "solve_n_d", "solve_n_reduced",
           "solve_n_retrieval", "solve_t", "solve_t_s", "solve_t_reduced", "solve_t_d"]

@@ -83,3 +83,19 @@ def test_library_pool_keeps_and_releases_memory():
     before, after = spike.release_cached()
     assert before >= 8 * 200_000 * 33  # at least the freed factor storage was still held
     assert after < before
+
+
+def test_nan_in_the_matrix_is_reported_not_an_error():
+    """A NaN on the diagonal of one block: the factorization and the solve succeed (LAPACK
+    semantics), the result carries NaN, and spike_info.numerics flags the NaN pivot; a clean
+    matrix reports no flag."""
+    n, k = 3000, 2
+    band, rng = inputs.make_band(n, k, k, seed=6, dd=1.5)
+    clean = spike.factor(_dev(band), k, k, 4)
+    assert clean.info()["numerics"] == 0
+    band[1500, k] = np.nan  # A(1500, 1500)
+    fac = spike.factor(_dev(band), k, k, 4)
+    assert fac.info()["numerics"] & spike.NUMERICS_NAN_PIVOT
+    X = _dev(rng.uniform(-1, 1, size=(1, n)))
+    fac.solve(X, "N")
+    assert torch.isnan(X).any()
