@@ -99,3 +99,24 @@ def test_nan_in_the_matrix_is_reported_not_an_error():
     X = _dev(rng.uniform(-1, 1, size=(1, n)))
     fac.solve(X, "N")
     assert torch.isnan(X).any()
+
+
+def test_singular_interface_block_is_reported():
+    """Two diagonal blocks of 2s coupled through the 2 x 2 block [[2, 2], [2, 2]] at their
+    boundary (rows 19 and 20): the tips are V_b = W_t = 2 / 2 = 1 exactly, so the interface
+    block S = I - W V of the reduced system (Sec. 2.2) is exactly 0 and A is singular (the
+    oracle's GEPP agrees).  The factorization succeeds and flags it in spike_info.numerics."""
+    n, k = 40, 1
+    _, offs, _ = spike.plan(n, k, k, 2)
+    assert list(offs) == [0, 20, 40]
+    band = np.zeros((n, 3))
+    band[:, 1] = 2.0    # diagonal
+    band[20, 0] = 2.0   # A(19, 20)
+    band[19, 2] = 2.0   # A(20, 19)
+    assert oracle.gbsv(band, k, k, np.ones(n))[1] > 0
+    fac = spike.factor(_dev(band), k, k, 2)
+    info = fac.info()
+    assert info["numerics"] & spike.NUMERICS_SINGULAR_INTERFACE and info["boosts"] == 0
+    X = _dev(np.ones((1, n)))
+    fac.solve(X, "N")
+    assert not torch.isfinite(X).all()
