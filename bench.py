@@ -664,6 +664,9 @@ def main():
         if it >= e2e_warm:
             e2e_s += dt
     e2e_step_s = e2e_s / args.e2e_steps if args.e2e_steps > 0 else float("nan")
+    e2e_ms, e2e_value = e2e_step_s * 1e3, world * bytes_step / e2e_step_s / 1e9
+    if dist is not None and args.e2e_steps > 0:  # max over ranks, as for the device-timed value
+        e2e_ms, e2e_value, _ = aggregate_over_ranks(e2e_ms, bytes_step, 1, dist, dev)
 
     mixed_workload = None
     if not args.no_mixed and extras:
@@ -710,10 +713,10 @@ def main():
                           "lu_equivalent_tflop_per_step": (2.0 * n * k * k + 3 * 4.0 * n * k * m) / 1e12},
         "stages_ms": st,
         "accuracy": {"backward_error_N": be_n, "backward_error_T": be_t},
-        "e2e": {"value": world * bytes_step / e2e_step_s / 1e9, "unit": "GB/s",
+        "e2e": {"value": e2e_value, "unit": "GB/s",
                 "h2d_bytes_per_step": int(8 * n * (2 * k + 1) + 2 * 8 * n * m),
                 "d2h_bytes_per_step": int(2 * 8 * n * m), "steps": args.e2e_steps, "warmup": e2e_warm,
-                "ms_per_step": e2e_step_s * 1e3},
+                "ms_per_step": e2e_ms},
         "variants": {"mixed_fp32_fp64_refinement": mixed, "mixed_precision_workload": mixed_workload,
                      "cuda_graphs_repeated_solves": graphs},
         "serving": serving,
