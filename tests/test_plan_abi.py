@@ -183,3 +183,15 @@ def test_bandwidth_limit(built):
         with pytest.raises(spike.SpikeError) as e:
             S.add_matrix(0, np.zeros((5000, 1027)), 513, 513)
         assert e.value.code == spike.SPIKE_ENOTSUP
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: without libspike.so every entry point of the binding raises."""
+    monkeypatch.setattr(spike, "_lib", None)
+    monkeypatch.setattr(spike, "LIB_PATH", str(tmp_path / "libspike.so"))
+    with pytest.raises(RuntimeError, match="libspike.so not found"):
+        spike.plan(1000, 2, 2, 4)
+    with pytest.raises(RuntimeError, match="libspike.so not found"):
+        spike.factor(np.zeros((1000, 5)), 2, 2, 4)
+    with pytest.raises(RuntimeError, match="libspike.so not found"):
+        spike.factor_bytes(1000, 2, 2, 4)
