@@ -22,6 +22,10 @@
  * (and mixed-precision refinement stops per column), so a request served in a busy
  * mix returns exactly what it returns alone.
  *
+ * Eviction: least recently used first by default; SPIKE_SERVE_EVICT_COST weighs each
+ * factorization by how often it is used, how long it took to build and how many bytes it
+ * holds (spike_server_config.evict_policy).
+ *
  * Memory accounting: the budget covers resident factorizations (spike_factor_bytes'
  * resident figure, then the handle's actual device_bytes), the factorization scratch
  * while a factorization runs, and every worker's solve workspace and batch buffer.
@@ -60,8 +64,18 @@ typedef struct {
   int32_t dryrun_factor_us;  /* SPIKE_SERVE_DRYRUN: simulated factorization time */
   int32_t dryrun_solve_us;   /* SPIKE_SERVE_DRYRUN: simulated time per solve */
   int32_t batch_systems;     /* most matrices whose FP64 requests share one solve (0 or 1: one matrix) */
-  int32_t reserved[6];
+  int32_t evict_policy;      /* SPIKE_SERVE_EVICT_*: which idle factorization leaves first */
+  int32_t reserved[5];
 } spike_server_config;
+
+/* Eviction policies.  LRU: the least recently used idle factorization.  COST: greedy-dual
+ * size-frequency -- every resident factorization carries the priority
+ *   L + (solves served since it was factored) x (its measured factorization time) / (its bytes),
+ * the idle one with the lowest priority leaves first and L rises to its priority, so
+ * factorizations that are used often, slow to rebuild or small stay resident, and L ages
+ * out the ones that stopped being used. */
+#define SPIKE_SERVE_EVICT_LRU 0
+#define SPIKE_SERVE_EVICT_COST 1
 
 typedef struct {
   int64_t submitted, completed, failed;

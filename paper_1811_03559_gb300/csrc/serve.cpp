@@ -1,6 +1,7 @@
 // Serving engine of libspike.so (spike_serve.h): a catalogue of banded matrices, their
 // factorizations kept resident in device memory under a byte budget (least recently
-// used evicted first), and workers that each own one host thread and one CUDA stream.
+// used, or lowest greedy-dual size-frequency priority, evicted first), and workers that
+// each own one host thread and one CUDA stream.
 //
 // A factorization is reused for every later request on its matrix, N and T alike
 // (Sec. 4 reuses the factors of Sec. 2 for the transpose solve).  Waiting requests
@@ -53,6 +54,9 @@ struct Fac {
   uint64_t last_use = 0;  // LRU clock
   bool resident = false;  // factored and held
   bool busy = false;      // a worker is factoring or solving with it
+  double cost_s = 0.0;    // wall time of its last factorization (SPIKE_SERVE_EVICT_COST)
+  int64_t uses = 0;       // solves served since it was factored
+  double prio = 0.0;      // greedy-dual priority: L + uses * cost_s / bytes
 };
 
 struct Mat {
@@ -78,6 +82,8 @@ struct spike_server_s {
   int dev = 0;
   int sms = 152;
   int batch_systems = 1;  // most matrices per solve (1: one matrix per solve)
+  int policy = SPIKE_SERVE_EVICT_LRU;
+  double gd_L = 0.0;      // greedy-dual inflation value: priority of the last evicted factorization
   bool dry = false;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -108,18 +114,25 @@ void account(spike_server_s *S, int64_t delta) {
   S->peak = std::max(S->peak, S->used);
 }
 
-// Make room for `bytes` more device bytes: evict least recently used factorizations
-// that no worker is using.  Waits while another worker that is not itself waiting
-// holds memory that it will release; returns false when the bytes cannot fit (so two
-// workers never wait on each other).
+// Which of two idle factorizations leaves first under the server's policy.
+bool evict_before(const spike_server_s *S, const Fac &a, const Fac &b) {
+  if (S->policy == SPIKE_SERVE_EVICT_COST && a.prio != b.prio) return a.prio < b.prio;
+  return a.last_use < b.last_use;
+}
+
+// Make room for `bytes` more device bytes: evict factorizations that no worker is using
+// (least recently used first, or lowest greedy-dual priority first).  Waits while another
+// worker that is not itself waiting holds memory that it will release; returns false when
+// the bytes cannot fit (so two workers never wait on each other).
 bool admit(spike_server_s *S, Lock &lk, int64_t bytes, std::vector<spike_handle> &victims) {
   if (bytes > S->cfg.budget_bytes) return false;
   while (S->used + bytes > S->cfg.budget_bytes) {
     Fac *v = nullptr;
     for (auto &kv : S->mats)
       for (auto &f : kv.second.fac)
-        if (f.resident && !f.busy && (!v || f.last_use < v->last_use)) v = &f;
+        if (f.resident && !f.busy && (!v || evict_before(S, f, *v))) v = &f;
     if (v) {
+      if (S->policy == SPIKE_SERVE_EVICT_COST) S->gd_L = std::max(S->gd_L, v->prio);
       victims.push_back(v->h);
       account(S, -v->bytes);
       v->h = nullptr;
@@ -292,6 +305,7 @@ void worker(spike_server_s *S, int w) {
         lk.unlock();
         spike_handle h = nullptr;
         int64_t actual = res + slack;
+        const double t_fac = now_s();
         if (S->dry) {
           sleep_us(S->cfg.dryrun_factor_us);
         } else {
@@ -305,6 +319,7 @@ void worker(spike_server_s *S, int w) {
             h = nullptr;
           }
         }
+        const double fac_s = now_s() - t_fac;
         lk.lock();
         ++S->nfact;
         if (rc >= 0) {  // rc > 0: singular (pivoting); kept, its solves report rc
@@ -312,6 +327,8 @@ void worker(spike_server_s *S, int w) {
           F.bytes = actual;
           F.h = h;
           F.resident = true;
+          F.cost_s = std::max(fac_s, 1e-6);
+          F.uses = 0;
         } else {
           account(S, -F.bytes);
           F.bytes = 0;
@@ -426,6 +443,8 @@ void worker(spike_server_s *S, int w) {
       S->rhs += g.cols;
       g.F->last_use = ++S->tick;
       g.F->busy = false;
+      ++g.F->uses;
+      g.F->prio = S->gd_L + (double)g.F->uses * g.F->cost_s / (double)std::max<int64_t>(g.F->bytes, 1);
     }
     ++S->batches;
     if (multi) ++S->multi;
@@ -444,12 +463,13 @@ extern "C" int spike_server_create(const spike_server_config *cfg, spike_server 
   if (!out) return -2;
   *out = nullptr;
   if (!cfg || cfg->budget_bytes <= 0 || cfg->streams < 1 || cfg->streams > 64 || cfg->max_batch_rhs < 1 ||
-      cfg->p < 0)
+      cfg->p < 0 || (cfg->evict_policy != SPIKE_SERVE_EVICT_LRU && cfg->evict_policy != SPIKE_SERVE_EVICT_COST))
     return -1;
   spike_server_s *S = new spike_server_s();
   S->cfg = *cfg;
   S->dry = (cfg->flags & SPIKE_SERVE_DRYRUN) != 0;
   if (cfg->batch_systems > 0) S->batch_systems = cfg->batch_systems;
+  S->policy = cfg->evict_policy;
   if (!S->dry) {
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {

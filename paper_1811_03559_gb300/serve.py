@@ -13,6 +13,7 @@ import numpy as np
 from . import spike
 
 DRYRUN = 1
+EVICT_LRU, EVICT_COST = 0, 1
 
 
 class ServerConfig(ctypes.Structure):
@@ -20,7 +21,7 @@ class ServerConfig(ctypes.Structure):
                 ("p", ctypes.c_int32), ("nrhs_hint", ctypes.c_int32), ("K", ctypes.c_double),
                 ("flags", ctypes.c_int32), ("dryrun_factor_us", ctypes.c_int32),
                 ("dryrun_solve_us", ctypes.c_int32), ("batch_systems", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("evict_policy", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class ServerStats(ctypes.Structure):
@@ -71,15 +72,16 @@ def _lib():
 
 class Server:
     """A spike_server: resident factorizations under `budget_bytes`, `streams` workers,
-    up to `max_batch_rhs` right-hand sides merged per solve."""
+    up to `max_batch_rhs` right-hand sides merged per solve; `evict` is "lru" (least
+    recently used first) or "cost" (greedy-dual size-frequency, spike_serve.h)."""
 
     def __init__(self, budget_bytes, streams=4, max_batch_rhs=64, p=0, nrhs_hint=0, K=0.0, dryrun=False,
-                 dryrun_factor_us=0, dryrun_solve_us=0, batch_systems=0):
+                 dryrun_factor_us=0, dryrun_solve_us=0, batch_systems=0, evict="lru"):
         self._keep = {}
         cfg = ServerConfig(budget_bytes=int(budget_bytes), streams=streams, max_batch_rhs=max_batch_rhs, p=p,
                            nrhs_hint=nrhs_hint, K=K, flags=DRYRUN if dryrun else 0,
                            dryrun_factor_us=dryrun_factor_us, dryrun_solve_us=dryrun_solve_us,
-                           batch_systems=batch_systems)
+                           batch_systems=batch_systems, evict_policy={"lru": EVICT_LRU, "cost": EVICT_COST}[evict])
         h = ctypes.c_void_p()
         rc = _lib().spike_server_create(ctypes.byref(cfg), ctypes.byref(h))
         if rc != 0:

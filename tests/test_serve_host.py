@@ -251,3 +251,55 @@ def test_drain_releases_request_buffers_and_shapes_are_checked():
             S.submit(0, np.ones((2, 299)))
         with pytest.raises(ValueError):
             S.submit(0, np.ones((2, 300)), X=np.empty((1, 300)))
+
+
+@pytest.mark.parametrize("evict,refactored", [("lru", True), ("cost", False)])
+def test_cost_aware_eviction_keeps_the_frequently_used(evict, refactored):
+    """Room for two of three equal factorizations: A serves three requests, B one, then C
+    arrives.  LRU evicts A (used least recently); the greedy-dual size-frequency policy evicts B
+    (one use against three), so a later request on A needs no new factorization."""
+    n, k, p = 4000, 4, 8
+    reserve, keep = _reserve(n, k, p)
+    budget = 2 * keep + (reserve - keep) + 24 * n + keep // 2
+    with serve.Server(budget, streams=1, max_batch_rhs=4, p=p, dryrun=True, dryrun_factor_us=20_000,
+                      evict=evict) as S:
+        for mid in "ABC":
+            S.add_matrix(ord(mid), _band(n, k), k, k)
+        F = np.ones((1, n))
+        for mid in "AAABC":
+            S.wait(S.submit(ord(mid), F)[0])
+        before = S.stats()
+        assert (before["factorizations"], before["evictions"]) == (3, 1)
+        S.wait(S.submit(ord("A"), F)[0])
+        assert (S.stats()["factorizations"] > before["factorizations"]) == refactored
+        assert S.stats()["peak_bytes"] <= budget
+
+
+@pytest.mark.parametrize("evict,refactored", [("lru", True), ("cost", False)])
+def test_cost_aware_eviction_prefers_large_factorizations(evict, refactored):
+    """Equal uses and build times: the greedy-dual priority is use x time / bytes, so the larger
+    factorization leaves first and the small, older one stays (LRU evicts the older one)."""
+    k, p = 4, 8
+    rs, ks_ = _reserve(4000, k, p)
+    rb, kb = _reserve(8000, k, p)
+    budget = ks_ + kb + 24 * 8000 + (rs - ks_) + ks_ // 2
+    with serve.Server(budget, streams=1, max_batch_rhs=4, p=p, dryrun=True, dryrun_factor_us=20_000,
+                      evict=evict) as S:
+        S.add_matrix(1, _band(4000, k), k, k)
+        S.add_matrix(2, _band(8000, k), k, k)
+        S.add_matrix(3, _band(4000, k, seed=1), k, k)
+        for mid, n in ((1, 4000), (2, 8000), (3, 4000)):
+            S.wait(S.submit(mid, np.ones((1, n)))[0])
+        before = S.stats()
+        assert (before["factorizations"], before["evictions"]) == (3, 1)
+        S.wait(S.submit(1, np.ones((1, 4000)))[0])
+        assert (S.stats()["factorizations"] > before["factorizations"]) == refactored
+        assert S.stats()["peak_bytes"] <= budget
+
+
+def test_unknown_eviction_policy_is_refused():
+    with pytest.raises(KeyError):
+        serve.Server(1 << 28, dryrun=True, evict="random")
+    cfg = serve.ServerConfig(budget_bytes=1 << 28, streams=1, max_batch_rhs=4, flags=serve.DRYRUN, evict_policy=7)
+    h = serve.ctypes.c_void_p()
+    assert serve._lib().spike_server_create(serve.ctypes.byref(cfg), serve.ctypes.byref(h)) == -1
