@@ -338,7 +338,7 @@ def tuning_leg(band, k, nrhs):
             "seconds": time.perf_counter() - t0}
 
 
-def serving_leg(dev, requests, streams, max_batch, passes=2, seed=None, batch_systems=1):
+def serving_leg(dev, requests, streams, max_batch, passes=2, seed=None, batch_systems=1, evict="lru"):
     """Many-matrix serving workload (inputs.SERVING) through the native serving engine.
 
     The catalogue bands live in device memory (the caller's; the budget covers the
@@ -370,7 +370,8 @@ def serving_leg(dev, requests, streams, max_batch, passes=2, seed=None, batch_sy
     cap = 1 << 29  # 4 GB of pinned result space, reused as a ring
     arena = torch.empty(cap, dtype=torch.float64).pin_memory().numpy()
     budget = int(cfg["budget_gb"] * 1e9)
-    S = serve.Server(budget, streams=streams, max_batch_rhs=max_batch, nrhs_hint=16, batch_systems=batch_systems)
+    S = serve.Server(budget, streams=streams, max_batch_rhs=max_batch, nrhs_hint=16, batch_systems=batch_systems,
+                     evict=evict)
     for i in used:
         S.add_matrix(i, bands[i], int(ks[i]), int(ks[i]))
     out = {"workload": "%d requests, Poisson %g/s, %d matrices (n log-uniform [%d, %d], k uniform {4..128 step 4}, "
@@ -378,7 +379,8 @@ def serving_leg(dev, requests, streams, max_batch, passes=2, seed=None, batch_sy
                        % (requests, cfg["rate"], cfg["matrices"], cfg["n_lo"], cfg["n_hi"], cfg["dd"], cfg["zipf"],
                           cfg["nrhs_max"], round(100 * cfg["trans_t"]), round(100 * cfg["mixed"]), cfg["budget_gb"]),
            "matrices_used": len(used), "catalogue_gb": sum(8.0 * ns[i] * (2 * ks[i] + 1) for i in used) / 1e9,
-           "streams": streams, "max_batch_rhs": max_batch, "batch_systems": batch_systems, "catalogue_gen_s": t_gen,
+           "streams": streams, "max_batch_rhs": max_batch, "batch_systems": batch_systems, "evict": evict,
+           "catalogue_gen_s": t_gen,
            "data": "synthetic (torch generator on the device for the bands, seeded per matrix)", "passes": []}
     launches0 = spike.kernel_launches()
 
@@ -496,6 +498,8 @@ def main():
     ap.add_argument("--serve-streams", type=int, default=8)
     ap.add_argument("--serve-batch", type=int, default=64)
     ap.add_argument("--serve-passes", type=int, default=2)
+    ap.add_argument("--serve-evict", choices=("lru", "cost"), default="lru",
+                    help="eviction policy of the serving engine (SPIKE_SERVE_EVICT_LRU / _COST)")
     ap.add_argument("--serve-batch-systems", type=int, default=1,
                     help="matrices whose FP64 requests may share one solve (spike_solve_batch)")
     args = ap.parse_args()
@@ -681,7 +685,7 @@ def main():
     serving = None
     if not args.no_serve and extras:
         serving = serving_leg(dev, args.serve_requests, args.serve_streams, args.serve_batch, args.serve_passes,
-                              batch_systems=args.serve_batch_systems)
+                              batch_systems=args.serve_batch_systems, evict=args.serve_evict)
         serving["cpu_baseline"] = cpu_serve
 
     if rank != 0:
