@@ -195,3 +195,45 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         spike.factor(np.zeros((1000, 5)), 2, 2, 4)
     with pytest.raises(RuntimeError, match="libspike.so not found"):
         spike.factor_bytes(1000, 2, 2, 4)
+
+
+def test_plan_structure_on_random_sizes(built):
+    """Structure of 400 random plans (Sec. 3.1): the blocks tile [0, n) with at least 2k rows each
+    (one block may be shorter: then it is the only one); P = 2^m partitions of which partitions
+    2..r+1 (1-based) are SPIKE 2x2 pairs (top half flag 2, bottom half flag 4|1: a UL block) and the
+    last block is UL; t_eff = P + r <= t blocks in all; one merge level for the pairs plus m; and the
+    plan is a fixed point (planning again with t_eff gives the same blocks)."""
+    rng = np.random.default_rng(12)
+    for _ in range(400):
+        n = int(np.exp(rng.uniform(0, np.log(2e6))))
+        k = int(rng.integers(0, 65))
+        k = min(k, max(n - 1, 0))
+        t = int(rng.integers(1, 400))
+        info, offs, flags = spike.plan(n, k, k, t)
+        kk = max(1, k)
+        sizes = np.diff(offs)
+        nb = len(sizes)
+        assert offs[0] == 0 and offs[-1] == n and np.all(sizes >= 1)
+        assert nb == 1 or np.all(sizes >= 2 * kk), (n, k, t)
+        P, r, m = info["P"], info["r"], info["m"]
+        assert P == 1 << m and nb == P + r == info["p_effective"] == info["leaves"] <= t
+        assert r <= max(P - 2, 0)
+        expect = [0] * nb
+        for j in range(r):
+            expect[1 + 2 * j], expect[2 + 2 * j] = 2, 5
+        if nb > 1:
+            expect[-1] = 1
+        assert list(flags) == expect, (n, k, t)
+        assert info["levels"] == m + (1 if r > 0 else 0)
+        again, offs2, _ = spike.plan(n, k, k, info["p_effective"])
+        assert again["p_effective"] == info["p_effective"] and np.array_equal(offs2, offs)
+
+
+@pytest.mark.parametrize("m", [2, 3, 5, 7])
+def test_one_below_a_power_of_two_idles_a_worker(built, m):
+    """t = 2^(m+1) - 1 would need r = 2^m - 1 pairs, but only the P - 2 inner partitions can be
+    split (the first and last use LU / UL alone); the paper runs it as 2^(m+1) - 2 workers with
+    one idle (Sec. 3.1)."""
+    t = (2 << m) - 1
+    info, _, _ = spike.plan(1 << 22, 4, 4, t)
+    assert info["p_effective"] == t - 1 and info["P"] == 1 << m and info["r"] == (1 << m) - 2
