@@ -356,3 +356,103 @@ def test_metrics_detect_planted_error():
     x2[0, 1000] += 1e-8
     assert metrics.backward_error(p["band"], 4, 4, x2, p["F"]) > 1e-10
     assert metrics.forward_error(x2, p["xstar"]) > 1e-9
+
+
+# ------------------------------------------------------------------ metric pins
+# The acceptance bars (backward error <= 1e-13, forward error <= 1e-9) are read through
+# oracle.metrics, so its norms are pinned to their definitions (Sec. 3.4 "relative
+# residual"; infinity norms, per column, max over columns): the band norms against
+# numpy's matrix norms of a dense copy built here, the error formulas against a 3 x 3
+# example worked by hand.  A swapped row/column sum, or a normalisation by the largest
+# entry of the whole X instead of each column's, fails these.
+
+def dense_from_band(band, kl, ku):
+    """Dense A from the LAPACK band layout, built independently of the oracle's helper."""
+    n = band.shape[0]
+    A = np.zeros((n, n))
+    for d in range(kl + ku + 1):
+        off = d - ku  # A(j + off, j) = band[j, d]
+        for j in range(n):
+            i = j + off
+            if 0 <= i < n:
+                A[i, j] = band[j, d]
+    return A
+
+
+@pytest.mark.parametrize("kl,ku", [(0, 0), (0, 3), (3, 0), (1, 4), (5, 2), (7, 7)])
+@pytest.mark.parametrize("ints", [True, False])
+def test_band_norms_equal_dense_norms(kl, ku, ints):
+    rng = np.random.default_rng(1000 + 31 * kl + ku)
+    n = 37
+    band = rng.integers(-9, 10, size=(n, kl + ku + 1)).astype(np.float64) if ints else rng.normal(size=(n, kl + ku + 1))
+    # entries outside the matrix (band corners) must be ignored: fill them with large values
+    for j in range(n):
+        for d in range(kl + ku + 1):
+            if not 0 <= j + d - ku < n:
+                band[j, d] = 1e6
+    A = dense_from_band(band, kl, ku)
+    rt = 0.0 if ints else 1e-15  # integer sums are exact in any order
+    assert metrics.band_norm_inf(band, kl, ku, "N") == pytest.approx(np.linalg.norm(A, np.inf), rel=rt, abs=0)
+    assert metrics.band_norm_inf(band, kl, ku, "T") == pytest.approx(np.linalg.norm(A.T, np.inf), rel=rt, abs=0)
+    assert condest.band_norm_1(band, kl, ku) == pytest.approx(np.linalg.norm(A, 1), rel=rt, abs=0)
+    if kl + ku > 0:
+        # row and column sums differ on these matrices, so a swap would be seen
+        assert np.linalg.norm(A, np.inf) != np.linalg.norm(A, 1)
+
+
+def hand_band():
+    """A = [[4, 1, 0], [2, 5, 3], [0, 1, 6]] (kl = ku = 1): row sums 5, 10, 7; column sums 6, 7, 9."""
+    A = np.array([[4.0, 1.0, 0.0], [2.0, 5.0, 3.0], [0.0, 1.0, 6.0]])
+    band = np.zeros((3, 3))
+    for j in range(3):
+        for i in range(max(0, j - 1), min(3, j + 2)):
+            band[j, 1 + i - j] = A[i, j]
+    return band
+
+
+def test_backward_error_hand_example_N():
+    band = hand_band()
+    # column 0: x = (1, 2, -1), A x = (6, 9, -4), f = (6, 9, -3.5): ||r|| = 0.5, ||x|| = 2 -> 0.5 / (10 * 2) = 0.025
+    # column 1: x = (0.5, 0, 0), A x = (2, 1, 0), f = (2, 1.25, 0): ||r|| = 0.25, ||x|| = 0.5 -> 0.25 / (10 * 0.5) = 0.05
+    X = np.array([[1.0, 2.0, -1.0], [0.5, 0.0, 0.0]])
+    F = np.array([[6.0, 9.0, -3.5], [2.0, 1.25, 0.0]])
+    assert metrics.band_norm_inf(band, 1, 1, "N") == 10.0
+    assert metrics.backward_error(band, 1, 1, X[:1], F[:1], "N") == pytest.approx(0.025, rel=1e-15)
+    assert metrics.backward_error(band, 1, 1, X[1:], F[1:], "N") == pytest.approx(0.05, rel=1e-15)
+    # max over columns, each column normalised by its own ||x||
+    assert metrics.backward_error(band, 1, 1, X, F, "N") == pytest.approx(0.05, rel=1e-15)
+
+
+def test_backward_error_hand_example_T():
+    band = hand_band()
+    # A^T = [[4, 2, 0], [1, 5, 1], [0, 3, 6]], ||A^T||_inf = 9 (column sums of A)
+    # column 0: A^T x = (8, 10, 0), f = (8, 10, 0.9): 0.9 / (9 * 2) = 0.05
+    # column 1: A^T x = (2, 0.5, 0), f = (2, 0.5, 0.3): 0.3 / (9 * 0.5) = 1/15
+    X = np.array([[1.0, 2.0, -1.0], [0.5, 0.0, 0.0]])
+    F = np.array([[8.0, 10.0, 0.9], [2.0, 0.5, 0.3]])
+    assert metrics.band_norm_inf(band, 1, 1, "T") == 9.0
+    assert metrics.backward_error(band, 1, 1, X[:1], F[:1], "T") == pytest.approx(0.05, rel=1e-15)
+    assert metrics.backward_error(band, 1, 1, X, F, "T") == pytest.approx(1.0 / 15.0, rel=1e-15)
+
+
+def test_forward_error_hand_example():
+    # per column ||x - x_ref||_inf / ||x_ref||_inf, max over columns:
+    # column 0: |(1, 2.5, -1) - (1, 2, -1)| = 0.5, ||x_ref|| = 2 -> 0.25
+    # column 1: |(0.5, 0.1, 0) - (0.5, 0, 0)| = 0.1, ||x_ref|| = 0.5 -> 0.2
+    X = np.array([[1.0, 2.5, -1.0], [0.5, 0.1, 0.0]])
+    Xref = np.array([[1.0, 2.0, -1.0], [0.5, 0.0, 0.0]])
+    assert metrics.forward_error(X[1:], Xref[1:]) == pytest.approx(0.2, rel=1e-15)
+    assert metrics.forward_error(X, Xref) == pytest.approx(0.25, rel=1e-15)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_inverse_norm_estimate_is_a_lower_bound(seed):
+    # Hager's estimate maximises ||A^{-1} x||_1 over unit vectors, so it never exceeds
+    # ||A^{-1}||_1; on small diagonally dominant matrices it reaches it.
+    n, kl, ku = 40, 2, 3
+    band, _ = inputs.make_band(n, kl, ku, seed=50 + seed, dd=1.3)
+    A = dense_from_band(band, kl, ku)
+    true = np.linalg.norm(np.linalg.inv(A), 1)
+    est = condest.inv_norm_1_estimate(oracle.BandLU(band, kl, ku))
+    assert est <= true * (1 + 1e-12)
+    assert est >= true * 0.5
