@@ -337,7 +337,11 @@ int64_t spike_kernel_launches(void);
  *   - nrhs above SPIKE_NOALLOC_MAX_NRHS returns SPIKE_ELIMIT (nothing runs).
  *   - The first call on a device looks up that array's device address (once
  *     per device, with the device current); make that first call before any
- *     stream capture.
+ *     stream capture.  The address is cached for the life of the process: after
+ *     cudaDeviceReset on a device, do not call this entry point on that device
+ *     again in the same process.
+ *   - `stream` must belong to the current device (the scratch used is the
+ *     current device's copy of the array).
  *   - Every call shares the one array: calls whose GPU work overlaps (other
  *     streams, other host threads) race on it and must be serialised by the
  *     caller.  Each call clears the part it uses before using it.

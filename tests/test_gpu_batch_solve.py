@@ -5,6 +5,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 from oracle import metrics
 from paper_1811_03559_gb300 import inputs, spike
 
@@ -56,8 +57,17 @@ def test_batch_equals_separate_solves(systems, trans):
     torch.cuda.synchronize()
     for i, (a, b) in enumerate(zip(alone, Fs)):
         assert torch.equal(a, b), (i, (a - b).abs().max().item())
-    band, k, _, F = systems[3]
-    assert metrics.backward_error(band, k, k, Fs[3].cpu().numpy(), F, trans) <= 1e-13
+    # every system against the oracle: backward error <= 1e-13 and forward error <= 1e-9
+    # against banded GEPP (the bands are diagonally dominant), the reused handle included
+    rhs = [F for _, _, _, F in systems] + [extra]
+    owners = list(range(len(systems))) + [1]
+    for i, (own, F) in enumerate(zip(owners, rhs)):
+        band, k, _, _ = systems[own]
+        X = Fs[i].cpu().numpy()
+        assert metrics.backward_error(band, k, k, X, F, trans) <= 1e-13, i
+        xo, info = oracle.gbsv(band, k, k, F, trans)
+        assert info == 0
+        assert metrics.forward_error(X, xo) <= 1e-9, i
 
 
 def test_batch_argument_checks(systems):

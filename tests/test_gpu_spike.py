@@ -1,6 +1,6 @@
 """GPU parity tests: libspike.so (through its C ABI) against the CPU oracle.
 
-Tolerances (from the task's accuracy bar, restated in the design doc): every FP64
+Tolerances: every FP64
 result must have backward error ||op(A)x - f|| / (||op(A)|| ||x||) <= 1e-13,
 and on diagonally dominant inputs a relative forward error <= 1e-9 against the
 oracle.  SPIKE and banded GEPP agree only up to rounding (different operation

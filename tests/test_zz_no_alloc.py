@@ -51,6 +51,29 @@ def test_noalloc_matches_allocating_entry_point_twice():
         assert np.all(got > 1e-12)
 
 
+@pytest.mark.parametrize("n,kl,ku,nrhs,trans", [(20_000, 7, 4, 8, "N"), (20_000, 7, 4, 40, "T"),
+                                                (300, 2, 3, spike.NOALLOC_MAX_NRHS, "N")])
+def test_noalloc_tiled_path_and_limit(n, kl, ku, nrhs, trans):
+    """Eight or more right-hand sides take the tiled residual kernel; nrhs at exactly the limit
+    fills the whole fixed array (its last words hold the finished per-column errors)."""
+    pr = inputs.make_problem(n, kl, ku, nrhs, seed=33 + nrhs, dd=1.1)
+    band = torch.from_numpy(pr["band"]).cuda()
+    X = torch.from_numpy(pr["xstar"].copy()).cuda()
+    X[:, n // 3] += 1e-6  # a residual well above rounding in every column
+    F = torch.from_numpy(inputs.band_matvec(pr["band"], kl, ku, pr["xstar"], trans)).cuda()
+    for _ in range(2):  # the second call must not see the first one's maxima
+        ref = spike.backward_error(band, kl, ku, X, F, trans)
+        got = _call_noalloc(band, kl, ku, X, F, trans)
+        np.testing.assert_allclose(got, ref, rtol=1e-12, atol=0)
+        assert np.all(got > 1e-12)
+    # a smaller residual afterwards: the words reused from the larger call are cleared
+    X2 = torch.from_numpy(pr["xstar"].copy()).cuda()
+    got2 = _call_noalloc(band, kl, ku, X2, F, trans)
+    ref2 = spike.backward_error(band, kl, ku, X2, F, trans)
+    np.testing.assert_allclose(got2, ref2, rtol=1e-12, atol=1e-300)
+    assert np.all(got2 < 1e-13)
+
+
 def test_noalloc_rejects_nrhs_above_limit():
     L = spike.lib()
     band = torch.zeros((10, 3), dtype=torch.float64, device="cuda")
