@@ -88,6 +88,13 @@ extern "C" {
  * the scratch is the handle's own or the spike_solve_ws workspace).  Not used with
  * SPIKE_FLAG_TIMING, mixed precision, host F or the legacy default stream (NULL). */
 #define SPIKE_FLAG_GRAPHS 32
+/* Mixed precision: form the refinement residuals with FP64 FMAs instead of the tensor-core
+ * residual (see spike_residual).  By default a mixed-precision handle splits op(A) once, at
+ * factorization, into integer digit planes (about 16 n (kl + ku + 35) bytes for N and T
+ * together, counted by spike_factor_bytes) and forms each residual of 8 or more columns on
+ * the tensor cores, to FP64 accuracy; with fewer columns, or bandwidths above about 330,
+ * the FP64 kernel is used either way. */
+#define SPIKE_FLAG_FP64_RESIDUAL 64
 #define SPIKE_MIXED_TOL 1e-14
 #define SPIKE_MIXED_MAX_STEPS 10
 
@@ -268,6 +275,19 @@ int spike_get_tips(spike_handle h, int level, double *host_dst);
 int spike_backward_error(const double *band, int64_t ldab, int64_t n, int kl, int ku, const double *X,
                          const double *F, int nrhs, char trans, void *stream, double *berr);
 
+/* R = F - op(A) X for a mixed-precision handle (SPIKE_FLAG_MIXED without
+ * SPIKE_FLAG_FP64_RESIDUAL), with the kernel its iterative refinement uses (Sec. 5: the
+ * residual of an approximate factorization is formed in the working precision, FP64):
+ * every entry of op(A) (from the handle's FP64 band) and of X is written as a 56-bit
+ * fixed-point number relative to a power of two of its row / column, split into 8 base-128
+ * digits, and the digit products are accumulated exactly on the bf16 tensor cores; only the
+ * two fixed-point roundings (2^-56 of the row and column scale), the final sum in FP64 and
+ * f - Ax round.  X, F, R: device pointers, n x nrhs, leading dimension n (R may not alias
+ * X).  berr (host, nrhs doubles, may be NULL) receives ||r_c||_inf / (||op(A)||_inf
+ * ||x_c||_inf) per column.  Runs on the handle's stream and synchronises it; allocates its
+ * scratch from the library's pool.  SPIKE_ENOTSUP for other handles or host pointers. */
+int spike_residual(spike_handle h, const double *X, const double *F, double *R, int nrhs, char trans, double *berr);
+
 /* Stage times of the last factorization and the last N and T solves of a handle
  * created with SPIKE_FLAG_TIMING (indices SPIKE_T_*; -1 for stages not run).
  * Synchronises the handle's stream.  ms must hold `count` doubles. */
@@ -350,6 +370,62 @@ int64_t spike_kernel_launches(void);
  * Arguments, layout and synchronisation are those of spike_backward_error. */
 int spike_backward_error_noalloc(const double *band, int64_t ldab, int64_t n, int kl, int ku, const double *X,
                                  const double *F, int nrhs, char trans, void *stream, double *berr);
+
+/* ---------------------------------------------------------------------------------------
+ * Partition-range sharding of one system over nranks GPUs (the SPIKE-MPI direction named in
+ * Sec. 3, with the recursive reduced system of Sec. 2.2 carried across ranks).  Rank g owns
+ * P / nranks consecutive partitions of the plan of (n, kl, ku, p): blocks
+ * [leaf_first[g], leaf_first[g+1]) and rows [row_first[g], row_first[g+1]).  The pair level
+ * and the first log2(P / nranks) power-of-two merge levels stay inside a rank; each of the
+ * top log2(nranks) levels is one exchange, in which every rank contributes a fixed-size
+ * buffer (the spike tips of its boundary blocks: 4 k x k in the factorization; its boundary
+ * right-hand-side tips: 2 k x nrhs in the solves; one k x nrhs partial product per level in
+ * the transposed solve) and receives all ranks' buffers (an all-gather, made by the caller
+ * over NCCL, MPI or any transport).  Non-pivoting FP64 handles only.
+ *
+ * Protocol, per operation (spike_shard_factor, then any number of spike_shard_solve):
+ *   while (spike_shard_pending(h, &count) == 0 && count > 0) {
+ *     spike_shard_export(h, send);          // send: count doubles, device
+ *     all-gather send over the ranks into recv (nranks x count doubles, rank-major, device)
+ *     spike_shard_import(h, recv);
+ *   }
+ * Every rank runs the same number of exchanges with the same count.  A new operation may
+ * start only when the previous one has no pending exchange (SPIKE_ENOTSUP otherwise).
+ * ------------------------------------------------------------------------------------ */
+
+/* The ranges of each rank (no GPU).  nranks must be a power of two between 1 and the plan's
+ * partition count P (-5 otherwise).  row_first, leaf_first: nranks + 1 entries;
+ * *local_levels: merge levels that stay inside one rank (the rest are exchanges). */
+int spike_shard_plan(int64_t n, int kl, int ku, int p, int nranks, const spike_options *opt, int64_t *row_first,
+                     int32_t *leaf_first, int32_t *local_levels);
+
+/* Factor rank `rank`'s blocks (Sec. 2.3) and the merge levels inside them (Sec. 2.2).
+ * band: device pointer to global band columns col0, col0 + 1, ... (LAPACK layout, ldab)
+ * covering at least columns [max(0, r0 - k), min(n, r1 + k)) where [r0, r1) are the rank's
+ * rows (spike_shard_plan) and k = max(kl, ku): the rank's rows and their couplings.  It is
+ * read during the call only.  Other arguments as spike_factor_ex; the options' flags may not
+ * include SPIKE_FLAG_MIXED.  -3: col0 is past the rank's first needed column; -9: a rank
+ * count the plan cannot take.  The factorization is complete when no exchange is pending.
+ * The diagonal boosting threshold (Sec. 2.3) is taken from the rank's own block entries. */
+int spike_shard_factor(const double *band, int64_t ldab, int64_t col0, int64_t n, int kl, int ku, int p, int rank,
+                       int nranks, const spike_options *opt, spike_handle *out);
+
+/* Start a solve of A X = F (trans 'N') or A^T X = F ('T', Sec. 4) with the rank's rows of F:
+ * F is a device pointer, (rows of the rank) x nrhs, leading dimension ldf; it is overwritten
+ * with the rank's rows of X when the last exchange has been imported. */
+int spike_shard_solve(spike_handle h, double *F, int64_t ldf, int nrhs, char trans);
+
+/* Doubles each rank contributes to the pending exchange (0: the operation is complete). */
+int spike_shard_pending(spike_handle h, int64_t *count);
+
+/* Write this rank's contribution to the pending exchange to `send` (device, count doubles);
+ * synchronises the handle's stream. */
+int spike_shard_export(spike_handle h, double *send);
+
+/* Run the pending level with the gathered contributions (recv: device, nranks x count
+ * doubles, rank g's at recv + g * count; complete before the call).  Asynchronous on the
+ * handle's stream, except the factorization's levels, which read a flag per merge back. */
+int spike_shard_import(spike_handle h, const double *recv);
 
 /* Release a handle and all its device memory.  NULL is ignored. */
 void spike_free(spike_handle h);

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libspike.so")
-SOURCES = ["api.cu", "leaf.cu", "dense.cu", "plan.cpp", "serve.cpp", "tune.cpp"]
+SOURCES = ["api.cu", "leaf.cu", "dense.cu", "resid_split.cu", "plan.cpp", "serve.cpp", "tune.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -255,6 +255,11 @@ struct spike_ctx {
   size_t es = sizeof(double);
   double *band64 = nullptr;                // mixed: FP64 copy of the band for the refinement residuals
   int64_t ldab64 = 0;
+  // mixed: op(A) split into int8 digit fragments for the tensor-core residual (resid_split.cu),
+  // [0] = N (rows of A), [1] = T (rows of A^T); null when the FP64 residual is used
+  void *sfrag[2] = {nullptr, nullptr};
+  int *srexp[2] = {nullptr, nullptr};
+  unsigned long long *snorm = nullptr;     // ||A||_inf, ||A^T||_inf (bit patterns)
   double refine_tol = SPIKE_MIXED_TOL;     // mixed: per-column stopping backward error
   int last_iters = 0;                      // mixed: refinement steps of the last solve
   double last_berr = 0.0;                  //        and its final backward error
@@ -271,6 +276,21 @@ struct spike_ctx {
   size_t scr_bytes = 0;
   char *dargs = nullptr;
   size_t dargs_bytes = 0;
+  // partition-range sharding (spike_shard_factor): this rank owns leaves [l0, l1), rows
+  // [row0, row0 + nrow); its factors, work arrays and right-hand sides hold only those rows
+  // (their base pointers are offset by -row0 so that kernels index them by global row).
+  // Spike tips and reduced unknowns keep the global leaf numbering.  The first `lvl` merge
+  // levels lie inside the rank; the others are run one per exchange (sh_op, sh_level).
+  int shard = 0, rank = 0, nranks = 1, l0 = 0, l1 = 0, lvl = 0;
+  int64_t row0 = 0, nrow = 0;
+  std::vector<int> leaf_first;             // nranks + 1 leaf boundaries
+  int sh_op = 0;                           // pending exchange: SH_* below
+  int sh_level = 0;
+  char *sh_fscr = nullptr;                 // factor scratch kept until the coarse levels are done
+  size_t sh_tmp_off = 0, sh_tmp_bytes = 0;
+  double *sh_F = nullptr;                  // the solve's own rows of F
+  int64_t sh_ld = 0;
+  int sh_m = 0;
   // stage timing (SPIKE_FLAG_TIMING): boundary events of the last factor / N solve / T solve
   bool timing = false;
   cudaEvent_t fev[5] = {}, nev[4] = {}, tev[4] = {};
@@ -356,6 +376,26 @@ extern "C" int spike_plan(int64_t n, int kl, int ku, int p, const spike_options 
       leaf_flags[i] = (pl.leaves[i].rev ? 1 : 0) | (pl.leaves[i].half == 1 ? 2 : 0) | (pl.leaves[i].half == 2 ? 4 : 0);
   }
   if (leaf_offsets) leaf_offsets[pl.nleaves] = n;
+  return 0;
+}
+
+extern "C" int spike_shard_plan(int64_t n, int kl, int ku, int p, int nranks, const spike_options *opt,
+                                int64_t *row_first, int32_t *leaf_first, int32_t *local_levels) {
+  if (!row_first) return -7;
+  if (!leaf_first) return -8;
+  if (!local_levels) return -9;
+  Plan pl;
+  const int rc = make_plan(n, kl, ku, p, opt ? opt->K : 0.0, opt ? opt->nrhs_hint : 0, opt ? opt->flags : 0,
+                           opt ? opt->R13 : 0.0, pl);
+  if (rc != 0) return rc;
+  std::vector<int> lf;
+  int ll = 0;
+  if (shard_ranges(pl, nranks, lf, ll) != 0) return -5;
+  for (int g = 0; g <= nranks; ++g) {
+    leaf_first[g] = lf[g];
+    row_first[g] = (lf[g] < pl.nleaves) ? pl.leaves[lf[g]].start : n;
+  }
+  *local_levels = ll;
   return 0;
 }
 
@@ -622,14 +662,22 @@ struct FactorLayout {
   int64_t zacc = 0, maxlen = 0, nmerge = 0;
   size_t o_fb = 0, o_dinv = 0, o_b64 = 0, o_ipiv = 0, o_cpl = 0, o_spk = 0, o_mlu = 0, o_mpiv = 0, o_id = 0,
          o_st = 0, mem = 0;
+  bool split = false;
+  size_t o_sfrag[2] = {0, 0}, o_srexp[2] = {0, 0}, o_snorm = 0;
   size_t s_band = 0, s_z = 0, s_zoff = 0, s_leaf = 0, s_tmp = 0, tmp_bytes = 0, scr = 0;
   std::vector<int64_t> zoff;
 };
 
 // borrow: a mixed-precision handle reads the caller's device band for its residuals
 // (SPIKE_FLAG_BORROW_BAND) instead of keeping a copy.
+// Mixed-precision handles form their refinement residuals on the tensor cores (resid_split.cu)
+// unless SPIKE_FLAG_FP64_RESIDUAL asks for FP64 FMAs or the band is too wide for its tiles.
+static bool use_split_residual(const Plan &pl, int f32, int flags) {
+  return f32 && !(flags & SPIKE_FLAG_FP64_RESIDUAL) && split_supported(pl.kl, pl.ku);
+}
+
 static void factor_layout(const Plan &pl, int pivot, int f32, int64_t ldab, bool band_dev, bool borrow,
-                          FactorLayout &L) {
+                          FactorLayout &L, int flags) {
   const int64_t n = pl.n;
   const int k = pl.k, nlv = pl.nleaves;
   const size_t es = f32 ? sizeof(float) : sizeof(double);
@@ -668,6 +716,14 @@ static void factor_layout(const Plan &pl, int pivot, int f32, int64_t ldab, bool
   L.o_mpiv = carve(sizeof(int) * (size_t)std::max<int64_t>(L.nmerge, 1) * 2 * k);
   L.o_id = carve(sizeof(double) * (size_t)kk);
   L.o_st = carve(sizeof(unsigned long long) * 8);
+  L.split = use_split_residual(pl, f32, flags);
+  if (L.split) {
+    for (int t = 0; t < 2; ++t) {
+      L.o_sfrag[t] = carve(split_band_bytes(n, pl.kl, pl.ku));
+      L.o_srexp[t] = carve(sizeof(int) * (size_t)n);
+    }
+    L.o_snorm = carve(sizeof(unsigned long long) * 2);
+  }
   L.mem = off;
   off = 0;
   L.s_band = band_dev ? 0 : carve(sizeof(double) * (size_t)n * ldab);
@@ -692,14 +748,28 @@ extern "C" int spike_factor_bytes(int64_t n, int kl, int ku, int p, int pivot, c
   if (f32 && pivot) return SPIKE_ENOTSUP;
   FactorLayout L;
   factor_layout(pl, pivot, f32, (int64_t)kl + ku + 1, host_band == 0,
-                (opt && (opt->flags & SPIKE_FLAG_BORROW_BAND)) != 0, L);
+                (opt && (opt->flags & SPIKE_FLAG_BORROW_BAND)) != 0, L, opt ? opt->flags : 0);
   *resident = (int64_t)L.mem;
   *transient = (int64_t)L.scr;
   return 0;
 }
 
+// A rank's part of a sharded factorization: `band` holds global band columns from col0 on.
+struct ShardSpec {
+  int rank, nranks;
+  int64_t col0;
+};
+
+static int factor_impl(const double *band, int64_t ldab, int64_t n, int kl, int ku, int p, int pivot,
+                       const spike_options *opt, spike_handle *out, const ShardSpec *sh);
+
 extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int kl, int ku, int p, int pivot,
                                const spike_options *opt, spike_handle *out) {
+  return factor_impl(band, ldab, n, kl, ku, p, pivot, opt, out, nullptr);
+}
+
+static int factor_impl(const double *band, int64_t ldab, int64_t n, int kl, int ku, int p, int pivot,
+                       const spike_options *opt, spike_handle *out, const ShardSpec *sh) {
   if (!out) return -9;
   *out = nullptr;
   if (!band) return -1;
@@ -752,9 +822,41 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
   };
 
   const bool band_dev = is_device_ptr(band);
+  // sharded: this rank's leaves and rows; the other leaves are given no rows, so every kernel
+  // over the blocks skips them, and the band is addressed by global column
+  Plan plx = pl;
+  if (sh) {
+    if (pivot || c->f32 || !band_dev) {
+      delete c;
+      return SPIKE_ENOTSUP;
+    }
+    if (shard_ranges(pl, sh->nranks, c->leaf_first, c->lvl) != 0 || sh->rank < 0 || sh->rank >= sh->nranks) {
+      delete c;
+      return -9;
+    }
+    c->shard = 1;
+    c->rank = sh->rank;
+    c->nranks = sh->nranks;
+    c->l0 = c->leaf_first[sh->rank];
+    c->l1 = c->leaf_first[sh->rank + 1];
+    c->row0 = pl.leaves[c->l0].start;
+    c->nrow = ((c->l1 < pl.nleaves) ? pl.leaves[c->l1].start : n) - c->row0;
+    if (sh->col0 < 0 || sh->col0 > std::max<int64_t>(0, c->row0 - pl.k)) {
+      delete c;
+      return -3;
+    }
+    for (int i = 0; i < pl.nleaves; ++i)
+      if (i < c->l0 || i >= c->l1) {
+        plx.leaves[i].len = 0;
+        plx.leaves[i].has_prev = plx.leaves[i].has_next = 0;
+        plx.leaves[i].start = c->row0;
+      }
+    plx.n = c->nrow;
+    band = (const double *)((const char *)band - (ptrdiff_t)(sh->col0 * ldab * (int64_t)sizeof(double)));
+  }
   FactorLayout FL;
   const bool borrow = c->f32 && band_dev && opt && (opt->flags & SPIKE_FLAG_BORROW_BAND);
-  factor_layout(pl, pivot, c->f32, ldab, band_dev, borrow, FL);
+  factor_layout(plx, pivot, c->f32, ldab, band_dev, borrow, FL, opt ? opt->flags : 0);
   c->dofs = FL.dofs;
   c->ldf = FL.ldf;
   const std::vector<int64_t> &zoff = FL.zoff;
@@ -762,7 +864,7 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
   // leaves
   c->hl.resize(nlv);
   for (int i = 0; i < nlv; ++i) {
-    const Leaf &L = pl.leaves[i];
+    const Leaf &L = plx.leaves[i];
     LeafDev d;
     d.start = L.start;
     d.len = L.len;
@@ -795,8 +897,9 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
       return fail(SPIKE_ENOMEM);
     }
   }
-  c->fbc = c->mem + o_fb;
-  c->dinvc = c->mem + o_dinv;
+  // (sharded: offset by -row0 so that the kernels index the rank's rows by global row)
+  c->fbc = c->mem + o_fb - (ptrdiff_t)(c->row0 * c->ldf * (int64_t)c->es);
+  c->dinvc = c->mem + o_dinv - (ptrdiff_t)(c->row0 * (int64_t)c->es);
   if (c->f32) {
     c->band64 = borrow ? const_cast<double *>(band) : (double *)(c->mem + o_b64);
     c->ldab64 = ldab;
@@ -808,6 +911,13 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
   c->mpiv = (int *)(c->mem + o_mpiv);
   c->ident = (double *)(c->mem + o_id);
   c->status = (unsigned long long *)(c->mem + o_st);
+  if (FL.split) {
+    for (int t = 0; t < 2; ++t) {
+      c->sfrag[t] = c->mem + FL.o_sfrag[t];
+      c->srexp[t] = (int *)(c->mem + FL.o_srexp[t]);
+    }
+    c->snorm = (unsigned long long *)(c->mem + FL.o_snorm);
+  }
 
   // factor-time scratch: staged band (host input), Z, per-merge temporaries
   const size_t s_band = FL.s_band, s_z = FL.s_z, s_zoff = FL.s_zoff, s_leaf = FL.s_leaf, s_tmp = FL.s_tmp;
@@ -860,6 +970,13 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
                     cudaSuccess) {
     g_cuda_err = "band copy";
     return fail2(SPIKE_ECUDA);
+  }
+  // mixed: the digit fragments of A and A^T for the tensor-core refinement residual
+  for (int t = 0; t < 2 && c->sfrag[0]; ++t) {
+    if ((rc = launch_split_band(c->band64, ldab, n, kl, ku, t, c->srexp[t], c->snorm + t, c->sfrag[t], s)) != 0) {
+      g_cuda_err = std::string("split kernels: ") + cudaGetErrorString((cudaError_t)rc);
+      return fail2(SPIKE_ECUDA);
+    }
   }
   if ((rc = launch_repack(dband, ldab, kl, ku, n, k, c->ldf, c->dofs, dleaf, nlv, c->fbc, &c->status[3], s, maxlen,
                           c->f32)) != 0 ||
@@ -926,8 +1043,9 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
     return fail2(SPIKE_ECUDA);
   }
   if (c->timing) cudaEventRecord(c->fev[3], s);
-  // 4. recursive reduced system factorization
-  for (int lv = 0; lv < c->NL; ++lv) {
+  // 4. recursive reduced system factorization (sharded: the levels inside the rank; the others
+  // follow the exchanges of spike_shard_import)
+  for (int lv = 0; lv < (c->shard ? c->lvl : c->NL); ++lv) {
     if ((rc = factor_reduced_level(c, lv, tmp, tmp_bytes)) != 0) return fail2(rc);
   }
   if (c->timing) {
@@ -941,7 +1059,15 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
     g_cuda_err = std::string("factor: ") + cudaGetErrorString(cudaGetLastError());
     return fail2(SPIKE_ECUDA);
   }
-  cudaFreeAsync(fscr, s);
+  if (c->shard && c->lvl < c->NL) {
+    c->sh_fscr = fscr;  // the per-merge temporaries of the coarse levels
+    c->sh_tmp_off = s_tmp;
+    c->sh_tmp_bytes = tmp_bytes;
+    c->sh_op = 1;
+    c->sh_level = c->lvl;
+  } else {
+    cudaFreeAsync(fscr, s);
+  }
   c->boosts = (int64_t)st[0];
   c->zero_col = (st[1] == ULLONG_MAX) ? 0 : (int64_t)st[1];
   c->nan_flag = (int)st[2];
@@ -1001,6 +1127,10 @@ static int factor_reduced_level(spike_ctx *c, int lv, char *tmp, size_t tmp_byte
   int maxn = 0;
   for (int m = 0; m < nm; ++m) {
     const Merge &mg = ms[m];
+    // a rank forms the merges inside its leaves and, above them, the one merge containing them
+    const bool inside = !c->shard || (mg.a >= c->l0 && mg.c <= c->l1);
+    const bool mine = c->shard && mg.a <= c->l0 && c->l1 <= mg.c;
+    if (!inside && !mine) continue;
     const int64_t gm = c->merge_off[lv] + m;
     double *lu = c->mlu + gm * 4 * kk;
     int *piv = c->mpiv + gm * 2 * k;
@@ -1047,7 +1177,48 @@ static int factor_reduced_level(spike_ctx *c, int lv, char *tmp, size_t tmp_byte
     }
     maxn = std::max(maxn, L.n);
     lus.push_back(L);
-    if (!last) {
+    if (!last && !inside) {
+      // merge over several ranks: update this rank's leaves only.  L-side leaves [la, lb),
+      // R-side leaves [ra, rb); the interface tips (b-1, bottom) and (b, top) come from the
+      // 2k solve when the rank holds them (the formulas below give the same values).
+      const int b = mg.b;
+      const int la = std::max(mg.a, c->l0), lb = std::min(b, c->l1);
+      const int ra = std::max(b, c->l0), rb = std::min(mg.c, c->l1);
+      auto zero = [&](int sp, int i0, int rows) {
+        gC.add(gd(nullptr, 0, 0, nullptr, 0, 0, nullptr, 0, 0, TIP(c, lv + 1, sp, i0, 0), k, 1, rows, k, 0, 0.0, 0.0));
+      };
+      if (lb > la) {
+        const int ML = 2 * (lb - la) * k;
+        if (mg.hasV)
+          gC.add(gd(TIP(c, lv, 0, la, 0), k, 1, be, k, 1, nullptr, 0, 0, TIP(c, lv + 1, 0, la, 0), k, 1, ML, k, k, -1.0,
+                    0.0));
+        else
+          zero(0, la, ML);
+        if (mg.hasW)
+          gC.add(gd(TIP(c, lv, 0, la, 0), k, 1, de, k, 1, TIP(c, lv, 1, la, 0), k, 1, TIP(c, lv + 1, 1, la, 0), k, 1, ML,
+                    k, k, -1.0, 1.0));
+        else
+          zero(1, la, ML);
+      }
+      if (rb > ra) {
+        const int t0 = (ra == b) ? 1 : 0;  // holding b: its top tip comes from the solve
+        const int MR = (2 * (rb - ra) - t0) * k;
+        if (mg.hasV) {
+          gC.add(gd(TIP(c, lv, 1, ra, t0), k, 1, al, k, 1, TIP(c, lv, 0, ra, t0), k, 1, TIP(c, lv + 1, 0, ra, t0), k, 1,
+                    MR, k, k, -1.0, 1.0));
+          if (t0) gC.add(gd(nullptr, 0, 0, nullptr, 0, 0, be, k, 1, TIP(c, lv + 1, 0, b, 0), k, 1, k, k, 0, 0.0, 1.0));
+        } else {
+          zero(0, ra, 2 * (rb - ra) * k);
+        }
+        if (mg.hasW) {
+          gC.add(gd(TIP(c, lv, 1, ra, t0), k, 1, ga, k, 1, nullptr, 0, 0, TIP(c, lv + 1, 1, ra, t0), k, 1, MR, k, k,
+                    -1.0, 0.0));
+          if (t0) gC.add(gd(nullptr, 0, 0, nullptr, 0, 0, de, k, 1, TIP(c, lv + 1, 1, b, 0), k, 1, k, k, 0, 0.0, 1.0));
+        } else {
+          zero(1, ra, 2 * (rb - ra) * k);
+        }
+      }
+    } else if (!last) {
       const int a = mg.a, b = mg.b, cc = mg.c;
       const int ML = 2 * (b - a) * k, MR = (2 * (cc - b) - 1) * k, MA = 2 * (cc - a) * k;
       if (mg.hasV) {
@@ -1102,14 +1273,26 @@ struct SolveBufs {
 // Record the SPIKE solve of op(A) X = W (Sec. 2.1-2.3 for N, Sec. 4 for T) on the
 // row-major work array W, in place.  f32: W and H are FP32 and the leaf sweeps run
 // in FP32 (mixed-precision handles); the reduced system is always FP64.
-static void build_solve_body(spike_ctx *c, Pipeline &pp, const SolveBufs &B, int m, int tr, bool marks);
-static void build_solve(spike_ctx *c, Pipeline &pp, const SolveBufs &B, int m, int tr, bool marks) {
+// Which parts of a solve to record: the first stage (head: D stage for N, S^T stage for T),
+// the merge levels [lv_lo, lv_hi) of the reduced system, the last stage (tail: retrieval for
+// N, D^T stage for T).  A sharded handle records only its own blocks and the merges inside
+// them; the merges over several ranks are run by the exchange steps.
+struct SolveRange {
+  bool head = true, tail = true;
+  int lv_lo = 0, lv_hi = INT_MAX;
+};
+
+static void build_solve_body(spike_ctx *c, Pipeline &pp, const SolveBufs &B, int m, int tr, bool marks,
+                             const SolveRange &rg);
+static void build_solve(spike_ctx *c, Pipeline &pp, const SolveBufs &B, int m, int tr, bool marks,
+                        const SolveRange &rg = SolveRange()) {
   c->in_solve = 1;
-  build_solve_body(c, pp, B, m, tr, marks);
+  build_solve_body(c, pp, B, m, tr, marks, rg);
   c->in_solve = 0;
 }
 
-static void build_solve_body(spike_ctx *c, Pipeline &pp, const SolveBufs &B, int m, int tr, bool marks) {
+static void build_solve_body(spike_ctx *c, Pipeline &pp, const SolveBufs &B, int m, int tr, bool marks,
+                             const SolveRange &rg) {
   const int64_t n = c->pl.n;
   const int k = c->k, nlv = c->nleaves;
   const int64_t kk = (int64_t)k * k, km = (int64_t)k * m;
@@ -1143,15 +1326,25 @@ static void build_solve_body(spike_ctx *c, Pipeline &pp, const SolveBufs &B, int
     cudaEvent_t e = evs[i];
     pp.op([=](char *) { return (int)cudaEventRecord(e, s); });
   };
+  auto own = [&](int i) { return !c->shard || (i >= c->l0 && i < c->l1); };
+  auto inside = [&](const Merge &mg) { return !c->shard || (mg.a >= c->l0 && mg.c <= c->l1); };
+  // the H rows this handle holds (all rows, or a rank's own rows)
+  void *Hmem = c->shard ? (void *)eptr(H, c->row0 * (int64_t)m) : H;
+  const size_t Hbytes = es * (size_t)(c->shard ? c->nrow : n) * m;
+  const int lv_lo = std::max(0, rg.lv_lo), lv_hi = std::min(c->NL, rg.lv_hi);
   pp.key(0, 0);
-  memset_op(H, es * (size_t)n * m);
-  memset_op(Y, sizeof(double) * (size_t)nlv * 2 * km);
+  if (rg.head) {
+    memset_op(Hmem, Hbytes);
+    memset_op(Y, sizeof(double) * (size_t)nlv * 2 * km);
+  }
 
   if (tr == 0) {
     pp.key(1, 0);
+    if (rg.head) {
     // ---------------- D stage (Eq. Dstage) with the sweep savings of Sec. 2.3
     std::vector<SweepDesc> sa(nlv, empty_sweep()), sb(nlv, empty_sweep());
     for (int i = 0; i < nlv; ++i) {
+      if (!own(i)) continue;
       const LeafDev &L = c->hl[i];
       const int nl = (int)L.len;
       const View fv = rview(L, W), hv = rview(L, H);
@@ -1163,6 +1356,7 @@ static void build_solve_body(spike_ctx *c, Pipeline &pp, const SolveBufs &B, int
     // gather Y tips (global rows) from H
     GemmBatch g0;
     for (int i = 0; i < nlv; ++i) {
+      if (!own(i)) continue;
       const LeafDev &L = c->hl[i];
       if (i > 0)
         g0.add(typed(gd(nullptr, 0, 0, nullptr, 0, 0, rows(H, L.start), m, 1, YB(i, 0), m, 1, k, m, 0, 0.0, 1.0), tC0));
@@ -1173,14 +1367,16 @@ static void build_solve_body(spike_ctx *c, Pipeline &pp, const SolveBufs &B, int
     }
     pp.gemm(g0);
     mark(1);
+    }
     // ---------------- reduced system, levels ascending: D^[1]^-1 ... (Eqs. D1Inverse, S2Inverse)
-    for (int lv = 0; lv < c->NL; ++lv) {
+    for (int lv = lv_lo; lv < lv_hi; ++lv) {
       pp.key(2, lv);
       const auto &ms = c->pl.levels[lv];
       GemmBatch g1, g2, g3;
       TrsBatch ts;
       for (int mi = 0; mi < (int)ms.size(); ++mi) {
         const Merge &mg = ms[mi];
+        if (!inside(mg)) continue;
         const int64_t gm = c->merge_off[lv] + mi;
         const double *lu = c->mlu + gm * 4 * kk;
         const int *pv = c->mpiv + gm * 2 * k;
@@ -1209,12 +1405,14 @@ static void build_solve_body(spike_ctx *c, Pipeline &pp, const SolveBufs &B, int
       pp.gemm(g3);
     }
     mark(2);
+    if (!rg.tail) return;
     // ---------------- retrieval (Eqs. one/two/three): X_i = U^{-1}(L^{-1}F - L^{-1}[R_top x_top; 0; R_bot x_bot])
     pp.key(3, 0);
-    memset_op(H, es * (size_t)n * m);
+    memset_op(Hmem, Hbytes);
     GemmBatch gc;
     std::vector<SweepDesc> sc(nlv, empty_sweep()), sd(nlv, empty_sweep());
     for (int i = 0; i < nlv; ++i) {
+      if (!own(i)) continue;
       const LeafDev &L = c->hl[i];
       const int nl = (int)L.len;
       const View fv = rview(L, W), hv = rview(L, H);
@@ -1238,8 +1436,10 @@ static void build_solve_body(spike_ctx *c, Pipeline &pp, const SolveBufs &B, int
   } else {
     // ---------------- transpose: S^T Y = F then D^T X = Y (Sec. 4.1, 4.2)
     pp.key(1, 0);
+    if (rg.head) {
     GemmBatch g0, gz;
     for (int i = 0; i < nlv; ++i) {
+      if (!own(i)) continue;
       const LeafDev &L = c->hl[i];
       if (i > 0) {
         double *v = rows(W, L.start);
@@ -1256,6 +1456,7 @@ static void build_solve_body(spike_ctx *c, Pipeline &pp, const SolveBufs &B, int
     pp.gemm(gz);
     std::vector<SweepDesc> sa(nlv, empty_sweep()), sb(nlv, empty_sweep()), e0(nlv, empty_sweep());
     for (int i = 0; i < nlv; ++i) {
+      if (!own(i)) continue;
       const LeafDev &L = c->hl[i];
       const int nl = (int)L.len;
       const View fv = rview(L, W), hv = rview(L, H);
@@ -1275,6 +1476,7 @@ static void build_solve_body(spike_ctx *c, Pipeline &pp, const SolveBufs &B, int
     // G tips: y_{j+1,top} -= Bhat_j^T z_{j,bot}, y_{j-1,bot} -= Chat_j^T z_{j,top} (Eqs. G_in_transpose_1/2)
     GemmBatch gg;
     for (int j = 0; j < nlv; ++j) {
+      if (!own(j)) continue;
       const LeafDev &L = c->hl[j];
       const int nl = (int)L.len;
       const View hv = rview(L, H);
@@ -1292,8 +1494,9 @@ static void build_solve_body(spike_ctx *c, Pipeline &pp, const SolveBufs &B, int
     }
     pp.gemm(gg);
     mark(1);
+    }
     // ---------------- transposed reduced system, levels descending (Sec. 4.3)
-    for (int lv = c->NL - 1; lv >= 0; --lv) {
+    for (int lv = lv_hi - 1; lv >= lv_lo; --lv) {
       pp.key(2, -lv);  // levels descending: higher levels first in every system
       const auto &ms = c->pl.levels[lv];
       GemmBatch gpart, g2, g3, g4;
@@ -1302,6 +1505,7 @@ static void build_solve_body(spike_ctx *c, Pipeline &pp, const SolveBufs &B, int
       int64_t maxe = 0;
       for (int mi = 0; mi < (int)ms.size(); ++mi) {
         const Merge &mg = ms[mi];
+        if (!inside(mg)) continue;
         const int64_t gm = c->merge_off[lv] + mi;
         const double *lu = c->mlu + gm * 4 * kk;
         const int *pv = c->mpiv + gm * 2 * k;
@@ -1339,12 +1543,14 @@ static void build_solve_body(spike_ctx *c, Pipeline &pp, const SolveBufs &B, int
       pp.gemm(g4);
     }
     mark(2);
+    if (!rg.tail) return;
     // ---------------- D^T stage (Eq. sweeps_in_D): X_i = L^{-T}(w + U^{-T}[y_top; 0; y_bot])
     pp.key(3, 0);
-    memset_op(H, es * (size_t)n * m);
+    memset_op(Hmem, Hbytes);
     GemmBatch gp;
     std::vector<SweepDesc> sc(nlv, empty_sweep()), sd(nlv, empty_sweep());
     for (int i = 0; i < nlv; ++i) {
+      if (!own(i)) continue;
       const LeafDev &L = c->hl[i];
       const int nl = (int)L.len;
       const View fv = rview(L, W), hv = rview(L, H);
@@ -1444,6 +1650,7 @@ static int solve_impl(spike_handle h, double *F, int64_t ldf, int nrhs, char tra
   if (!valid(h)) return SPIKE_EHANDLE;
   if (!F && !need) return -2;
   spike_ctx *c = h;
+  if (c->shard) return SPIKE_ENOTSUP;  // a rank's part: spike_shard_solve
   const int64_t n = c->pl.n;
   if (ldf < n) return -3;
   if (nrhs < 0) return -4;
@@ -1482,6 +1689,10 @@ static int solve_impl(spike_handle h, double *F, int64_t ldf, int nrhs, char tra
   const size_t o_r = mixed ? carve(nm8) : 0;
   const size_t o_nrm = mixed ? carve(sizeof(unsigned long long) * (1 + 2 * (size_t)m)) : 0;
   const size_t o_act = mixed ? carve(sizeof(int) * (size_t)m) : 0;
+  // tensor-core residual: the digit planes of X (for 8 or more columns; fewer take the FP64 kernel)
+  const bool split = mixed && c->sfrag[0] != nullptr && m >= 8;
+  const size_t xdig_bytes = split ? split_x_bytes(n, c->pl.kl, c->pl.ku, m) : 0;
+  const size_t o_xd = split ? carve(xdig_bytes) : 0;
   if (need) {
     *need = (int64_t)off;
     return 0;
@@ -1583,6 +1794,8 @@ static int solve_impl(spike_handle h, double *F, int64_t ldf, int nrhs, char tra
     SP_CUDA(cudaMemcpy2DAsync(F0, sizeof(double) * n, Fd, sizeof(double) * ld, sizeof(double) * n, m,
                               cudaMemcpyDeviceToDevice, s));
     SP_CUDA(cudaMemsetAsync(X, 0, nm8, s));
+    void *xdig = split ? (void *)(base + o_xd) : nullptr;
+    if (split) SP_CUDA(cudaMemsetAsync(xdig, 0x40, xdig_bytes, s));  // digit 0 around every column
     const double *rhs = F0;  // first step: x = 0, r = F
     int steps = 0;
     double worst = INFINITY;
@@ -1601,9 +1814,17 @@ static int solve_impl(spike_handle h, double *F, int64_t ldf, int nrhs, char tra
         const float *d = (const float *)B.W;
         pp.ops.push_back([=](char *) { return launch_add_work32(X, n, d, n, m, dact, s); });
       }
-      // r = F - op(A) x (FP64, original band) and the per-column backward errors
-      pp.ops.push_back([=](char *) { return (int)cudaMemsetAsync(nrm, 0, sizeof(unsigned long long) * (1 + 2 * (size_t)m), s); });
-      {
+      // r = F - op(A) x (FP64-accurate, original band) and the per-column backward errors
+      if (split) {
+        const void *fr = c->sfrag[tr];
+        const int *rx = c->srexp[tr];
+        const unsigned long long *an = c->snorm + tr;
+        const int kl = c->pl.kl, ku = c->pl.ku;
+        pp.ops.push_back([=](char *) {
+          return launch_resid_split(fr, rx, an, n, kl, ku, tr, X, F0, R, m, xdig, nrm, s);
+        });
+      } else {
+        pp.ops.push_back([=](char *) { return (int)cudaMemsetAsync(nrm, 0, sizeof(unsigned long long) * (1 + 2 * (size_t)m), s); });
         const double *band = c->band64;
         const int64_t ldb = c->ldab64;
         const int kl = c->pl.kl, ku = c->pl.ku;
@@ -1654,6 +1875,404 @@ static int solve_impl(spike_handle h, double *F, int64_t ldf, int nrhs, char tra
   return 0;
 }
 
+// ============================================================ sharded solves
+// Partition-range sharding over ranks (NEXT to Sec. 3's SPIKE-MPI remark; the recursion of
+// Sec. 2.2 across ranks).  Each rank holds its own blocks and rows; the merge levels inside
+// a rank run locally, and every level above them is one exchange: the caller all-gathers a
+// fixed-size buffer from every rank (spike_shard_pending / _export), hands the gathered
+// buffers back (spike_shard_import) and the handle runs that level for the merge that
+// contains its blocks.  What a level needs from the other ranks is only the spike or
+// right-hand-side tips at the rank boundaries (k x k per spike in the factorization, k x m
+// in the solves), or, for the transposed solve, one k x m partial product per rank.
+enum ShardOp { SH_NONE = 0, SH_FACTOR = 1, SH_N_LEVEL = 2, SH_N_FINAL = 3, SH_T_GTIPS = 4, SH_T_LEVEL = 5 };
+
+// the merge of level lv that contains this rank's blocks (index in the level)
+static int shard_merge(spike_ctx *c, int lv) {
+  const auto &ms = c->pl.levels[lv];
+  for (int mi = 0; mi < (int)ms.size(); ++mi)
+    if (ms[mi].a <= c->l0 && c->l1 <= ms[mi].c) return mi;
+  return -1;
+}
+
+// rank whose first block is `leaf` (merge boundaries above the local levels are rank boundaries)
+static int shard_rank_at(spike_ctx *c, int leaf) {
+  for (int g = 0; g <= c->nranks; ++g)
+    if (c->leaf_first[g] == leaf) return g;
+  return -1;
+}
+
+struct ShardBufs {
+  double *Wm, *Hm;  // the rank's rows of the work arrays (row-major, nrow x m)
+  SolveBufs B;      // the same with W, H offset by -row0 (global row indexing)
+  double *XP;       // the transposed solve's partial product (k x m)
+};
+
+static ShardBufs shard_bufs(spike_ctx *c, int m, size_t *bytes) {
+  size_t off = 0;
+  auto carve = [&](size_t b) {
+    size_t o = off;
+    off = (off + b + 255) & ~size_t(255);
+    return o;
+  };
+  const int64_t km = (int64_t)c->k * m;
+  const size_t rows = sizeof(double) * (size_t)c->nrow * m;
+  size_t maxm = 1;
+  for (auto &lvv : c->pl.levels) maxm = std::max(maxm, lvv.size());
+  const size_t ow = carve(rows), oh = carve(rows), oy = carve(sizeof(double) * (size_t)c->nleaves * 2 * km),
+               ot = carve(sizeof(double) * maxm * 2 * km), op = carve(sizeof(double) * (size_t)c->nleaves * km),
+               ox = carve(sizeof(double) * km);
+  ShardBufs S;
+  char *base = c->scr;
+  if (bytes) {
+    *bytes = off;
+    base = nullptr;
+  }
+  S.Wm = (double *)(base + ow);
+  S.Hm = (double *)(base + oh);
+  S.B.W = (char *)S.Wm - (ptrdiff_t)(c->row0 * m * (int64_t)sizeof(double));
+  S.B.H = (char *)S.Hm - (ptrdiff_t)(c->row0 * m * (int64_t)sizeof(double));
+  S.B.Y = (double *)(base + oy);
+  S.B.TM = (double *)(base + ot);
+  S.B.PP = (double *)(base + op);
+  S.XP = (double *)(base + ox);
+  return S;
+}
+
+// The transposed solve's partial product of level lv: sum over this rank's blocks (in block
+// order) of V_i^T y_i (the rank is on the left of its merge) or W_i^T y_i (on the right).
+static void shard_t_partial(spike_ctx *c, Pipeline &pp, const ShardBufs &S, int m, int lv) {
+  const int k = c->k;
+  const int64_t km = (int64_t)k * m;
+  const Merge &mg = c->pl.levels[lv][shard_merge(c, lv)];
+  const int sp = (c->l0 < mg.b) ? 0 : 1;
+  GemmBatch gpart;
+  for (int i = c->l0; i < c->l1; ++i)
+    gpart.add(gd(TIP(c, lv, sp, i, 0), 1, k, S.B.Y + (int64_t)i * 2 * km, m, 1, nullptr, 0, 0,
+                 S.B.PP + (int64_t)i * km, m, 1, k, m, 2 * k, 1.0, 0.0));
+  pp.gemm(gpart);
+  std::vector<SumDesc> sums{SumDesc{S.B.PP + (int64_t)c->l0 * km, S.XP, km, km, c->l1 - c->l0, 0}};
+  pp.sums(sums, km);
+}
+
+// One merge level above the rank (N solve, Eqs. D1Inverse / S2Inverse): the 2k interface solve
+// of the rank's merge from the gathered boundary tips, then the updates of this rank's tips.
+static void shard_n_level(spike_ctx *c, Pipeline &pp, const ShardBufs &S, int m, int lv) {
+  const int k = c->k;
+  const int64_t kk = (int64_t)k * k, km = (int64_t)k * m;
+  const int mi = shard_merge(c, lv);
+  const Merge &mg = c->pl.levels[lv][mi];
+  double *Y = S.B.Y;
+  auto YB = [&](int i, int t) { return Y + ((int64_t)i * 2 + t) * km; };
+  const int64_t gm = c->merge_off[lv] + mi;
+  const double *lu = c->mlu + gm * 4 * kk;
+  const int *pv = c->mpiv + gm * 2 * k;
+  double *ta = S.B.TM, *tb = ta + km;
+  const int b = mg.b;
+  const double *Vlb = TIP(c, lv, 0, b - 1, 1), *Wrt = TIP(c, lv, 1, b, 0);
+  GemmBatch g1, g2, g3;
+  TrsBatch ts;
+  if (c->schur[lv][mi]) {
+    g1.add(gd(Wrt, k, 1, YB(b - 1, 1), m, 1, YB(b, 0), m, 1, tb, m, 1, k, m, k, -1.0, 1.0));
+    ts.add(lu, pv, k, k, tb, m, m, 0, 1.0);
+    g2.add(gd(Vlb, k, 1, tb, m, 1, YB(b - 1, 1), m, 1, ta, m, 1, k, m, k, -1.0, 1.0));
+  } else {
+    g1.add(gd(nullptr, 0, 0, nullptr, 0, 0, YB(b - 1, 1), m, 1, ta, m, 1, k, m, 0, 0.0, 1.0));
+    g1.add(gd(nullptr, 0, 0, nullptr, 0, 0, YB(b, 0), m, 1, tb, m, 1, k, m, 0, 0.0, 1.0));
+    ts.add(lu, pv, 2 * k, 2 * k, ta, m, m, 0, 1.0);
+  }
+  // y_L -= V_L b on this rank's left-side tips, y_R -= W_R a on its right-side tips; the
+  // interface tips (b-1, bottom) and (b, top) are a and b themselves
+  const int la = std::max(mg.a, c->l0), lb = std::min(b, c->l1);
+  const int ra = std::max(b, c->l0), rb = std::min(mg.c, c->l1);
+  if (lb > la) {
+    const int last = (lb == b) ? 1 : 0;
+    const int ML = (2 * (lb - la) - last) * k;
+    g3.add(gd(TIP(c, lv, 0, la, 0), k, 1, tb, m, 1, YB(la, 0), m, 1, YB(la, 0), m, 1, ML, m, k, -1.0, 1.0));
+    if (last) g3.add(gd(nullptr, 0, 0, nullptr, 0, 0, ta, m, 1, YB(b - 1, 1), m, 1, k, m, 0, 0.0, 1.0));
+  }
+  if (rb > ra) {
+    const int first = (ra == b) ? 1 : 0;
+    const int MR = (2 * (rb - ra) - first) * k;
+    g3.add(gd(TIP(c, lv, 1, ra, first), k, 1, ta, m, 1, YB(ra, first), m, 1, YB(ra, first), m, 1, MR, m, k, -1.0,
+              1.0));
+    if (first) g3.add(gd(nullptr, 0, 0, nullptr, 0, 0, tb, m, 1, YB(b, 0), m, 1, k, m, 0, 0.0, 1.0));
+  }
+  pp.gemm(g1);
+  pp.trs(ts);
+  pp.gemm(g2);
+  pp.gemm(g3);
+}
+
+// One merge level above the rank (transposed solve, Sec. 4.3): g1 / g2 are the sums of the
+// gathered partial products of the left / right ranks (rank order), then the transposed
+// interface solve and the updates of the interface tips this rank holds.
+static void shard_t_level(spike_ctx *c, Pipeline &pp, const ShardBufs &S, int m, int lv, const double *recv) {
+  const int k = c->k;
+  const int64_t kk = (int64_t)k * k, km = (int64_t)k * m;
+  const int mi = shard_merge(c, lv);
+  const Merge &mg = c->pl.levels[lv][mi];
+  double *Y = S.B.Y;
+  auto YB = [&](int i, int t) { return Y + ((int64_t)i * 2 + t) * km; };
+  const int64_t gm = c->merge_off[lv] + mi;
+  const double *lu = c->mlu + gm * 4 * kk;
+  const int *pv = c->mpiv + gm * 2 * k;
+  double *s2 = S.B.TM, *s1 = s2 + km;  // [g2; g1] -> [s2; s1]
+  const int gl0 = shard_rank_at(c, mg.a), gl1 = shard_rank_at(c, mg.b), gr1 = shard_rank_at(c, mg.c);
+  std::vector<SumDesc> sums{SumDesc{recv + (int64_t)gl0 * km, s1, km, km, gl1 - gl0, 0},
+                            SumDesc{recv + (int64_t)gl1 * km, s2, km, km, gr1 - gl1, 0}};
+  pp.sums(sums, km);
+  const int b = mg.b;
+  const double *Vlb = TIP(c, lv, 0, b - 1, 1), *Wrt = TIP(c, lv, 1, b, 0);
+  GemmBatch g2, g3, g4;
+  TrsBatch ts;
+  if (c->schur[lv][mi]) {
+    g2.add(gd(Vlb, 1, k, s2, m, 1, s1, m, 1, s1, m, 1, k, m, k, -1.0, 1.0));
+    ts.add(lu, pv, k, k, s1, m, m, 1, 1.0);
+    g3.add(gd(Wrt, 1, k, s1, m, 1, s2, m, 1, s2, m, 1, k, m, k, -1.0, 1.0));
+  } else {
+    ts.add(lu, pv, 2 * k, 2 * k, s2, m, m, 1, 1.0);
+  }
+  if (b >= c->l0 && b < c->l1)
+    g4.add(gd(c->ident, k, 1, s1, m, 1, YB(b, 0), m, 1, YB(b, 0), m, 1, k, m, k, -1.0, 1.0));
+  if (b - 1 >= c->l0 && b - 1 < c->l1)
+    g4.add(gd(c->ident, k, 1, s2, m, 1, YB(b - 1, 1), m, 1, YB(b - 1, 1), m, 1, k, m, k, -1.0, 1.0));
+  pp.gemm(g2);
+  pp.trs(ts);
+  pp.gemm(g3);
+  pp.gemm(g4);
+}
+
+// copy `rows` x m of the work array back to the caller's F (column-major)
+static void shard_finish(spike_ctx *c, Pipeline &pp, const ShardBufs &S, int m) {
+  double *src = S.Wm, *dst = c->sh_F;
+  const int64_t rows = c->nrow, ld = c->sh_ld;
+  cudaStream_t s = c->stream;
+  pp.ops.push_back([=](char *) { return launch_transpose(src, dst, rows, m, ld, 0, s); });
+}
+
+extern "C" int spike_shard_factor(const double *band, int64_t ldab, int64_t col0, int64_t n, int kl, int ku, int p,
+                                  int rank, int nranks, const spike_options *opt, spike_handle *out) {
+  if (!out) return -11;
+  *out = nullptr;
+  if (!band) return -1;
+  if (n < 1) return -4;
+  if (kl < 0) return -5;
+  if (ku < 0) return -6;
+  if (ldab < (int64_t)kl + ku + 1) return -2;
+  if (p < 1) return -7;
+  if (nranks < 1) return -9;
+  if (rank < 0 || rank >= nranks) return -8;
+  if (col0 < 0) return -3;
+  ShardSpec sh{rank, nranks, col0};
+  const int rc = factor_impl(band, ldab, n, kl, ku, p, 0, opt, out, &sh);
+  // factor_impl numbers arguments as spike_factor_ex (n, kl, ku, p = -3..-6); -3 and -9 here
+  // are its shard checks (col0 past the rank's first column, a rank count the plan cannot take)
+  switch (rc) {
+    case -4: return -5;
+    case -5: return -6;
+    case -6: return -7;
+    default: return rc;
+  }
+}
+
+extern "C" int spike_shard_pending(spike_handle h, int64_t *count) {
+  if (!valid(h)) return SPIKE_EHANDLE;
+  if (!count) return -2;
+  const int64_t k = h->k, m = h->sh_m;
+  switch (h->sh_op) {
+    case SH_FACTOR: *count = 4 * k * k; break;
+    case SH_N_LEVEL:
+    case SH_N_FINAL:
+    case SH_T_GTIPS: *count = 2 * k * m; break;
+    case SH_T_LEVEL: *count = k * m; break;
+    default: *count = 0;
+  }
+  return 0;
+}
+
+extern "C" int spike_shard_export(spike_handle h, double *send) {
+  if (!valid(h)) return SPIKE_EHANDLE;
+  if (!send) return -2;
+  spike_ctx *c = h;
+  cudaStream_t s = c->stream;
+  const int64_t kk = (int64_t)c->k * c->k, km = (int64_t)c->k * c->sh_m;
+  auto cp = [&](double *dst, const double *src, int64_t cnt) {
+    return cudaMemcpyAsync(dst, src, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, s);
+  };
+  const ShardBufs S = shard_bufs(c, std::max(1, c->sh_m), nullptr);
+  auto YB = [&](int i, int t) { return S.B.Y + ((int64_t)i * 2 + t) * km; };
+  const int lv = c->sh_level;
+  switch (c->sh_op) {
+    case SH_FACTOR:
+      SP_CUDA(cp(send, TIP(c, lv, 0, c->l0, 0), kk));
+      SP_CUDA(cp(send + kk, TIP(c, lv, 1, c->l0, 0), kk));
+      SP_CUDA(cp(send + 2 * kk, TIP(c, lv, 0, c->l1 - 1, 1), kk));
+      SP_CUDA(cp(send + 3 * kk, TIP(c, lv, 1, c->l1 - 1, 1), kk));
+      break;
+    case SH_N_LEVEL:
+    case SH_N_FINAL:
+      SP_CUDA(cp(send, YB(c->l0, 0), km));
+      SP_CUDA(cp(send + km, YB(c->l1 - 1, 1), km));
+      break;
+    case SH_T_GTIPS:  // this rank's corrections of its neighbours' boundary tips (zero at the ends)
+      if (c->l0 > 0) SP_CUDA(cp(send, YB(c->l0 - 1, 1), km));
+      else SP_CUDA(cudaMemsetAsync(send, 0, sizeof(double) * km, s));
+      if (c->l1 < c->nleaves) SP_CUDA(cp(send + km, YB(c->l1, 0), km));
+      else SP_CUDA(cudaMemsetAsync(send + km, 0, sizeof(double) * km, s));
+      break;
+    case SH_T_LEVEL:
+      SP_CUDA(cp(send, S.XP, km));
+      break;
+    default:
+      return SPIKE_ENOTSUP;  // no exchange pending
+  }
+  SP_CUDA(cudaStreamSynchronize(s));
+  return 0;
+}
+
+extern "C" int spike_shard_import(spike_handle h, const double *recv) {
+  if (!valid(h)) return SPIKE_EHANDLE;
+  if (!recv) return -2;
+  spike_ctx *c = h;
+  cudaStream_t s = c->stream;
+  const int G = c->nranks, m = std::max(1, c->sh_m);
+  const int64_t kk = (int64_t)c->k * c->k, km = (int64_t)c->k * m;
+  auto cp = [&](double *dst, const double *src, int64_t cnt) {
+    return cudaMemcpyAsync(dst, src, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, s);
+  };
+  const int lv = c->sh_level;
+  if (c->sh_op == SH_FACTOR) {
+    for (int g = 0; g < G; ++g) {
+      if (g == c->rank) continue;
+      const double *r = recv + (int64_t)g * 4 * kk;
+      const int f = c->leaf_first[g], l = c->leaf_first[g + 1] - 1;
+      SP_CUDA(cp(TIP(c, lv, 0, f, 0), r, kk));
+      SP_CUDA(cp(TIP(c, lv, 1, f, 0), r + kk, kk));
+      SP_CUDA(cp(TIP(c, lv, 0, l, 1), r + 2 * kk, kk));
+      SP_CUDA(cp(TIP(c, lv, 1, l, 1), r + 3 * kk, kk));
+    }
+    SP_TRY(factor_reduced_level(c, lv, c->sh_fscr + c->sh_tmp_off, c->sh_tmp_bytes));
+    c->sh_level = lv + 1;
+    if (c->sh_level >= c->NL) {
+      unsigned long long st[8];
+      SP_CUDA(cudaMemcpyAsync(st, c->status, sizeof(st), cudaMemcpyDeviceToHost, s));
+      SP_CUDA(cudaStreamSynchronize(s));
+      c->nan_flag = (int)st[2];
+      cudaFreeAsync(c->sh_fscr, s);
+      c->sh_fscr = nullptr;
+      c->sh_op = SH_NONE;
+    }
+    return 0;
+  }
+  const ShardBufs S = shard_bufs(c, m, nullptr);
+  auto YB = [&](int i, int t) { return S.B.Y + ((int64_t)i * 2 + t) * km; };
+  const int tr = (c->sh_op == SH_T_GTIPS || c->sh_op == SH_T_LEVEL) ? 1 : 0;
+  Pipeline pp;
+  pp.st = s;
+  switch (c->sh_op) {
+    case SH_N_LEVEL:
+      for (int g = 0; g < G; ++g) {
+        if (g == c->rank) continue;
+        SP_CUDA(cp(YB(c->leaf_first[g], 0), recv + (int64_t)g * 2 * km, km));
+        SP_CUDA(cp(YB(c->leaf_first[g + 1] - 1, 1), recv + (int64_t)g * 2 * km + km, km));
+      }
+      shard_n_level(c, pp, S, m, lv);
+      c->sh_level = lv + 1;
+      if (c->sh_level >= c->NL) c->sh_op = SH_N_FINAL;
+      break;
+    case SH_N_FINAL: {
+      // the neighbours' boundary solution tips, then the retrieval of this rank's blocks
+      if (c->rank > 0) SP_CUDA(cp(YB(c->l0 - 1, 1), recv + (int64_t)(c->rank - 1) * 2 * km + km, km));
+      if (c->rank + 1 < G) SP_CUDA(cp(YB(c->l1, 0), recv + (int64_t)(c->rank + 1) * 2 * km, km));
+      SolveRange rg;
+      rg.head = false;
+      rg.lv_lo = rg.lv_hi = c->NL;
+      build_solve(c, pp, S.B, m, 0, false, rg);
+      shard_finish(c, pp, S, m);
+      c->sh_op = SH_NONE;
+      break;
+    }
+    case SH_T_GTIPS: {
+      GemmBatch ga;
+      if (c->rank > 0)
+        ga.add(gd(c->ident, c->k, 1, recv + (int64_t)(c->rank - 1) * 2 * km + km, m, 1, YB(c->l0, 0), m, 1,
+                  YB(c->l0, 0), m, 1, c->k, m, c->k, 1.0, 1.0));
+      if (c->rank + 1 < G)
+        ga.add(gd(c->ident, c->k, 1, recv + (int64_t)(c->rank + 1) * 2 * km, m, 1, YB(c->l1 - 1, 1), m, 1,
+                  YB(c->l1 - 1, 1), m, 1, c->k, m, c->k, 1.0, 1.0));
+      pp.gemm(ga);
+      c->sh_level = c->NL - 1;
+      shard_t_partial(c, pp, S, m, c->sh_level);
+      c->sh_op = SH_T_LEVEL;
+      break;
+    }
+    case SH_T_LEVEL:
+      shard_t_level(c, pp, S, m, lv, recv);
+      if (lv - 1 >= c->lvl) {
+        c->sh_level = lv - 1;
+        shard_t_partial(c, pp, S, m, lv - 1);
+      } else {
+        SolveRange rg;
+        rg.head = false;
+        rg.lv_lo = 0;
+        rg.lv_hi = c->lvl;
+        build_solve(c, pp, S.B, m, 1, false, rg);
+        shard_finish(c, pp, S, m);
+        c->sh_op = SH_NONE;
+      }
+      break;
+    default:
+      return SPIKE_ENOTSUP;
+  }
+  (void)tr;
+  return pp.run(c);
+}
+
+extern "C" int spike_shard_solve(spike_handle h, double *F, int64_t ldf, int nrhs, char trans) {
+  if (!valid(h)) return SPIKE_EHANDLE;
+  spike_ctx *c = h;
+  if (!c->shard || c->f32 || c->pivot) return SPIKE_ENOTSUP;
+  if (c->sh_op != SH_NONE) return SPIKE_ENOTSUP;  // the previous operation still has exchanges to run
+  if (!F) return -2;
+  if (ldf < c->nrow) return -3;
+  if (nrhs < 1) return -4;
+  const int tr = (trans == 'N' || trans == 'n') ? 0 : ((trans == 'T' || trans == 't') ? 1 : -1);
+  if (tr < 0) return -5;
+  if (!is_device_ptr(F)) return SPIKE_ENOTSUP;
+  const int m = nrhs;
+  cudaStream_t s = c->stream;
+  size_t need = 0;
+  shard_bufs(c, m, &need);
+  SP_TRY(ensure(&c->scr, &c->scr_bytes, need, s));
+  const ShardBufs S = shard_bufs(c, m, nullptr);
+  c->sh_F = F;
+  c->sh_ld = ldf;
+  c->sh_m = m;
+  Pipeline pp;
+  pp.st = s;
+  {
+    double *src = F, *dst = S.Wm;
+    const int64_t rows = c->nrow;
+    pp.ops.push_back([=](char *) { return launch_transpose(src, dst, rows, m, ldf, 1, s); });
+  }
+  const bool alone = c->nranks == 1;
+  SolveRange rg;
+  rg.tail = alone;
+  rg.lv_lo = 0;
+  rg.lv_hi = (tr == 0 || alone) ? c->lvl : 0;  // T runs the local levels last (descending)
+  build_solve(c, pp, S.B, m, tr, false, rg);
+  if (alone) {
+    shard_finish(c, pp, S, m);
+    c->sh_op = SH_NONE;
+  } else if (tr == 0) {
+    c->sh_op = SH_N_LEVEL;
+    c->sh_level = c->lvl;
+  } else {
+    c->sh_op = SH_T_GTIPS;
+  }
+  return pp.run(c);
+}
+
 extern "C" int spike_solve_ex(spike_handle h, double *F, int64_t ldf, int nrhs, char trans) {
   return solve_impl(h, F, ldf, nrhs, trans, nullptr, 0, nullptr, false);
 }
@@ -1696,7 +2315,7 @@ static int solve_batch_impl(const spike_handle *hs, double *const *F, const int 
   for (int i = 0; i < count; ++i) {
     spike_ctx *c = hs[i];
     if (!valid(c)) return SPIKE_EHANDLE;
-    if (c->f32 || c->pivot) return SPIKE_ENOTSUP;
+    if (c->f32 || c->pivot || c->shard) return SPIKE_ENOTSUP;
     if (nrhs[i] < 0) return -3;
     const int64_t n = c->pl.n, m = nrhs[i], km = (int64_t)c->k * m;
     size_t maxm = 1;
@@ -1864,6 +2483,51 @@ extern "C" int spike_backward_error(const double *band, int64_t ldab, int64_t n,
   return 0;
 }
 
+extern "C" int spike_residual(spike_handle h, const double *X, const double *F, double *R, int nrhs, char trans,
+                              double *berr) {
+  if (!valid(h)) return SPIKE_EHANDLE;
+  if (!X) return -2;
+  if (!F) return -3;
+  if (!R) return -4;
+  if (nrhs < 1) return -5;
+  const int tr = (trans == 'N' || trans == 'n') ? 0 : ((trans == 'T' || trans == 't') ? 1 : -1);
+  if (tr < 0) return -6;
+  if (!h->sfrag[0]) return SPIKE_ENOTSUP;
+  if (!is_device_ptr(X) || !is_device_ptr(F) || !is_device_ptr(R)) return SPIKE_ENOTSUP;
+  spike_ctx *c = h;
+  const int64_t n = c->pl.n;
+  cudaStream_t s = c->stream;
+  const size_t xb = split_x_bytes(n, c->pl.kl, c->pl.ku, nrhs);
+  const size_t nb = sizeof(unsigned long long) * (1 + 2 * (size_t)nrhs);
+  char *scr = nullptr;
+  SP_CUDA(dev_alloc((void **)&scr, xb + ((nb + 255) & ~size_t(255)), s));
+  unsigned long long *nrm = (unsigned long long *)(scr + xb);
+  int e = (int)cudaMemsetAsync(scr, 0x40, xb, s);
+  if (!e) e = launch_resid_split(c->sfrag[tr], c->srexp[tr], c->snorm + tr, n, c->pl.kl, c->pl.ku, tr, X, F, R, nrhs,
+                                 scr, nrm, s);
+  std::vector<unsigned long long> hn(1 + 2 * (size_t)nrhs);
+  if (!e) e = (int)cudaMemcpyAsync(hn.data(), nrm, nb, cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(scr, s);
+  if (!e) e = (int)cudaStreamSynchronize(s);
+  if (e) {
+    g_cuda_err = std::string("residual: ") + cudaGetErrorString((cudaError_t)e);
+    return SPIKE_ECUDA;
+  }
+  if (berr) {
+    auto as_d = [](unsigned long long b) {
+      double d;
+      memcpy(&d, &b, sizeof(d));
+      return d;
+    };
+    const double an = as_d(hn[0]);
+    for (int col = 0; col < nrhs; ++col) {
+      const double r = as_d(hn[1 + 2 * col]), x = as_d(hn[2 + 2 * col]);
+      berr[col] = (an > 0 && x > 0) ? r / (an * x) : (r == 0 ? 0.0 : INFINITY);
+    }
+  }
+  return 0;
+}
+
 extern "C" int spike_get_timings(spike_handle h, double *ms, int count) {
   if (!valid(h)) return SPIKE_EHANDLE;
   if (!ms || count < 0) return -2;
@@ -1912,6 +2576,7 @@ extern "C" void spike_free(spike_handle h) {
   for (auto &g : h->gcache) drop_graph(g, s);
   h->gcache.clear();
   if (h->mem) cudaFreeAsync(h->mem, s);
+  if (h->sh_fscr) cudaFreeAsync(h->sh_fscr, s);
   if (h->scr) cudaFreeAsync(h->scr, s);
   if (h->dargs) cudaFreeAsync(h->dargs, s);
   cudaStreamSynchronize(s);

@@ -49,6 +49,10 @@ struct Plan {
 // Returns 0 or -(argument index) on invalid input.  r13 > 0 overrides the partition ratio.
 int make_plan(int64_t n, int kl, int ku, int t, double K, int nrhs_hint, int flags, double r13, Plan &out);
 
+// Partition-range sharding: leaf_first (nranks + 1 entries) and the number of merge levels
+// that stay inside one rank.  0, or -1 for an invalid rank count (see plan.cpp).
+int shard_ranges(const Plan &pl, int nranks, std::vector<int> &leaf_first, int &local_levels);
+
 // ------------------------------------------------------- device descriptors
 
 // Leaf geometry as the kernels see it (local frame = reversed for UL leaves).
@@ -192,6 +196,20 @@ int launch_sum_blocks(const SumDesc *d, int ndesc, int64_t max_elems, void *stre
 // [0] ||op(A)||_inf, [1+2c] ||op(A)x_c - f_c||_inf, [2+2c] ||x_c||_inf.
 int launch_berr(const double *band, int64_t ldab, int64_t n, int kl, int ku, const double *X, const double *F,
                 int nrhs, int trans, unsigned long long *scratch, void *stream);
+
+// FP64-accurate residual on the tensor cores (resid_split.cu): op(A) split once per
+// factorization into int8 digit fragments (split_band_bytes per orientation, n int32 row
+// exponents, one norm word), X split per call into split_x_bytes of scratch (zeroed by the
+// caller before its first use: the zero rows around each column are never written).
+bool split_supported(int kl, int ku);
+size_t split_band_bytes(int64_t n, int kl, int ku);
+size_t split_x_bytes(int64_t n, int kl, int ku, int nrhs);
+int launch_split_band(const double *band, int64_t ldab, int64_t n, int kl, int ku, int trans, int *rexp,
+                      unsigned long long *norm_bits, void *frag, void *stream);
+// R = F - op(A) X; norms as launch_residual (all words written by the call)
+int launch_resid_split(const void *frag, const int *rexp, const unsigned long long *anorm_bits, int64_t n, int kl,
+                       int ku, int trans, const double *X, const double *F, double *R, int nrhs, void *xdig,
+                       unsigned long long *norms, void *stream);
 
 // spk tip storage index: level lv, spike s (0 = V, 1 = W), leaf i, tip t (0 = top, 1 = bottom)
 inline int64_t tip_index(int lv, int s, int i, int t, int nleaves, int k) {

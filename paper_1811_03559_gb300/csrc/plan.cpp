@@ -155,4 +155,28 @@ int make_plan(int64_t n, int kl, int ku, int t, double K, int nrhs_hint, int fla
   return -4;
 }
 
+// Partition-range sharding (the SPIKE-MPI direction of Sec. 3 with the recursion of Sec. 2.2):
+// rank g of nranks owns partitions [g P / nranks, (g + 1) P / nranks) of the plan, i.e. a
+// contiguous power-of-two range of the 2^m partitions with the 2x2 pairs inside them.  The
+// pair level and the first log2(P / nranks) power-of-two levels merge groups inside one rank;
+// the remaining log2(nranks) levels merge groups of several ranks.  Returns 0, or -1 when
+// nranks is not a power of two between 1 and P.
+int shard_ranges(const Plan &pl, int nranks, std::vector<int> &leaf_first, int &local_levels) {
+  if (nranks < 1 || (nranks & (nranks - 1)) != 0 || nranks > pl.P) return -1;
+  const int per = pl.P / nranks;
+  leaf_first.assign(nranks + 1, pl.nleaves);
+  for (int g = 0; g < nranks; ++g) {
+    for (int i = 0; i < pl.nleaves; ++i)
+      if (pl.leaves[i].part >= g * per) {
+        leaf_first[g] = i;
+        break;
+      }
+  }
+  leaf_first[nranks] = pl.nleaves;
+  int lg = 0;
+  while ((1 << lg) < per) ++lg;
+  local_levels = (pl.r > 0 ? 1 : 0) + lg;
+  return 0;
+}
+
 }  // namespace spk

@@ -56,7 +56,7 @@ EXPORTS = ["spike_plan", "spike_factor", "spike_factor_ex", "spike_solve", "spik
            "spike_free", "spike_strerror", "spike_last_cuda_error", "spike_backward_error_noalloc",
            "spike_measure_fp64_peak", "spike_factor_bytes", "spike_solve_workspace", "spike_solve_ws",
            "spike_measure_K", "spike_tune", "spike_solve_batch", "spike_solve_batch_workspace",
-           "spike_release_cached"]
+           "spike_release_cached", "spike_residual"]
 SPIKE_ELIMIT = -1006
 NOALLOC_MAX_NRHS = 1024
 
@@ -66,6 +66,7 @@ FLAG_MIXED = 4
 FLAG_BATCH_INVARIANT = 8
 FLAG_BORROW_BAND = 16
 FLAG_GRAPHS = 32
+FLAG_FP64_RESIDUAL = 64
 NUMERICS_NAN_PIVOT = 1
 NUMERICS_SINGULAR_INTERFACE = 2
 MIXED_TOL = 1e-14
@@ -110,6 +111,7 @@ def lib():
         L.spike_measure_K.argtypes = [dp, i64, i64, i32, i32, vp, ctypes.POINTER(ctypes.c_double)]
         L.spike_solve_batch.argtypes = [vp, vp, vp, i32, ctypes.c_char, vp, vp, i64]
         L.spike_release_cached.argtypes = [ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        L.spike_residual.argtypes = [vp, dp, dp, dp, i32, ctypes.c_char, dp]
         L.spike_solve_batch_workspace.argtypes = [vp, vp, i32, ctypes.c_char, ctypes.POINTER(i64)]
         L.spike_tune.argtypes = [dp, i64, i64, i32, i32, i32, i32, vp, i32, vp, i32, vp, vp,
                                  ctypes.POINTER(TuneResult)]
@@ -175,14 +177,15 @@ class Factorization:
 
     def __init__(self, band, kl, ku, p, pivot=0, K=0.0, nrhs_hint=0, stream=None, timing=False, n=None,
                  stage_balance=False, mixed=False, batch_invariant=False, R13=0.0, borrow_band=False,
-                 refine_tol=0.0, graphs=False):
+                 refine_tol=0.0, graphs=False, fp64_residual=False):
         rows, ldab = band.shape
         self.n, self.kl, self.ku = (rows if n is None else n), kl, ku
         n = self.n
         s = _torch_stream(band) if stream is None else ctypes.c_void_p(stream)
         flags = (FLAG_TIMING if timing else 0) | (FLAG_STAGE_BALANCE if stage_balance else 0) | \
             (FLAG_MIXED if mixed else 0) | (FLAG_BATCH_INVARIANT if batch_invariant else 0) | \
-            (FLAG_BORROW_BAND if borrow_band else 0) | (FLAG_GRAPHS if graphs else 0)
+            (FLAG_BORROW_BAND if borrow_band else 0) | (FLAG_GRAPHS if graphs else 0) | \
+            (FLAG_FP64_RESIDUAL if fp64_residual else 0)
         self._opt = SpikeOptions(K=K, nrhs_hint=nrhs_hint, flags=flags, stream=s, R13=R13, refine_tol=refine_tol)
         # a borrowed device band is read by every mixed-precision solve until spike_free
         self._borrowed = band if borrow_band else None
@@ -200,6 +203,18 @@ class Factorization:
         if rc != 0:
             raise SpikeError(rc, "spike_solve_ex")
         return F
+
+    def residual(self, X, F, R, trans="N"):
+        """R = F - op(A) X with the tensor-core residual of a mixed-precision handle
+        (spike_residual; device tensors of shape (nrhs, n)).  Returns the per-column
+        backward errors."""
+        nrhs = _check_rhs(X, self.n)
+        out = np.zeros(nrhs)
+        rc = lib().spike_residual(self._h, _ptr(X), _ptr(F), _ptr(R), nrhs, trans.encode(),
+                                  out.ctypes.data_as(ctypes.c_void_p))
+        if rc != 0:
+            raise SpikeError(rc, "spike_residual")
+        return out
 
     def workspace_bytes(self, nrhs, trans="N", host_f=False):
         """Device scratch that solve_ws needs for nrhs columns (spike_solve_workspace)."""
@@ -275,10 +290,10 @@ def kernel_launches():
 
 
 def factor_bytes(n, kl, ku, p, pivot=0, mixed=False, host_band=False, K=0.0, nrhs_hint=0, stage_balance=False,
-                 borrow_band=False):
+                 borrow_band=False, fp64_residual=False):
     """(resident, transient) device bytes of a factorization, computed without a GPU."""
     flags = (FLAG_STAGE_BALANCE if stage_balance else 0) | (FLAG_MIXED if mixed else 0) | \
-        (FLAG_BORROW_BAND if borrow_band else 0)
+        (FLAG_BORROW_BAND if borrow_band else 0) | (FLAG_FP64_RESIDUAL if fp64_residual else 0)
     opt = SpikeOptions(K=K, nrhs_hint=nrhs_hint, flags=flags)
     res, tr = ctypes.c_int64(0), ctypes.c_int64(0)
     rc = lib().spike_factor_bytes(n, kl, ku, p, pivot, ctypes.byref(opt), 1 if host_band else 0, ctypes.byref(res),

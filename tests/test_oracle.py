@@ -456,3 +456,43 @@ def test_inverse_norm_estimate_is_a_lower_bound(seed):
     est = condest.inv_norm_1_estimate(oracle.BandLU(band, kl, ku))
     assert est <= true * (1 + 1e-12)
     assert est >= true * 0.5
+
+
+# ------------------------------------------------------------ exact residual pins
+
+def test_residual_exact_integer_inputs_match_plain_residual():
+    # integer entries: every product and sum is exact in FP64, so both must agree bit for bit
+    rng = np.random.default_rng(71)
+    n, kl, ku = 60, 3, 5
+    band = rng.integers(-50, 51, size=(n, kl + ku + 1)).astype(np.float64)
+    X = rng.integers(-1000, 1001, size=(3, n)).astype(np.float64)
+    F = rng.integers(-10 ** 6, 10 ** 6, size=(3, n)).astype(np.float64)
+    for trans in ("N", "T"):
+        plain = F - oracle.gbmv(band, kl, ku, X, trans)
+        assert np.array_equal(metrics.residual_exact(band, kl, ku, X, F, trans), plain)
+
+
+def test_residual_exact_recovers_cancelled_bits():
+    # a x = (1 + 2^-30)(1 - 2^-30) = 1 - 2^-60: FP64 rounds the product to 1 and loses r
+    band = np.array([[1.0 + 2.0 ** -30]])
+    X = np.array([[1.0 - 2.0 ** -30]])
+    F = np.array([[1.0]])
+    assert (F - band[0, 0] * X)[0, 0] == 0.0
+    assert metrics.residual_exact(band, 0, 0, X, F)[0, 0] == 2.0 ** -60
+
+
+@pytest.mark.parametrize("trans", ["N", "T"])
+def test_residual_exact_against_rationals(trans):
+    from fractions import Fraction
+    rng = np.random.default_rng(72)
+    n, kl, ku = 14, 2, 3
+    band = rng.normal(size=(n, kl + ku + 1))
+    X = rng.normal(size=(2, n))
+    F = rng.normal(size=(2, n))
+    A = dense_from_band(band, kl, ku)
+    Aop = A if trans == "N" else A.T
+    R = metrics.residual_exact(band, kl, ku, X, F, trans)
+    for c in range(2):
+        for i in range(n):
+            exact = Fraction(F[c, i]) - sum(Fraction(Aop[i, j]) * Fraction(X[c, j]) for j in range(n))
+            assert R[c, i] == float(exact)  # correctly rounded

@@ -149,10 +149,15 @@ def test_factor_bytes_accounting(built, n, k, p):
     r64h, t64h = fb(host_band=True)
     assert r64h == r64 and r64 == fb(borrow_band=True)[0]  # FP64 handles keep no band
     assert abs((t64h - t64) - band_bytes) <= slack           # staged host band
-    rmix, tmix = fb(mixed=True)
-    rbor, _ = fb(mixed=True, borrow_band=True)
+    rmix, tmix = fb(mixed=True, fp64_residual=True)
+    rbor, _ = fb(mixed=True, borrow_band=True, fp64_residual=True)
     assert abs((rmix - rbor) - band_bytes) <= slack           # the FP64 band copy, unless borrowed
-    assert fb(mixed=True, borrow_band=True, host_band=True)[0] == rmix  # borrowing needs a device band
+    assert fb(mixed=True, borrow_band=True, host_band=True, fp64_residual=True)[0] == rmix  # needs a device band
+    # the tensor-core residual's digit planes of A and A^T: per 16-row block, 8 planes x
+    # ceil((16 + kl + ku + 3) / 32) chunks x 512 bytes, plus one int32 row exponent per row
+    nch = (16 + 2 * k + 3 + 31) // 32
+    split = 2 * (((n + 15) // 16) * 8 * nch * 512 + 4 * n)
+    assert abs((fb(mixed=True)[0] - rmix) - split) <= slack
     ldf = 2 * k + 2
     assert abs((r64 - rbor) - 4 * n * (ldf + 1)) <= slack     # factors and 1/u_jj: 8 -> 4 bytes
     assert abs((t64 - tmix) - 4 * n * 2 * k) <= slack         # the spike right-hand sides Z in FP32
