@@ -277,6 +277,163 @@ def mixed_workload_leg(dev, reps=2):
     return out
 
 
+def tensor_residual_leg(band, k, X, FN, FT, p, reps=5):
+    """The mixed-precision refinement residual on the tensor cores (spike_residual: int8 digit
+    slices, bf16 products with exact FP32 accumulation) against the FP64 kernel
+    (spike_backward_error) on the step's matrix and right-hand sides; tensor flops = 43 digit
+    products x 2 x (rows x K x columns) with K = 32 ceil((19 + kl + ku) / 32) columns per
+    16-row block."""
+    import torch
+    from paper_1811_03559_gb300 import spike
+    n, m = band.shape[0], X.shape[0]
+    fac = spike.Factorization(band, k, k, p, nrhs_hint=m, stage_balance=True, mixed=True)
+    R = torch.empty_like(FN)
+
+    def t(fn):
+        ts = []
+        for _ in range(reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts[1:]))
+
+    out = {}
+    KP = 32 * ((19 + 2 * k + 31) // 32)
+    flops = 43 * 2.0 * n * KP * m
+    for tr, F in (("N", FN), ("T", FT)):
+        ms = t(lambda: fac.residual(X, F, R, tr))
+        out[tr] = {"tensor_ms": ms, "fp64_ms": t(lambda: spike.backward_error(band, k, k, X, F, tr)),
+                   "tensor_tflops": flops / (ms * 1e-3) / 1e12}
+    fac.free()
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    bf16 = peaks.get("bf16_tflops")
+    out["flops_per_call"] = flops
+    out["peak_bf16_tflops_measured"] = bf16
+    out["frac_of_measured_bf16"] = out["N"]["tensor_tflops"] / bf16 if bf16 else None
+    out["note"] = ("legacy mma.sync bf16 path; an in-process probe of mma.sync m16n8k16 measured about 600 TFLOP/s "
+                   "on this part, the measured peak is cuBLAS (tcgen05)")
+    return out
+
+
+def config_grid_leg(dev, reps=2):
+    """Every point of the large dominant workload: n = 2^20, k in {32, 128, 320}, p in {64, 148,
+    192}, nrhs in {1, 64} (DD 1.01; the times do not depend on the values): factor + N solve +
+    T solve per point, with algorithmic GB/s, method TFLOP/s against the FP64 peak and the
+    backward error.  Bands are drawn on the device (inputs.make_band_torch)."""
+    import torch
+    from paper_1811_03559_gb300 import inputs, spike
+    n, dd = 1 << 20, 1.01
+    rows = []
+    for k in (32, 128, 320):
+        band = inputs.make_band_torch(n, k, k, seed=1, dd=dd, device=dev)
+        for m in (1, 64):
+            g = torch.Generator(device=dev)
+            g.manual_seed(11 + m)
+            xs = torch.rand((m, n), generator=g, dtype=torch.float64, device=dev) * 2.0 - 1.0
+            FN = inputs.band_matvec_torch(band, k, k, xs, "N")
+            FT = inputs.band_matvec_torch(band, k, k, xs, "T")
+            for p in (64, 148, 192):
+                _, offs, flags = spike.plan(n, k, k, p, nrhs_hint=m, stage_balance=True)
+                fl = method_flops(offs, flags, k, m)
+                times, st = [], {}
+                for rep in range(reps + 1):
+                    X1, X2 = FN.clone(), FT.clone()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize()
+                    e0.record()
+                    fac = spike.Factorization(band, k, k, p, nrhs_hint=m, stage_balance=True, timing=rep == reps)
+                    fac.solve(X1, "N")
+                    fac.solve(X2, "T")
+                    e1.record()
+                    torch.cuda.synchronize()
+                    if rep:
+                        times.append(e0.elapsed_time(e1))
+                    if rep == reps:
+                        st = fac.timings()
+                    fac.free()
+                ms = float(np.median(times))
+                rows.append({"k": k, "nrhs": m, "p": p, "ms_per_step": ms, "GB_s": alg_bytes(n, k, m) / (ms * 1e-3) / 1e9,
+                             "method_tflops": fl["step"] / (ms * 1e-3) / 1e12,
+                             "frac_fp64": fl["step"] / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                             "block_lu_frac_fp64": fl["block_lu"] / (st["block_lu"] * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                             "factor_ms": st["factor"], "solve_n_ms": st["solve_n"], "solve_t_ms": st["solve_t"],
+                             "backward_error": max(float(spike.backward_error(band, k, k, X1, FN, "N").max()),
+                                                   float(spike.backward_error(band, k, k, X2, FT, "T").max()))})
+            del FN, FT, xs
+        del band
+        torch.cuda.empty_cache()
+    return {"workload": "n=%d, DD %g, k in {32,128,320}, p in {64,148,192}, nrhs in {1,64}: spike_factor + "
+                        "spike_solve N + spike_solve T (stage-balanced sizing), median of %d" % (n, dd, reps),
+            "unit": "GB/s", "points": rows}
+
+
+def pivoting_leg(dev, reps=3):
+    """The pivoting workload (Sec. 5): n = 262,144, k in {16, 64}, nrhs = 8, p = 148, N(0,1) entries
+    with the diagonal at 0.3 x the row's off-diagonal absolute sum (sign kept), factor + N + T.
+    The block GEPP's method flops (k multipliers and a k x 2k update per column, U filled to
+    2k) against the FP64 peak, beside the non-pivoting block LU's rate on the same matrix."""
+    import torch
+    from paper_1811_03559_gb300 import inputs, spike
+    n, p, m = 262_144, 148, 8
+    out = {"workload": "n=%d p=%d nrhs=%d, N(0,1) entries, diagonal 0.3 x row off-diagonal |.| sum (seed 2)"
+                       % (n, p, m), "cases": []}
+    for k in (16, 64):
+        seed = 2
+        while True:
+            pr = inputs.make_problem(n, k, k, m, seed=seed, dist="normal", dd=0.3, keep_sign=True)
+            band = torch.from_numpy(pr["band"]).to(dev)
+            fac = spike.Factorization(band, k, k, p, pivot=1, nrhs_hint=m)
+            ok = fac.status == 0
+            fac.free()
+            if ok:
+                break
+            seed += 1
+        FN = torch.from_numpy(pr["F"]).to(dev)
+        FT = torch.from_numpy(inputs.band_matvec(pr["band"], k, k, pr["xstar"], "T")).to(dev)
+        _, offs, _ = spike.plan(n, k, k, p, nrhs_hint=m)
+        sizes = np.diff(offs).astype(np.float64)
+        lu_flops = float(np.sum(sizes * (4.0 * k * k + k)))  # per row: k multipliers, k x 2k update
+        row = {"k": k, "seed": seed}
+        for piv in (1, 0):
+            times, st = [], {}
+            for rep in range(reps + 1):
+                X1, X2 = FN.clone(), FT.clone()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record()
+                fac = spike.Factorization(band, k, k, p, pivot=piv, nrhs_hint=m, timing=True)
+                fac.solve(X1, "N")
+                fac.solve(X2, "T")
+                e1.record()
+                torch.cuda.synchronize()
+                if rep:
+                    times.append(e0.elapsed_time(e1))
+                st = fac.timings()
+                fac.free()
+            ms = float(np.median(times))
+            key = "pivoting" if piv else "non_pivoting"
+            flops = lu_flops if piv else float(np.sum(sizes * (2.0 * k * k + k)))
+            row[key] = {"ms_per_step": ms, "GB_s": alg_bytes(n, k, m) / (ms * 1e-3) / 1e9,
+                        "factor_ms": st["factor"], "block_lu_ms": st["block_lu"], "spikes_ms": st["spikes"],
+                        "solve_n_ms": st["solve_n"], "solve_t_ms": st["solve_t"],
+                        "block_lu_gflops": flops / (st["block_lu"] * 1e-3) / 1e9,
+                        "backward_error": max(float(spike.backward_error(band, k, k, X1, FN, "N").max()),
+                                              float(spike.backward_error(band, k, k, X2, FT, "T").max()))}
+            if piv:
+                row[key]["block_lu_frac_fp64"] = flops / (st["block_lu"] * 1e-3) / 1e12 / FP64_PEAK_TFLOPS
+        out["cases"].append(row)
+        del band, FN, FT
+    return out
+
+
 def _cpu_serve_one(args):
     """One request of the serving workload on the CPU oracle: banded GEPP + solve (one core)."""
     import oracle
@@ -486,7 +643,9 @@ def main():
     ap.add_argument("--p", type=int, default=148)
     ap.add_argument("--nrhs", type=int, default=64)
     ap.add_argument("--dd", type=float, default=1.01)
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=None, help="host-buffer steps (default: --steps)")
+    ap.add_argument("--no-grid", action="store_true", help="skip the timed grid of the large dominant workload")
+    ap.add_argument("--no-pivot", action="store_true", help="skip the pivoting workload leg")
     ap.add_argument("--cpu-sample", type=int, default=262144,
                     help="rows of the workload the CPU oracle baseline solves (about 10 s on one Arm core)")
     ap.add_argument("--no-cpu", action="store_true")
@@ -503,6 +662,8 @@ def main():
     ap.add_argument("--serve-batch-systems", type=int, default=1,
                     help="matrices whose FP64 requests may share one solve (spike_solve_batch)")
     args = ap.parse_args()
+    if args.e2e_steps is None:
+        args.e2e_steps = args.steps
     n, k, p, m, dd, seed = args.n, args.k, args.p, args.nrhs, args.dd, 1
     workload = "n=%d kl=ku=%d p=%d nrhs=%d DD=%g: spike_factor + spike_solve N + spike_solve T" % (n, k, p, m, dd)
 
@@ -641,8 +802,11 @@ def main():
         mx = variant(m, True)
         f1 = variant(1, False)
         m1 = variant(1, True)
+        tres = tensor_residual_leg(band, k, torch.from_numpy(pr["xstar"]).to(dev), F1src, F2src, p)
         mixed = {"method": "FP32 block factorizations and sweeps, FP64 spike tips and reduced system, FP64 "
-                           "iterative refinement to backward error <= 1e-14 (SPIKE_FLAG_MIXED)",
+                           "iterative refinement to backward error <= 1e-14 (SPIKE_FLAG_MIXED), residuals "
+                           "on the tensor cores to FP64 accuracy",
+                 "tensor_residual": tres,
                  "unit": "GB/s",
                  "nrhs_%d" % m: dict(mx, speedup_vs_fp64=(ms / args.steps) / mx["ms_per_step"]),
                  "nrhs_1": {"fp64": f1, "mixed": m1, "speedup_vs_fp64": f1["ms_per_step"] / m1["ms_per_step"]}}
@@ -675,6 +839,8 @@ def main():
     mixed_workload = None
     if not args.no_mixed and extras:
         mixed_workload = mixed_workload_leg(dev)
+    grid = config_grid_leg(dev) if extras and not args.no_grid else None
+    pivoting = pivoting_leg(dev) if extras and not args.no_pivot else None
     graphs = graphs_leg(dev) if extras and not args.no_tune else None
     tuning = None
     if not args.no_tune and extras:
@@ -722,6 +888,7 @@ def main():
                 "d2h_bytes_per_step": int(2 * 8 * n * m), "steps": args.e2e_steps, "warmup": e2e_warm,
                 "ms_per_step": e2e_ms},
         "variants": {"mixed_fp32_fp64_refinement": mixed, "mixed_precision_workload": mixed_workload,
+                     "large_dominant_grid": grid, "pivoting_workload": pivoting,
                      "cuda_graphs_repeated_solves": graphs},
         "serving": serving,
         "tuning": tuning,

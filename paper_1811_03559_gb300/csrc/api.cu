@@ -1922,11 +1922,13 @@ static ShardBufs shard_bufs(spike_ctx *c, int m, size_t *bytes) {
                ot = carve(sizeof(double) * maxm * 2 * km), op = carve(sizeof(double) * (size_t)c->nleaves * km),
                ox = carve(sizeof(double) * km);
   ShardBufs S;
-  char *base = c->scr;
+  memset(&S, 0, sizeof(S));
   if (bytes) {
     *bytes = off;
-    base = nullptr;
+    return S;
   }
+  char *base = c->scr;
+  if (!base) return S;  // no solve scratch yet (a factorization's exchanges)
   S.Wm = (double *)(base + ow);
   S.Hm = (double *)(base + oh);
   S.B.W = (char *)S.Wm - (ptrdiff_t)(c->row0 * m * (int64_t)sizeof(double));
