@@ -81,7 +81,7 @@ extern "C" {
 #define SPIKE_FLAG_BORROW_BAND 16
 /* CUDA graphs for repeated solves: an FP64 solve of device buffers is run directly the
  * first time a call (nrhs, trans, F pointer, ldf, scratch) is seen, captured as a CUDA
- * graph the second time, and replayed from then on (up to 8 graphs per handle, least
+ * graph the second time, and replayed from then on (up to 16 graphs per handle, least
  * recently used replaced).  A replay launches the whole solve at once instead of a few
  * dozen separate launches; results are those of the direct launches.  The buffers a
  * graph was captured with must not be freed while it may be replayed (F is the caller's;
@@ -92,8 +92,9 @@ extern "C" {
  * residual (see spike_residual).  By default a mixed-precision handle splits op(A) once, at
  * factorization, into integer digit planes (about 16 n (kl + ku + 35) bytes for N and T
  * together, counted by spike_factor_bytes) and forms each residual of 8 or more columns on
- * the tensor cores, to FP64 accuracy; with fewer columns, or bandwidths above about 330,
- * the FP64 kernel is used either way. */
+ * the tensor cores, to FP64 accuracy; with fewer columns (except on SPIKE_FLAG_BATCH_INVARIANT
+ * handles, which use it for every column count), or kl + ku above about 540, the FP64 kernel
+ * is used. */
 #define SPIKE_FLAG_FP64_RESIDUAL 64
 #define SPIKE_MIXED_TOL 1e-14
 #define SPIKE_MIXED_MAX_STEPS 10
@@ -249,6 +250,20 @@ int spike_solve_ws(spike_handle h, double *F, int64_t ldf, int nrhs, char trans,
  * must not be used by other threads during the call. */
 int spike_solve_batch(const spike_handle *hs, double *const *F, const int *nrhs, int count, char trans,
                       void *stream, void *workspace, int64_t ws_bytes);
+
+/* Factor `count` independent systems together (FP64, non-pivoting): system i is the band
+ * bands[i] (device pointer, ldab[i]) of order n[i] with bandwidths kl[i], ku[i], split for
+ * p[i] workers (Sec. 3).  Every system's blocks (Sec. 2.3: the LU and the spike sweeps of each
+ * block) run in ONE launch, persistent CTAs taking the blocks of all systems from a work queue,
+ * largest first, so many small uneven systems fill the GPU together; the reduced systems
+ * (Sec. 2.2) run one merge level of every system per batched launch (levels aligned from the
+ * bottom) with one device round trip per level.  out[i] receives system i's handle, exactly
+ * the handle spike_factor_ex(bands[i], ldab[i], n[i], kl[i], ku[i], p[i], 0, opt) would return
+ * (same factors, bit for bit).  opt (may be NULL) is shared; its stream carries all the work;
+ * SPIKE_FLAG_MIXED and SPIKE_FLAG_TIMING are not supported (SPIKE_ENOTSUP), nor host bands.
+ * Blocks until done.  On failure no handle is returned. */
+int spike_factor_batch(const double *const *bands, const int64_t *ldab, const int64_t *n, const int *kl,
+                       const int *ku, const int *p, int count, const spike_options *opt, spike_handle *out);
 
 /* Device scratch bytes spike_solve_batch needs for these handles and column counts. */
 int spike_solve_batch_workspace(const spike_handle *hs, const int *nrhs, int count, char trans, int64_t *bytes);

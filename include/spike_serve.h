@@ -52,6 +52,18 @@ typedef struct spike_server_s *spike_server;
  * bytes, and a "solve" copies F to X (host memory) after sleeping the configured
  * times.  Exercises admission, eviction, batching and latency accounting. */
 #define SPIKE_SERVE_DRYRUN 1
+/* CUDA graphs per shape bucket: FP64 factorizations are made with SPIKE_FLAG_GRAPHS, and a
+ * single-matrix FP64 solve of c merged columns runs as a solve of the next power of two
+ * columns (the extra ones zero; results do not depend on them), on the worker's fixed
+ * right-hand-side and workspace buffers, so each (matrix, trans, bucket) is captured once
+ * and replayed afterwards. */
+#define SPIKE_SERVE_GRAPHS 2
+/* Tuned worker counts (with p = 0): the first factorization of each size class (floor(log2 n),
+ * k) times factor + solve of nrhs_hint columns for a few worker counts around the default
+ * rule (spike_tune, on that matrix's device band) and every later factorization of the class
+ * uses the fastest.  The tuning runs on the worker that meets the class first and allocates
+ * its own n x nrhs_hint right-hand sides outside the budget. */
+#define SPIKE_SERVE_TUNED 4
 
 typedef struct {
   int64_t budget_bytes;    /* device bytes for factorizations, their scratch and the workspaces (> 0) */
@@ -90,11 +102,12 @@ typedef struct {
   int32_t max_batch;        /* most requests merged into one solve */
   int64_t multi_solves;     /* solves that covered more than one matrix (spike_solve_batch) */
   int32_t max_systems;      /* most matrices in one solve */
-  int32_t pad;
+  int32_t tuned_classes;    /* SPIKE_SERVE_TUNED: size classes tuned so far */
   double p50_ms, p99_ms, max_ms, mean_ms;  /* latency: submit -> result in X */
   double span_s;            /* first submit -> last completion */
   double solves_per_s;      /* completed requests / span_s */
   double rhs_per_s;         /* right-hand sides / span_s */
+  int64_t graph_replays;    /* SPIKE_SERVE_GRAPHS: solves replayed from captured graphs (resident handles) */
 } spike_server_stats;
 
 /* Create a server on the current CUDA device (dry-run: no device).  Returns 0, -1 for

@@ -654,6 +654,15 @@ static void merge_phase(Phase &dst, const Phase &src) {
 // ============================================================== factor
 static int factor_reduced_level(spike_ctx *c, int lv, char *tmp, size_t tmp_bytes);
 
+// The launches of one merge level of the reduced system, for one or several systems.
+struct LevelBatch {
+  GemmBatch gA, gB, gC;
+  std::vector<LuDesc> lus;
+  TrsBatch tr;
+  int maxn = 0;
+  std::vector<std::function<int(char *)>> copies;
+};
+
 // Device memory of one factorization: the persistent block (owned by the handle) and
 // the scratch that spike_factor uses and frees before returning.  Offsets are 256-byte
 // aligned carvings of one allocation each.
@@ -760,8 +769,20 @@ struct ShardSpec {
   int64_t col0;
 };
 
+// A factorization stopped before its block LU (spike_factor_batch): the block tasks go to a
+// launch shared with other systems; the rest continues from this state.
+struct FactorCont {
+  char *fscr = nullptr;
+  LeafDev *dleaf = nullptr;
+  char *zbuf = nullptr;
+  int64_t *dzoff = nullptr;
+  char *tmp = nullptr;
+  size_t tmp_bytes = 0;
+};
+
 static int factor_impl(const double *band, int64_t ldab, int64_t n, int kl, int ku, int p, int pivot,
-                       const spike_options *opt, spike_handle *out, const ShardSpec *sh);
+                       const spike_options *opt, spike_handle *out, const ShardSpec *sh,
+                       std::vector<FactorTask> *tasks = nullptr, FactorCont *cont = nullptr);
 
 extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int kl, int ku, int p, int pivot,
                                const spike_options *opt, spike_handle *out) {
@@ -769,7 +790,8 @@ extern "C" int spike_factor_ex(const double *band, int64_t ldab, int64_t n, int 
 }
 
 static int factor_impl(const double *band, int64_t ldab, int64_t n, int kl, int ku, int p, int pivot,
-                       const spike_options *opt, spike_handle *out, const ShardSpec *sh) {
+                       const spike_options *opt, spike_handle *out, const ShardSpec *sh,
+                       std::vector<FactorTask> *tasks, FactorCont *cont) {
   if (!out) return -9;
   *out = nullptr;
   if (!band) return -1;
@@ -1003,6 +1025,32 @@ static int factor_impl(const double *band, int64_t ldab, int64_t n, int kl, int 
       if (mid) ub[i] = sdesc(c, i, UN, 0, nl, 2 * k, zt, nullptr, none, 0.0, zt);
       else if (L.bot_nbr) ub[i] = sdesc(c, i, UN, nl - k, nl, k, zb, nullptr, none, 0.0, zb);
     }
+    if (tasks) {
+      // several systems: this one's blocks join the shared launch (spike_factor_batch)
+      for (int i = 0; i < nlv; ++i) {
+        FactorTask t;
+        memset(&t, 0, sizeof(t));
+        t.leaf = c->hl[i];
+        t.k = k;
+        t.ldf = c->ldf;
+        t.fb_all = c->fbc;
+        t.dinv_all = c->dinvc;
+        t.Z = zbuf + zoff[i] * (int64_t)c->es;
+        t.amax_bits = &c->status[3];
+        t.status = c->status;
+        t.sw[0] = lbot[i];
+        t.sw[1] = ub[i];
+        tasks->push_back(t);
+      }
+      cont->fscr = fscr;
+      cont->dleaf = dleaf;
+      cont->zbuf = zbuf;
+      cont->dzoff = dzoff;
+      cont->tmp = tmp;
+      cont->tmp_bytes = tmp_bytes;
+      *out = c;
+      return 0;
+    }
     if (!pivot) {
       std::vector<SweepDesc> pairs;
       for (int i = 0; i < nlv; ++i) {
@@ -1080,6 +1128,113 @@ extern "C" int spike_factor(const double *band, int64_t n, int kl, int ku, int p
   return spike_factor_ex(band, (int64_t)kl + ku + 1, n, kl, ku, p, pivot, nullptr, out);
 }
 
+static int factor_reduced_level(spike_ctx *c, int lv, char *tmp, size_t tmp_bytes);
+static void reduced_level_build(spike_ctx *c, int lv, char *tmp, LevelBatch &LB);
+static void reduced_level_emit(LevelBatch &LB, Pipeline &pp);
+static int reduced_level_flags(const std::vector<spike_ctx *> &cs, int lv, cudaStream_t s, spike_ctx *args);
+
+extern "C" int spike_factor_batch(const double *const *bands, const int64_t *ldab, const int64_t *n, const int *kl,
+                                  const int *ku, const int *p, int count, const spike_options *opt,
+                                  spike_handle *out) {
+  if (!bands) return -1;
+  if (!ldab) return -2;
+  if (!n) return -3;
+  if (!kl) return -4;
+  if (!ku) return -5;
+  if (!p) return -6;
+  if (count < 0) return -7;
+  if (!out) return -9;
+  for (int i = 0; i < count; ++i) out[i] = nullptr;
+  if (count == 0) return 0;
+  if (opt && (opt->flags & (SPIKE_FLAG_MIXED | SPIKE_FLAG_TIMING))) return SPIKE_ENOTSUP;
+  for (int i = 0; i < count; ++i)
+    if (!bands[i] || !is_device_ptr(bands[i])) return SPIKE_ENOTSUP;
+  std::vector<spike_ctx *> cs;
+  std::vector<FactorCont> conts((size_t)count);
+  std::vector<FactorTask> tasks;
+  int maxk = 1;
+  auto fail = [&](int code) {
+    for (size_t i = 0; i < cs.size(); ++i) {
+      if (conts[i].fscr) cudaFreeAsync(conts[i].fscr, cs[i]->stream);
+      spike_free(cs[i]);
+    }
+    for (int i = 0; i < count; ++i) out[i] = nullptr;
+    return code;
+  };
+  // 1. every system's plan, memory and setup kernels, up to its block LU
+  for (int i = 0; i < count; ++i) {
+    spike_handle h = nullptr;
+    const int rc = factor_impl(bands[i], ldab[i], n[i], kl[i], ku[i], p[i], 0, opt, &h, nullptr, &tasks, &conts[i]);
+    if (rc != 0 || !h) return fail(rc != 0 ? rc : SPIKE_ECUDA);
+    cs.push_back(h);
+    maxk = std::max(maxk, h->k);
+  }
+  spike_ctx *c0 = cs[0];
+  cudaStream_t s = c0->stream;
+  // 2. all blocks of all systems in one launch, largest first, from a work queue
+  std::stable_sort(tasks.begin(), tasks.end(), [](const FactorTask &a, const FactorTask &b) {
+    return (double)a.leaf.len * a.k * a.k > (double)b.leaf.len * b.k * b.k;
+  });
+  {
+    Arena ar;
+    const size_t ot = ar.put(tasks);
+    const size_t oq = ar.put(std::vector<unsigned>(1, 0u));
+    int rc = ensure(&c0->dargs, &c0->dargs_bytes, ar.h.size(), s);
+    if (rc != 0) return fail(rc);
+    if (cudaMemcpyAsync(c0->dargs, ar.h.data(), ar.h.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return fail(SPIKE_ECUDA);
+    rc = launch_factor_tasks((const FactorTask *)(c0->dargs + ot), (int)tasks.size(), maxk,
+                             (unsigned *)(c0->dargs + oq), s);
+    if (rc != 0) {
+      g_cuda_err = std::string("factor tasks: ") + cudaGetErrorString((cudaError_t)rc);
+      return fail(SPIKE_ECUDA);
+    }
+  }
+  // 3. tips of every system
+  for (size_t i = 0; i < cs.size(); ++i) {
+    spike_ctx *c = cs[i];
+    const int rc = launch_tips0(conts[i].dleaf, c->nleaves, c->k, conts[i].zbuf, conts[i].dzoff, c->spk, s, 0);
+    if (rc != 0) return fail(SPIKE_ECUDA);
+  }
+  // 4. the reduced systems, one merge level of every system per round (levels aligned from the
+  // bottom), one flag round trip and one set of batched launches per level
+  int maxnl = 0;
+  for (auto *c : cs) maxnl = std::max(maxnl, c->NL);
+  for (int lv = 0; lv < maxnl; ++lv) {
+    std::vector<spike_ctx *> at;
+    std::vector<size_t> idx;
+    for (size_t i = 0; i < cs.size(); ++i)
+      if (lv < cs[i]->NL) {
+        at.push_back(cs[i]);
+        idx.push_back(i);
+      }
+    int rc = reduced_level_flags(at, lv, s, c0);
+    if (rc != 0) return fail(rc);
+    LevelBatch LB;
+    for (size_t j = 0; j < at.size(); ++j) reduced_level_build(at[j], lv, conts[idx[j]].tmp, LB);
+    Pipeline pp;
+    pp.st = s;
+    reduced_level_emit(LB, pp);
+    if ((rc = pp.run(c0)) != 0) return fail(rc);
+  }
+  // 5. status of every system
+  std::vector<unsigned long long> st((size_t)8 * cs.size());
+  for (size_t i = 0; i < cs.size(); ++i)
+    if (cudaMemcpyAsync(&st[8 * i], cs[i]->status, sizeof(unsigned long long) * 8, cudaMemcpyDeviceToHost, s) !=
+        cudaSuccess)
+      return fail(SPIKE_ECUDA);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return fail(SPIKE_ECUDA);
+  for (size_t i = 0; i < cs.size(); ++i) {
+    spike_ctx *c = cs[i];
+    cudaFreeAsync(conts[i].fscr, s);
+    c->boosts = (int64_t)st[8 * i];
+    c->zero_col = (st[8 * i + 1] == ULLONG_MAX) ? 0 : (int64_t)st[8 * i + 1];
+    c->nan_flag = (int)st[8 * i + 2];
+    out[i] = c;
+  }
+  return 0;
+}
+
 // One merge level of the reduced system (Sec. 2.2): for each pair of adjacent
 // groups L = [a,b), R = [b,c) factor the 2k x 2k interface
 //   M = [ I  V_{b-1,bot} ; W_{b,top}  I ]
@@ -1090,41 +1245,18 @@ extern "C" int spike_factor(const double *band, int64_t n, int kl, int ku, int p
 // When |W_{b,top}| <= 1 the pivoted LU of M keeps the identity rows for the first k
 // columns, so M = [I 0; W I][I V; 0 S] with S = I - W V: only S is LU-factored
 // (same pivot decisions as partial pivoting on M), otherwise M itself is.
-static int factor_reduced_level(spike_ctx *c, int lv, char *tmp, size_t tmp_bytes) {
-  (void)tmp_bytes;
+static void reduced_level_build(spike_ctx *c, int lv, char *tmp, LevelBatch &LB) {
   const Plan &pl = c->pl;
   const auto &ms = pl.levels[lv];
   const int nm = (int)ms.size();
   const int k = c->k;
   const int64_t kk = (int64_t)k * k;
-  cudaStream_t s = c->stream;
-  int rc;
-  // flags: one device round trip per level
-  {
-    std::vector<const double *> w(nm);
-    for (int m = 0; m < nm; ++m) w[m] = TIP(c, lv, 1, ms[m].b, 0);
-    Arena ar;
-    const size_t ow = ar.put(w);
-    const size_t of = ar.put(std::vector<int>(nm, 0));
-    SP_TRY(ensure(&c->dargs, &c->dargs_bytes, ar.h.size(), s));
-    SP_CUDA(cudaMemcpyAsync(c->dargs, ar.h.data(), ar.h.size(), cudaMemcpyHostToDevice, s));
-    if ((rc = launch_noswap_flags((const double *const *)(c->dargs + ow), k, nm, (int *)(c->dargs + of), s)) != 0) {
-      g_cuda_err = std::string("noswap: ") + cudaGetErrorString((cudaError_t)rc);
-      return SPIKE_ECUDA;
-    }
-    std::vector<int> f(nm);
-    SP_CUDA(cudaMemcpyAsync(f.data(), c->dargs + of, sizeof(int) * nm, cudaMemcpyDeviceToHost, s));
-    SP_CUDA(cudaStreamSynchronize(s));
-    c->schur[lv] = f;
-  }
   const std::vector<int> &sc = c->schur[lv];
   const bool last = (lv + 1 >= c->NL);
-  Pipeline pp;
-  pp.st = s;
-  GemmBatch gA, gB, gC;
-  std::vector<LuDesc> lus;
-  TrsBatch tr;
-  int maxn = 0;
+  GemmBatch &gA = LB.gA, &gB = LB.gB, &gC = LB.gC;
+  std::vector<LuDesc> &lus = LB.lus;
+  TrsBatch &tr = LB.tr;
+  int &maxn = LB.maxn;
   for (int m = 0; m < nm; ++m) {
     const Merge &mg = ms[m];
     // a rank forms the merges inside its leaves and, above them, the one merge containing them
@@ -1143,6 +1275,7 @@ static int factor_reduced_level(spike_ctx *c, int lv, char *tmp, size_t tmp_byte
     L.a = lu;
     L.ipiv = piv;
     L.active = 1;
+    L.status = c->status;
     if (sc[m]) {
       gA.add(gd(Wrt, k, 1, Vlb, k, 1, c->ident, k, 1, lu, k, 1, k, k, k, -1.0, 1.0));  // S = I - W V
       if (mg.hasW) gA.add(gd(Wrt, k, 1, Wlb, k, 1, nullptr, 0, 0, Tm, k, 1, k, k, k, 1.0, 0.0));
@@ -1241,22 +1374,81 @@ static int factor_reduced_level(spike_ctx *c, int lv, char *tmp, size_t tmp_byte
       }
     }
   }
-  pp.gemm(gA);
-  {
-    const size_t off = pp.ar.put(lus);
-    const int nd = (int)lus.size();
-    unsigned long long *st = c->status;
-    pp.ops.push_back([=](char *base) { return launch_getrf((LuDesc *)(base + off), nd, maxn, st, s); });
-  }
-  pp.trs(tr);
-  pp.gemm(gB);
   if (!last) {
     // untouched groups of this level keep their spikes: copy the whole level first
     double *src = TIP(c, lv, 0, 0, 0), *dst = TIP(c, lv + 1, 0, 0, 0);
     const size_t bytes = sizeof(double) * (size_t)2 * c->nleaves * 2 * kk;
-    pp.ops.push_back([=](char *) { return (int)cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s); });
-    pp.gemm(gC);
+    cudaStream_t s = c->stream;
+    LB.copies.push_back([=](char *) { return (int)cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s); });
   }
+}
+
+// Launch a level's batches (one system's or several systems'): interface LUs, the 2k solves,
+// then the level's spike copy and the merged-spike products.
+static void reduced_level_emit(LevelBatch &LB, Pipeline &pp) {
+  cudaStream_t s = pp.st;
+  pp.gemm(LB.gA);
+  if (!LB.lus.empty()) {
+    const size_t off = pp.ar.put(LB.lus);
+    const int nd = (int)LB.lus.size(), maxn = LB.maxn;
+    pp.ops.push_back([=](char *base) { return launch_getrf((LuDesc *)(base + off), nd, maxn, nullptr, s); });
+  }
+  pp.trs(LB.tr);
+  pp.gemm(LB.gB);
+  for (auto &o : LB.copies) pp.ops.push_back(o);
+  pp.gemm(LB.gC);
+}
+
+// The Schur-path flags of level lv of several systems (one flag per merge, Sec. 2.2 reading 12)
+// with one device round trip, into each system's schur[lv].
+static int reduced_level_flags(const std::vector<spike_ctx *> &cs, int lv, cudaStream_t s, spike_ctx *args) {
+  std::vector<const double *> w;
+  std::vector<int> cnt;
+  for (spike_ctx *c : cs) {
+    const auto &ms = c->pl.levels[lv];
+    for (auto &mg : ms) w.push_back(TIP(c, lv, 1, mg.b, 0));
+    cnt.push_back((int)ms.size());
+  }
+  const int nm = (int)w.size();
+  std::vector<int> f(nm, 0);
+  if (nm > 0) {
+    Arena ar;
+    const size_t ow = ar.put(w);
+    const size_t of = ar.put(f);
+    SP_TRY(ensure(&args->dargs, &args->dargs_bytes, ar.h.size(), s));
+    SP_CUDA(cudaMemcpyAsync(args->dargs, ar.h.data(), ar.h.size(), cudaMemcpyHostToDevice, s));
+    // one launch per system (each with its own k x k tips), one read-back for all of them
+    int pos = 0;
+    for (size_t i = 0; i < cs.size(); ++i) {
+      if (cnt[i] > 0) {
+        const int rc = launch_noswap_flags((const double *const *)(args->dargs + ow) + pos, cs[i]->k, cnt[i],
+                                           (int *)(args->dargs + of) + pos, s);
+        if (rc != 0) {
+          g_cuda_err = std::string("noswap: ") + cudaGetErrorString((cudaError_t)rc);
+          return SPIKE_ECUDA;
+        }
+      }
+      pos += cnt[i];
+    }
+    SP_CUDA(cudaMemcpyAsync(f.data(), args->dargs + of, sizeof(int) * nm, cudaMemcpyDeviceToHost, s));
+    SP_CUDA(cudaStreamSynchronize(s));
+  }
+  int pos = 0;
+  for (size_t i = 0; i < cs.size(); ++i) {
+    cs[i]->schur[lv].assign(f.begin() + pos, f.begin() + pos + cnt[i]);
+    pos += cnt[i];
+  }
+  return 0;
+}
+
+static int factor_reduced_level(spike_ctx *c, int lv, char *tmp, size_t tmp_bytes) {
+  (void)tmp_bytes;
+  SP_TRY(reduced_level_flags({c}, lv, c->stream, c));
+  LevelBatch LB;
+  reduced_level_build(c, lv, tmp, LB);
+  Pipeline pp;
+  pp.st = c->stream;
+  reduced_level_emit(LB, pp);
   return pp.run(c);
 }
 
@@ -1587,7 +1779,7 @@ static void build_solve_body(spike_ctx *c, Pipeline &pp, const SolveBufs &B, int
   }
 }
 
-constexpr size_t kGraphCache = 8;
+constexpr size_t kGraphCache = 16;
 
 static void drop_graph(GraphEntry &g, cudaStream_t s) {
   if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -1689,8 +1881,10 @@ static int solve_impl(spike_handle h, double *F, int64_t ldf, int nrhs, char tra
   const size_t o_r = mixed ? carve(nm8) : 0;
   const size_t o_nrm = mixed ? carve(sizeof(unsigned long long) * (1 + 2 * (size_t)m)) : 0;
   const size_t o_act = mixed ? carve(sizeof(int) * (size_t)m) : 0;
-  // tensor-core residual: the digit planes of X (for 8 or more columns; fewer take the FP64 kernel)
-  const bool split = mixed && c->sfrag[0] != nullptr && m >= 8;
+  // tensor-core residual: the digit planes of X (for 8 or more columns; fewer take the FP64 kernel,
+  // except on batch-invariant handles, whose columns must get the same bits in any solve: the
+  // tensor-core residual computes each column exactly from its own digits whatever the count)
+  const bool split = mixed && c->sfrag[0] != nullptr && (m >= 8 || c->invariant);
   const size_t xdig_bytes = split ? split_x_bytes(n, c->pl.kl, c->pl.ku, m) : 0;
   const size_t o_xd = split ? carve(xdig_bytes) : 0;
   if (need) {

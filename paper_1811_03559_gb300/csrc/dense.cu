@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(256) k_getrf(const LuDesc *descs, unsigned lon
         }
       if (!(b > 0.0)) {
         p = j;
-        atomicOr(&status[2], 2ull);  // singular interface block
+        atomicOr(D.status ? &D.status[2] : &status[2], 2ull);  // singular interface block
       }
       s_p = p;
       D.ipiv[j] = p;

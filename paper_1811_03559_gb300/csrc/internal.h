@@ -113,6 +113,7 @@ struct LuDesc {
   int n, lda;
   int active;  // 0: skip
   int pad;
+  unsigned long long *status;  // the matrix's system status words (null: the launch's)
 };
 
 // Batched solve with an LU of LuDesc: B <- alpha * op(M)^{-1} B (B row-major n x ncols).
@@ -161,6 +162,19 @@ int launch_factor_nopiv(const LeafDev *leaves, int nleaves, int k, int ldf, void
                         unsigned long long *status, const SweepDesc *sweeps, void *stream, int f32);
 int launch_factor_piv(const LeafDev *leaves, int nleaves, int k, int ldf, double *fb, double *dinv, int *ipiv,
                       unsigned long long *status, void *stream);
+// One block of one system for the multi-system factorization (FP64, no pivoting): its geometry,
+// the system's bandwidth and storage (ldf, factor and reciprocal bases, the block's Z columns),
+// the system's max|a_ij| and status words, and the two spike sweeps that follow its LU.
+struct FactorTask {
+  LeafDev leaf;
+  int k, ldf;
+  void *fb_all, *dinv_all, *Z;
+  const unsigned long long *amax_bits;
+  unsigned long long *status;
+  SweepDesc sw[2];
+};
+// Persistent CTAs over `ntasks` tasks from a zeroed counter (tasks listed largest first).
+int launch_factor_tasks(const FactorTask *tasks, int ntasks, int maxk, unsigned *queue, void *stream);
 // Runs per_cta consecutive descriptors per task (a leaf's sweep sequence), ncta tasks: one
 // CTA per task, or, with queue (a zeroed device counter), `grid` persistent CTAs taking
 // tasks in order.

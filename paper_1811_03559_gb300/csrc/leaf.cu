@@ -159,18 +159,13 @@ __device__ void sweep_run(const SweepDesc &D, int ldf, int dofs, T *sm);
 // U12 = L11^{-1} A12 (and the fused Z rows), then A22 -= L21 U12 on the k x k
 // window (and the fused Z rows below the panel).
 template <typename T>
-__global__ void __launch_bounds__(NTHREADS, 1)
-    k_factor_nopiv(const LeafDev *leaves, int k, int ldf, T *fb_all, T *dinv_all, T *zbuf,
-                   const int64_t *zoff, const unsigned long long *amax_bits, double boost_eps,
-                   unsigned long long *status, const SweepDesc *sweeps) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *smem = (T *)smem_raw;
-  const LeafDev L = leaves[blockIdx.x];
+__device__ void factor_leaf(const LeafDev &L, int k, int ldf, T *fb_all, T *dinv_all, T *Z,
+                            const unsigned long long *amax_bits, double boost_eps, unsigned long long *status,
+                            const SweepDesc &sw0, const SweepDesc &sw1, T *smem) {
   const int64_t nl = L.len;
   T *fb = fb_all + L.start * (int64_t)ldf;
   T *dinv = dinv_all + L.start;
   const bool fuse = L.top_nbr && L.bot_nbr;
-  T *Z = zbuf + zoff[blockIdx.x];
   const int kz = fuse ? k : 0;
   const int PLD = NB + k + 1;
   const int TLD = CW + 1;
@@ -333,9 +328,50 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (tid == 0 && nboost) atomicAdd(&status[0], nboost);
   // the leaf's spike sweeps, in the same CTA (shared memory reused)
   __syncthreads();
-  sweep_run<T>(sweeps[2 * blockIdx.x], ldf, k, smem);
+  sweep_run<T>(sw0, ldf, k, smem);
   __syncthreads();
-  sweep_run<T>(sweeps[2 * blockIdx.x + 1], ldf, k, smem);
+  sweep_run<T>(sw1, ldf, k, smem);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_factor_nopiv(const LeafDev *leaves, int k, int ldf, T *fb_all, T *dinv_all, T *zbuf,
+                   const int64_t *zoff, const unsigned long long *amax_bits, double boost_eps,
+                   unsigned long long *status, const SweepDesc *sweeps) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  factor_leaf<T>(leaves[blockIdx.x], k, ldf, fb_all, dinv_all, zbuf + zoff[blockIdx.x], amax_bits, boost_eps,
+                 status, sweeps[2 * blockIdx.x], sweeps[2 * blockIdx.x + 1], (T *)smem_raw);
+}
+
+// Blocks of several systems in one launch (spike_factor_batch): persistent CTAs take the tasks
+// from a zeroed counter in index order (the host lists them largest first); each task is one
+// block with its own system's bandwidth, storage and status words.
+__global__ void __launch_bounds__(NTHREADS, 1) k_factor_tasks(const FactorTask *tasks, int ntasks, unsigned *queue,
+                                                              double boost_eps) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_task;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_task = (int)atomicAdd(queue, 1u);
+    __syncthreads();
+    const int t = s_task;
+    if (t >= ntasks) break;
+    const FactorTask &T = tasks[t];
+    factor_leaf<double>(T.leaf, T.k, T.ldf, (double *)T.fb_all, (double *)T.dinv_all, (double *)T.Z, T.amax_bits,
+                        boost_eps, T.status, T.sw[0], T.sw[1], (double *)smem_raw);
+  }
+}
+
+int launch_factor_tasks(const FactorTask *tasks, int ntasks, int maxk, unsigned *queue, void *stream) {
+  if (ntasks <= 0) return 0;
+  size_t smem = sizeof(double) * ((size_t)NB * (NB + maxk + 1) + (size_t)NB * (CW + 1));
+  if (smem < SWEEP_SMEM) smem = SWEEP_SMEM;
+  const int e = smem_at_least((const void *)k_factor_tasks, smem);
+  if (e) return e;
+  const int grid = std::min(ntasks, device_sms());
+  k_factor_tasks<<<grid, NTHREADS, smem, (cudaStream_t)stream>>>(tasks, ntasks, queue, 1.4901161193847656e-08);
+  count_launch();
+  return (int)cudaGetLastError();
 }
 
 int launch_factor_nopiv(const LeafDev *leaves, int nleaves, int k, int ldf, void *fb, void *dinv, void *zbuf,
@@ -440,9 +476,147 @@ __global__ void __launch_bounds__(NTHREADS)
   }
 }
 
+// The same GEPP with the active window in shared memory.  At column j the window holds rows
+// j..j+k (the pivot candidates) and columns j..j+2k (the U fill, Sec. 5.1), plus one spare
+// row and one spare column: row j+k+1 and column j+2k+1 enter while step j updates, so a
+// column costs two CTA barriers.  Columns live in circular slots (c mod (2k+2)); rows are
+// reached through a slot map (row r -> map[r mod (k+2)]), so a row interchange swaps two
+// map entries instead of moving data.  Step j:
+//   A (warp 0): pivot = first row of largest |a_rj| among rows j..j+k; swap the map
+//     entries of rows j and p; 1 / pivot (0 for an all-zero column, whose step then changes
+//     nothing, as in the global-memory kernel).
+//   B (all): a_rc -= a_rj (u_c / pivot) for r in (j, j+k], c in (j, j+2k] (lanes over
+//     columns, warps over rows); write row j of U and the multipliers a_rj / pivot of
+//     column j to the leaf's band storage; load row j+k+1 and clear column j+2k+1.
+// Same storage, pivots and reciprocals as k_factor_piv (multipliers unpermuted, interleaved).
+constexpr int PIV_SMEM_MAX = 200 * 1024;
+
+__global__ void __launch_bounds__(NTHREADS)
+    k_factor_piv_smem(const LeafDev *leaves, int k, int ldf, double *fb_all, double *dinv_all, int *ipiv_all,
+                      unsigned long long *status) {
+  extern __shared__ __align__(16) unsigned char piv_raw[];
+  const int CS = 2 * k + 2, M = k + 2;
+  double *Wn = (double *)piv_raw;      // M row slots x CS column slots
+  int *map = (int *)(Wn + (size_t)M * CS);
+  __shared__ double s_rinv;
+  const LeafDev L = leaves[blockIdx.x];
+  const int nl = (int)L.len;
+  double *fb = fb_all + L.start * (int64_t)ldf;
+  double *dinv = dinv_all + L.start;
+  int *ipiv = ipiv_all + L.start;
+  const int dofs = 2 * k;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (nl <= 0) return;
+  // rows and columns by offset from j: row j + d sits in row slot map[(jm + d) mod M], column
+  // j + e in column slot (jc + e) mod CS; 0 <= d <= k + 1 and 0 <= e <= 2k + 1, so one wrap
+  auto wrapM = [&](int x) { return x >= M ? x - M : x; };
+  auto wrapC = [&](int x) { return x >= CS ? x - CS : x; };
+  // band entry (r, c) of the leaf before elimination (zero outside the band)
+  auto orig = [&](int r, int c) -> double {
+    if (r < 0 || r >= nl || c < 0 || c >= nl || r - c > k || c - r > 2 * k) return 0.0;
+    return fb[(int64_t)c * ldf + dofs + r - c];
+  };
+  for (int i = tid; i < M; i += NTHREADS) map[i] = i;
+  // rows 0..k (slots 0..k), columns 0..2k+1
+  for (int idx = tid; idx < (k + 1) * CS; idx += NTHREADS) {
+    const int r = idx / CS, c = idx - r * CS;
+    Wn[(size_t)r * CS + c] = (c <= 2 * k) ? orig(r, c) : 0.0;
+  }
+  __syncthreads();
+  int jm = 0, jc = 0;
+  // the entering row j + k + 1 is read one step ahead (thread tid holds column j + 1 + tid)
+  double nxt = (tid <= 2 * k) ? orig(k + 1, 1 + tid) : 0.0;
+  for (int j = 0; j < nl; ++j) {
+    const int dl = min(k, nl - 1 - j);      // rows j .. j + dl are candidates
+    const int ec = min(2 * k, nl - 1 - j);  // columns j .. j + ec hold U fill
+    // A: pivot search on column j
+    if (warp == 0) {
+      double best = -1.0;
+      int bd = 0;
+      for (int d = lane; d <= dl; d += 32) {
+        const double v = fabs(Wn[(size_t)map[wrapM(jm + d)] * CS + jc]);
+        if (v > best) {
+          best = v;
+          bd = d;
+        }
+      }
+      for (int o = 16; o; o >>= 1) {
+        const double ov = __shfl_down_sync(FULLMASK, best, o);
+        const int od = __shfl_down_sync(FULLMASK, bd, o);
+        if (ov > best || (ov == best && od < bd)) {
+          best = ov;
+          bd = od;
+        }
+      }
+      if (lane == 0) {
+        ipiv[j] = j + bd;
+        const bool zero = !(best > 0.0);
+        if (zero) {
+          const int64_t gcol = L.rev ? (L.start + nl - 1 - j) : (L.start + j);
+          atomicMin(&status[1], (unsigned long long)(gcol + 1));
+          if (isnan(best)) atomicOr(&status[2], 1ull);
+        }
+        if (bd != 0) {
+          const int b = wrapM(jm + bd);
+          const int t = map[jm];
+          map[jm] = map[b];
+          map[b] = t;
+        }
+        const double piv = Wn[(size_t)map[jm] * CS + jc];
+        const double ri = zero ? 0.0 : 1.0 / piv;
+        s_rinv = ri;
+        dinv[j] = ri;
+      }
+    }
+    __syncthreads();
+    // B: trailing update, write-out of row j of U and column j of L, next row and column in
+    const double rinv = s_rinv;
+    const double *Wj = Wn + (size_t)map[jm] * CS;
+    {
+      double v[8];
+      int cs[8];
+      int nq = 0;
+      for (int e = 1 + lane; e <= ec && nq < 8; e += 32) {
+        cs[nq] = wrapC(jc + e);
+        v[nq] = Wj[cs[nq]] * rinv;
+        ++nq;
+      }
+      for (int d = 1 + warp; d <= dl; d += NTHREADS / 32) {
+        double *Wr = Wn + (size_t)map[wrapM(jm + d)] * CS;
+        const double a = Wr[jc];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (q < nq) Wr[cs[q]] = fma(-a, v[q], Wr[cs[q]]);
+      }
+    }
+    for (int e = tid; e <= ec; e += NTHREADS) fb[(int64_t)(j + e) * ldf + dofs - e] = Wj[wrapC(jc + e)];
+    for (int d = 1 + tid; d <= dl; d += NTHREADS)
+      fb[(int64_t)j * ldf + dofs + d] = Wn[(size_t)map[wrapM(jm + d)] * CS + jc] * rinv;
+    {
+      const int cn = wrapC(jc + 2 * k + 1);
+      if (j + k + 1 < nl) {
+        double *Wn_new = Wn + (size_t)map[wrapM(jm + k + 1)] * CS;  // the slot row j-1 left
+        if (tid <= 2 * k) Wn_new[wrapC(jc + 1 + tid)] = nxt;
+      }
+      nxt = (tid <= 2 * k) ? orig(j + k + 2, j + 2 + tid) : 0.0;
+      for (int d = 1 + tid; d <= k; d += NTHREADS) Wn[(size_t)map[wrapM(jm + d)] * CS + cn] = 0.0;
+    }
+    jm = wrapM(jm + 1);
+    jc = wrapC(jc + 1);
+    __syncthreads();
+  }
+}
+
 int launch_factor_piv(const LeafDev *leaves, int nleaves, int k, int ldf, double *fb, double *dinv, int *ipiv,
                       unsigned long long *status, void *stream) {
-  k_factor_piv<<<nleaves, NTHREADS, 0, (cudaStream_t)stream>>>(leaves, k, ldf, fb, dinv, ipiv, status);
+  const size_t smem = sizeof(double) * (size_t)(k + 2) * (2 * k + 2) + sizeof(int) * (size_t)(k + 2);
+  if (smem <= PIV_SMEM_MAX && k <= 127) {  // 8 columns per lane cover the 2k fill columns; a thread per entering entry
+    const int e = smem_at_least((const void *)k_factor_piv_smem, smem);
+    if (e) return e;
+    k_factor_piv_smem<<<nleaves, NTHREADS, smem, (cudaStream_t)stream>>>(leaves, k, ldf, fb, dinv, ipiv, status);
+  } else {
+    k_factor_piv<<<nleaves, NTHREADS, 0, (cudaStream_t)stream>>>(leaves, k, ldf, fb, dinv, ipiv, status);
+  }
   count_launch();
   return (int)cudaGetLastError();
 }
@@ -843,59 +1017,167 @@ int launch_sweeps(const SweepDesc *descs, int ncta, int per_cta, int ldf, int do
 }
 
 // ------------------------------------------------ pivoted L sweeps (Sec. 5.1)
-// In place on X, rows [r0, r1) with r1 = nl.  One warp per RHS column, lanes over rows.
+// In place on X, rows [r0, r1) with r1 = nl.  One warp per RHS column.
 //   LN (forward):  for j: swap X_j <-> X_ipiv[j]; X_{j+1..j+k} -= l_{.,j} X_j
 //   LT (backward): for j descending: X_j -= sum_i l_{i,j} X_i; swap X_j <-> X_ipiv[j]
+// The rows a step touches (j..j+k; ipiv[j] <= j+k) live in a per-warp circular window in
+// shared memory (row i at slot i mod (k+1)); rows enter and leave it once, through registers
+// that hold the next 32 rows to load and the last 32 finished rows (one per lane), so the
+// dependent chain of a step stays in shared memory and shuffles.
+constexpr int LPRE = 4;  // multipliers a lane prefetches per step (k <= 128; wider bands read the rest directly)
+
 template <int KIND>
 __global__ void __launch_bounds__(NTHREADS) k_piv_sweep(const SweepDesc *descs, int k, int ldf, int dofs) {
+  extern __shared__ double pwin[];
   const SweepDesc D = descs[blockIdx.x];
   if (D.ncols <= 0 || D.r1 <= D.r0) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int WIN = k + 1;
+  double *buf = pwin + (size_t)warp * (k + 2);
+  // row j + d (0 <= d <= k) sits in slot (jw + d) mod WIN, jw = j mod WIN kept incrementally
+  auto wrap = [&](int x) { return x >= WIN ? x - WIN : x; };
+  const int r0 = (int)D.r0, r1 = (int)D.r1;
+  const int64_t rs = D.x_rs;
   for (int col = warp; col < D.ncols; col += NTHREADS / 32) {
     double *x = D.x + (int64_t)col * D.x_cs;
-    const int64_t rs = D.x_rs;
     if (KIND == LN) {
-      for (int64_t j = D.r0; j < D.r1; ++j) {
-        const int64_t p = D.ipiv[j];
-        if (lane == 0 && p != j) {
-          const double t = x[j * rs];
-          x[j * rs] = x[p * rs];
-          x[p * rs] = t;
+      int jw = r0 % WIN;
+      const int top = min(r0 + k, r1 - 1);
+      for (int d = lane; d <= top - r0; d += 32) buf[wrap(jw + d)] = x[(int64_t)(r0 + d) * rs];
+      int pbase = r0 + k + 1;  // rows pbase .. pbase+31 are held in `pre` (lane l: row pbase + l)
+      double pre = (pbase + lane < r1) ? x[(int64_t)(pbase + lane) * rs] : 0.0;
+      int obase = r0;  // finished rows obase .. held in `outv` (lane l: row obase + l)
+      double outv = 0.0;
+      double lc[LPRE];  // multipliers of the current step (lane l: rows j + 1 + l + 32 t)
+      {
+        const double *l0 = D.fb + (int64_t)r0 * ldf + dofs;
+        const int d0 = min(k, r1 - 1 - r0);
+#pragma unroll
+        for (int t = 0; t < LPRE; ++t) lc[t] = (1 + lane + 32 * t <= d0) ? l0[1 + lane + 32 * t] : 0.0;
+      }
+      __syncwarp();
+      for (int j = r0; j < r1; ++j) {
+        const int pd = D.ipiv[j] - j;
+        if (lane == 0 && pd != 0) {
+          const int b = wrap(jw + pd);
+          const double t = buf[jw];
+          buf[jw] = buf[b];
+          buf[b] = t;
         }
         __syncwarp();
-        const double xj = x[j * rs];
-        const int64_t last = min(j + (int64_t)k, (int64_t)D.r1 - 1);
-        for (int64_t i = j + 1 + lane; i <= last; i += 32) x[i * rs] = fma(-D.fb[j * ldf + dofs + i - j], xj, x[i * rs]);
+        const double xj = buf[jw];
+        const int dl = min(k, r1 - 1 - j);
+#pragma unroll
+        for (int t = 0; t < LPRE; ++t) {
+          const int d = 1 + lane + 32 * t;
+          if (d <= dl) {
+            const int sl = wrap(jw + d);
+            buf[sl] = fma(-lc[t], xj, buf[sl]);
+          }
+        }
+        for (int d = 1 + lane + 32 * LPRE; d <= dl; d += 32) {  // k > 32 LPRE
+          const int sl = wrap(jw + d);
+          buf[sl] = fma(-D.fb[(int64_t)j * ldf + dofs + d], xj, buf[sl]);
+        }
+        // the next step's multipliers (column j + 1 of L), read while this step finishes
+        if (j + 1 < r1) {
+          const double *ln = D.fb + (int64_t)(j + 1) * ldf + dofs;
+          const int dn = min(k, r1 - 2 - j);
+#pragma unroll
+          for (int t = 0; t < LPRE; ++t) lc[t] = (1 + lane + 32 * t <= dn) ? ln[1 + lane + 32 * t] : 0.0;
+        }
+        if (lane == j - obase) outv = xj;
+        if (j - obase == 31 || j == r1 - 1) {
+          if (obase + lane <= j) x[(int64_t)(obase + lane) * rs] = outv;
+          obase = j + 1;
+        }
         __syncwarp();
+        const int rn = j + k + 1;  // enters the slot row j leaves: (jw + k + 1) mod WIN = jw
+        if (rn < r1) {
+          const double v = __shfl_sync(FULLMASK, pre, rn - pbase);
+          if (lane == 0) buf[jw] = v;
+          if (rn - pbase == 31) {
+            pbase += 32;
+            pre = (pbase + lane < r1) ? x[(int64_t)(pbase + lane) * rs] : 0.0;
+          }
+        }
+        jw = wrap(jw + 1);
       }
     } else {
-      for (int64_t j = D.r1 - 1; j >= D.r0; --j) {
-        const int64_t last = min(j + (int64_t)k, (int64_t)D.r1 - 1);
-        double s = 0.0;
-        for (int64_t i = j + 1 + lane; i <= last; i += 32) s = fma(D.fb[j * ldf + dofs + i - j], x[i * rs], s);
-        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(FULLMASK, s, o);
+      int jw = (r1 - 1) % WIN;
+      int pbase = r1 - 1;  // rows pbase, pbase-1, ... held in `pre` (lane l: row pbase - l)
+      double pre = (pbase - lane >= r0) ? x[(int64_t)(pbase - lane) * rs] : 0.0;
+      int obase = r1 - 1;  // finished rows obase, obase-1, ... held in `outv`
+      double outv = 0.0;
+      double lc[LPRE];  // multipliers of the current step (the last row has none)
+#pragma unroll
+      for (int t = 0; t < LPRE; ++t) lc[t] = 0.0;
+      for (int j = r1 - 1; j >= r0; --j) {
+        const double xj = __shfl_sync(FULLMASK, pre, pbase - j);
+        if (pbase - j == 31) {
+          pbase -= 32;
+          pre = (pbase - lane >= r0) ? x[(int64_t)(pbase - lane) * rs] : 0.0;
+        }
+        const int dl = min(k, r1 - 1 - j);
+        double sacc = 0.0;
+#pragma unroll
+        for (int t = 0; t < LPRE; ++t) {
+          const int d = 1 + lane + 32 * t;
+          if (d <= dl) sacc = fma(lc[t], buf[wrap(jw + d)], sacc);
+        }
+        for (int d = 1 + lane + 32 * LPRE; d <= dl; d += 32)
+          sacc = fma(D.fb[(int64_t)j * ldf + dofs + d], buf[wrap(jw + d)], sacc);
+        // the next step's multipliers (column j - 1 of L)
+        if (j - 1 >= r0) {
+          const double *ln = D.fb + (int64_t)(j - 1) * ldf + dofs;
+          const int dn = min(k, r1 - j);
+#pragma unroll
+          for (int t = 0; t < LPRE; ++t) lc[t] = (1 + lane + 32 * t <= dn) ? ln[1 + lane + 32 * t] : 0.0;
+        }
+        for (int o = 16; o; o >>= 1) sacc += __shfl_xor_sync(FULLMASK, sacc, o);
+        const double v = xj - sacc;
+        const int pd = D.ipiv[j] - j;
         if (lane == 0) {
-          const double v = x[j * rs] - s;
-          const int64_t p = D.ipiv[j];
-          if (p != j) {
-            x[j * rs] = x[p * rs];
-            x[p * rs] = v;
+          if (pd != 0) {
+            const int b = wrap(jw + pd);
+            buf[jw] = buf[b];
+            buf[b] = v;
           } else {
-            x[j * rs] = v;
+            buf[jw] = v;
           }
         }
         __syncwarp();
+        // row j + k is final now (later steps swap only rows below j + k); its slot is reused
+        // by row j - 1
+        const int rl = j + k;
+        if (rl <= r1 - 1) {
+          const double fv = buf[wrap(jw + k)];
+          if (lane == obase - rl) outv = fv;
+          if (obase - rl == 31) {
+            if (obase - lane >= rl) x[(int64_t)(obase - lane) * rs] = outv;
+            obase = rl - 1;
+          }
+        }
+        __syncwarp();
+        jw = (jw == 0) ? WIN - 1 : jw - 1;
       }
+      // the rows still held: pending `outv` (obase down to r0 + k) and the window r0 .. r0+k-1
+      const int wtop = min(r0 + k - 1, r1 - 1);
+      if (obase > wtop && obase - lane > wtop && obase - lane >= r0) x[(int64_t)(obase - lane) * rs] = outv;
+      const int w0 = r0 % WIN;
+      for (int d = lane; d <= wtop - r0; d += 32) x[(int64_t)(r0 + d) * rs] = buf[wrap(w0 + d)];
     }
+    __syncwarp();
   }
 }
 
 int launch_piv_sweep(int kind, const SweepDesc *descs, int ndesc, int k, int ldf, int dofs, void *stream) {
   if (ndesc <= 0) return 0;
+  const size_t smem = sizeof(double) * (size_t)(NTHREADS / 32) * (k + 2);
   if (kind == LN)
-    k_piv_sweep<LN><<<ndesc, NTHREADS, 0, (cudaStream_t)stream>>>(descs, k, ldf, dofs);
+    k_piv_sweep<LN><<<ndesc, NTHREADS, smem, (cudaStream_t)stream>>>(descs, k, ldf, dofs);
   else
-    k_piv_sweep<LT><<<ndesc, NTHREADS, 0, (cudaStream_t)stream>>>(descs, k, ldf, dofs);
+    k_piv_sweep<LT><<<ndesc, NTHREADS, smem, (cudaStream_t)stream>>>(descs, k, ldf, dofs);
   count_launch();
   return (int)cudaGetLastError();
 }

@@ -197,7 +197,7 @@ __device__ __forceinline__ void digits_to_bf16(uint32_t w, uint32_t &lo, uint32_
 
 __device__ __forceinline__ void mma_bf16(float *c, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
                                          uint32_t b1) {
-  asm volatile(
+  asm(
       "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
       : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
@@ -234,6 +234,18 @@ __global__ void __launch_bounds__(SPL_WARPS * 32, 1)
   const int XW = (MBS - 1) * 16 + KP + 16;  // staged rows (multiple of 16)
   const bool active = mb < nmb;
   const uint4 *fr = frag + (mb * SPL_PLANES) * (int64_t)nchunks * 32 + lane;
+  // the warp's A fragments of the next chunk are copied to shared memory while the current
+  // chunk computes (each lane copies and later reads back its own 16 bytes per plane)
+  uint4 *abuf = (uint4 *)(xs + (size_t)SPL_PLANES * SPL_MC * XWP) + (size_t)warp * SPL_PLANES * 32 + lane;
+  auto prefetch = [&](int ch) {
+#pragma unroll
+    for (int p = 0; p < SPL_PLANES; ++p) {
+      const unsigned d = (unsigned)__cvta_generic_to_shared(abuf + p * 32);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(fr + ((int64_t)p * nchunks + ch) * 32)
+                   : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
   for (int c0 = 0; c0 < nrhs; c0 += SPL_MC) {
     __syncthreads();  // the previous pass's reads of xs are done
     {
@@ -278,18 +290,22 @@ __global__ void __launch_bounds__(SPL_WARPS * 32, 1)
         }
     };
     const uint8_t *xcol = xs + (int64_t)(16 * wcol + g) * XWP + woff + 4 * t;
+    prefetch(0);
     for (int ch = 0; ch < nchunks; ++ch) {
       // A digits of the chunk, all planes: [plane][k-half][4 regs]
       uint32_t a[SPL_PLANES][2][4];
+      asm volatile("cp.async.wait_all;\n" ::: "memory");
 #pragma unroll
       for (int p = 0; p < SPL_PLANES; ++p) {
-        const uint4 w = fr[((int64_t)p * nchunks + ch) * 32];
+        const uint4 w = abuf[p * 32];
         // k-half 0: rows g (w.x) and g+8 (w.y), columns 4t..4t+3; k-half 1: w.z, w.w
         digits_to_bf16(w.x, a[p][0][0], a[p][0][2]);
         digits_to_bf16(w.y, a[p][0][1], a[p][0][3]);
         digits_to_bf16(w.z, a[p][1][0], a[p][1][2]);
         digits_to_bf16(w.w, a[p][1][1], a[p][1][3]);
       }
+      // the converted fragments are in registers: the buffer takes the next chunk
+      if (ch + 1 < nchunks) prefetch(ch + 1);
 #pragma unroll
       for (int q = 0; q < SPL_PLANES; ++q) {
         uint32_t b[SPL_NT][2][2];
@@ -360,11 +376,12 @@ static size_t split_smem(int kl, int ku, int *xwp) {
   int XWP = XW;
   while (XWP % 128 != 16) XWP += 16;  // column stride = 16 mod 128 bytes: conflict-free B fragments
   if (xwp) *xwp = XWP;
-  return (size_t)SPL_PLANES * SPL_MC * XWP;
+  // X digit planes, then one chunk of A fragments per warp (8 planes x 32 lanes x 16 bytes)
+  return (size_t)SPL_PLANES * SPL_MC * XWP + (size_t)SPL_WARPS * SPL_PLANES * 32 * 16;
 }
 
-// The staged X digits must fit a CTA's shared memory (bandwidths up to about 330).
-bool split_supported(int kl, int ku) { return split_smem(kl, ku, nullptr) <= 200 * 1024; }
+// The staged X digits and A fragments must fit a CTA's shared memory (kl + ku up to about 540).
+bool split_supported(int kl, int ku) { return split_smem(kl, ku, nullptr) <= 227 * 1024; }
 
 int64_t split_ldx(int64_t n, int kl, int ku) { return ((n + 2 * (int64_t)split_xpad(kl, ku)) + 15) & ~(int64_t)15; }
 

@@ -15,7 +15,9 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <mutex>
+#include <set>
 #include <string>
 #include <thread>
 #include <unordered_map>
@@ -102,6 +104,10 @@ struct spike_server_s {
   int max_batch = 0, max_systems = 0;
   double t_first = -1.0, t_last = 0.0;
   std::vector<double> lat;
+  // SPIKE_SERVE_TUNED: fastest worker count per size class (floor(log2 n), k); classes being tuned
+  std::map<std::pair<int, int>, int> tuned;
+  std::set<std::pair<int, int>> tuning;
+  int64_t greplays = 0;  // SPIKE_SERVE_GRAPHS: solves replayed from graphs
   std::string last_error;  // CUDA error text of the last failed request (worker threads' own)
 };
 
@@ -291,7 +297,21 @@ void worker(spike_server_s *S, int w) {
       o.K = S->cfg.K;
       o.nrhs_hint = S->cfg.nrhs_hint > 0 ? S->cfg.nrhs_hint : 16;
       o.flags = SPIKE_FLAG_STAGE_BALANCE | SPIKE_FLAG_BATCH_INVARIANT | (prec ? SPIKE_FLAG_MIXED : 0) |
-                (M.host ? 0 : SPIKE_FLAG_BORROW_BAND);
+                (M.host ? 0 : SPIKE_FLAG_BORROW_BAND) |
+                ((S->cfg.flags & SPIKE_SERVE_GRAPHS) && !prec ? SPIKE_FLAG_GRAPHS : 0);
+      // SPIKE_SERVE_TUNED: the size class's measured worker count, or tune it now
+      bool tune_now = false;
+      std::pair<int, int> cls(0, std::max(M.kl, M.ku));
+      if ((S->cfg.flags & SPIKE_SERVE_TUNED) && S->cfg.p == 0 && !M.host && !S->dry && !M.pivot) {
+        while ((2LL << cls.first) <= M.n) ++cls.first;
+        auto it = S->tuned.find(cls);
+        if (it != S->tuned.end()) {
+          M.p = it->second;
+        } else if (!S->tuning.count(cls)) {
+          S->tuning.insert(cls);
+          tune_now = true;
+        }
+      }
       o.stream = st;
       int64_t res = 0, tr = 0;
       rc = spike_factor_bytes(M.n, M.kl, M.ku, M.p, M.pivot, &o, M.host ? 1 : 0, &res, &tr);
@@ -305,6 +325,24 @@ void worker(spike_server_s *S, int w) {
         lk.unlock();
         spike_handle h = nullptr;
         int64_t actual = res + slack;
+        if (tune_now) {
+          // a few worker counts around the rule, factor + one solve of nrhs_hint columns each
+          const int64_t kk = std::max(1, std::max(M.kl, M.ku));
+          const int pmax = (int)std::max<int64_t>(1, M.n / (4 * kk));
+          std::vector<int> cand;
+          for (int c : {std::max(1, M.p / 2), M.p, 2 * M.p, 4 * M.p})
+            if (c <= pmax && std::find(cand.begin(), cand.end(), c) == cand.end()) cand.push_back(c);
+          spike_tune_result tr_;
+          const int trc = spike_tune(M.band, M.ldab, M.n, M.kl, M.ku, o.nrhs_hint, 1, cand.data(), (int)cand.size(),
+                                     nullptr, 0, st, nullptr, &tr_);
+          lk.lock();
+          if (trc == 0) {
+            S->tuned[cls] = tr_.best_p;
+            M.p = tr_.best_p;
+          }
+          S->tuning.erase(cls);
+          lk.unlock();
+        }
         const double t_fac = now_s();
         if (S->dry) {
           sleep_us(S->cfg.dryrun_factor_us);
@@ -343,6 +381,12 @@ void worker(spike_server_s *S, int w) {
     if (rc == 0 && prec == 0 && !M.pivot && S->batch_systems > 1)
       pick_more(S, trans, r0.mid, S->batch_systems - 1, groups);
     const bool multi = groups.size() > 1;
+    // SPIKE_SERVE_GRAPHS: a single-matrix FP64 solve runs as the next power of two of columns
+    const bool graphs = (S->cfg.flags & SPIKE_SERVE_GRAPHS) && !multi && prec == 0 && !S->dry;
+    int scols = cols;
+    if (graphs)
+      while (scols & (scols - 1)) scols += scols & -scols;  // round up to a power of two
+    if (graphs) groups[0].cols = scols;
 
     // 3. buffers: merged right-hand sides and solve workspace of this worker
     std::vector<int64_t> fb_off(groups.size(), 0);
@@ -364,7 +408,7 @@ void worker(spike_server_s *S, int w) {
       } else if (multi) {
         rc = spike_solve_batch_workspace(hs.data(), gcols.data(), (int)hs.size(), trans, &ws_need);
       } else {
-        rc = spike_solve_workspace(F.h, cols, trans, 0, &ws_need);
+        rc = spike_solve_workspace(F.h, scols, trans, 0, &ws_need);
       }
       if (rc == 0) rc = grow(S, lk, &B.ws, &B.ws_bytes, ws_need, st);
       if (rc == 0) rc = grow(S, lk, (char **)&B.fb, &B.fb_bytes, fb_need, st);
@@ -394,11 +438,27 @@ void worker(spike_server_s *S, int w) {
             off += r->nrhs;
           }
         }
+        if (!rc && scols > cols &&
+            cudaMemsetAsync(fptr[0] + (int64_t)cols * M.n, 0, sizeof(double) * M.n * (scols - cols), st) != cudaSuccess)
+          rc = SPIKE_ECUDA;
+        int64_t replays0 = 0;
+        if (graphs && F.h) {
+          spike_info gi;
+          if (spike_get_info(F.h, &gi) == 0) replays0 = gi.graph_replays;
+        }
         if (!rc && multi) {
           rc = spike_solve_batch(hs.data(), fptr.data(), gcols.data(), (int)hs.size(), trans, st, B.ws, B.ws_bytes);
         } else if (!rc) {
           rc = spike_set_stream(F.h, st);
-          if (!rc) rc = spike_solve_ws(F.h, fptr[0], M.n, cols, trans, B.ws, B.ws_bytes);
+          if (!rc) rc = spike_solve_ws(F.h, fptr[0], M.n, scols, trans, B.ws, B.ws_bytes);
+        }
+        if (graphs && F.h && !rc) {
+          spike_info gi;
+          if (spike_get_info(F.h, &gi) == 0) {
+            lk.lock();
+            S->greplays += gi.graph_replays - replays0;
+            lk.unlock();
+          }
         }
         for (size_t g = 0; g < groups.size(); ++g) {
           const int64_t n = groups[g].M->n;
@@ -615,6 +675,8 @@ extern "C" int spike_server_stats_get(spike_server S, spike_server_stats *o) {
   o->max_batch = S->max_batch;
   o->multi_solves = S->multi;
   o->max_systems = S->max_systems;
+  o->tuned_classes = (int32_t)S->tuned.size();
+  o->graph_replays = S->greplays;
   if (!S->lat.empty()) {
     std::vector<double> v = S->lat;
     std::sort(v.begin(), v.end());

@@ -13,6 +13,8 @@ import numpy as np
 from . import spike
 
 DRYRUN = 1
+GRAPHS = 2
+TUNED = 4
 EVICT_LRU, EVICT_COST = 0, 1
 
 
@@ -30,12 +32,13 @@ class ServerStats(ctypes.Structure):
                 ("evictions", ctypes.c_int64), ("admission_waits", ctypes.c_int64),
                 ("used_bytes", ctypes.c_int64), ("peak_bytes", ctypes.c_int64), ("resident", ctypes.c_int32),
                 ("max_batch", ctypes.c_int32), ("multi_solves", ctypes.c_int64), ("max_systems", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("tuned_classes", ctypes.c_int32), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
                 ("max_ms", ctypes.c_double), ("mean_ms", ctypes.c_double), ("span_s", ctypes.c_double),
-                ("solves_per_s", ctypes.c_double), ("rhs_per_s", ctypes.c_double)]
+                ("solves_per_s", ctypes.c_double), ("rhs_per_s", ctypes.c_double),
+                ("graph_replays", ctypes.c_int64)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 _bound = False
@@ -76,10 +79,11 @@ class Server:
     recently used first) or "cost" (greedy-dual size-frequency, spike_serve.h)."""
 
     def __init__(self, budget_bytes, streams=4, max_batch_rhs=64, p=0, nrhs_hint=0, K=0.0, dryrun=False,
-                 dryrun_factor_us=0, dryrun_solve_us=0, batch_systems=0, evict="lru"):
+                 dryrun_factor_us=0, dryrun_solve_us=0, batch_systems=0, evict="lru", graphs=False, tuned=False):
         self._keep = {}
         cfg = ServerConfig(budget_bytes=int(budget_bytes), streams=streams, max_batch_rhs=max_batch_rhs, p=p,
-                           nrhs_hint=nrhs_hint, K=K, flags=DRYRUN if dryrun else 0,
+                           nrhs_hint=nrhs_hint, K=K,
+                           flags=(DRYRUN if dryrun else 0) | (GRAPHS if graphs else 0) | (TUNED if tuned else 0),
                            dryrun_factor_us=dryrun_factor_us, dryrun_solve_us=dryrun_solve_us,
                            batch_systems=batch_systems, evict_policy={"lru": EVICT_LRU, "cost": EVICT_COST}[evict])
         h = ctypes.c_void_p()

@@ -56,7 +56,7 @@ EXPORTS = ["spike_plan", "spike_factor", "spike_factor_ex", "spike_solve", "spik
            "spike_free", "spike_strerror", "spike_last_cuda_error", "spike_backward_error_noalloc",
            "spike_measure_fp64_peak", "spike_factor_bytes", "spike_solve_workspace", "spike_solve_ws",
            "spike_measure_K", "spike_tune", "spike_solve_batch", "spike_solve_batch_workspace",
-           "spike_release_cached", "spike_residual"]
+           "spike_release_cached", "spike_residual", "spike_factor_batch"]
 SPIKE_ELIMIT = -1006
 NOALLOC_MAX_NRHS = 1024
 
@@ -112,6 +112,7 @@ def lib():
         L.spike_solve_batch.argtypes = [vp, vp, vp, i32, ctypes.c_char, vp, vp, i64]
         L.spike_release_cached.argtypes = [ctypes.POINTER(i64), ctypes.POINTER(i64)]
         L.spike_residual.argtypes = [vp, dp, dp, dp, i32, ctypes.c_char, dp]
+        L.spike_factor_batch.argtypes = [vp, vp, vp, vp, vp, vp, i32, ctypes.POINTER(SpikeOptions), vp]
         L.spike_solve_batch_workspace.argtypes = [vp, vp, i32, ctypes.c_char, ctypes.POINTER(i64)]
         L.spike_tune.argtypes = [dp, i64, i64, i32, i32, i32, i32, vp, i32, vp, i32, vp, vp,
                                  ctypes.POINTER(TuneResult)]
@@ -195,6 +196,14 @@ class Factorization:
         self.status = rc
         if rc < 0:
             raise SpikeError(rc, "spike_factor_ex")
+
+    @classmethod
+    def _adopt(cls, h, n, kl, ku, opt):
+        """Wrap a handle made by spike_factor_batch."""
+        self = cls.__new__(cls)
+        self.n, self.kl, self.ku = n, kl, ku
+        self._opt, self._borrowed, self._h, self.status = opt, None, ctypes.c_void_p(h), 0
+        return self
 
     def solve(self, F, trans="N"):
         """Overwrite F (shape (nrhs, n) or (n,)) with op(A)^{-1} F.  Returns F."""
@@ -361,6 +370,29 @@ def solve_batch(facs, Fs, trans="N", workspace=None):
     if rc != 0:
         raise SpikeError(rc, "spike_solve_batch")
     return workspace
+
+
+def factor_batch(bands, kls, kus, ps, nrhs_hint=0, stage_balance=False, batch_invariant=False):
+    """spike_factor_batch: factor several device bands (torch tensors (n_i, kl_i+ku_i+1)) together,
+    their blocks in one launch and their reduced systems level by level.  Returns one
+    Factorization per band."""
+    cnt = len(bands)
+    for b in bands:
+        if not (_is_torch(b) and b.is_cuda):
+            raise ValueError("factor_batch takes CUDA tensors")
+    ptrs = (ctypes.c_void_p * cnt)(*[b.data_ptr() for b in bands])
+    ld = (ctypes.c_int64 * cnt)(*[b.shape[1] for b in bands])
+    ns = (ctypes.c_int64 * cnt)(*[b.shape[0] for b in bands])
+    kl_ = (ctypes.c_int * cnt)(*kls)
+    ku_ = (ctypes.c_int * cnt)(*kus)
+    p_ = (ctypes.c_int * cnt)(*ps)
+    flags = (FLAG_STAGE_BALANCE if stage_balance else 0) | (FLAG_BATCH_INVARIANT if batch_invariant else 0)
+    opt = SpikeOptions(nrhs_hint=nrhs_hint, flags=flags, stream=_torch_stream(bands[0]))
+    out = (ctypes.c_void_p * cnt)()
+    rc = lib().spike_factor_batch(ptrs, ld, ns, kl_, ku_, p_, cnt, ctypes.byref(opt), out)
+    if rc != 0:
+        raise SpikeError(rc, "spike_factor_batch")
+    return [Factorization._adopt(out[i], bands[i].shape[0], kls[i], kus[i], opt) for i in range(cnt)]
 
 
 def factor(band, kl, ku, p, pivot=0, **kw):

@@ -165,3 +165,49 @@ def test_factor_bytes_and_workspace_solve(cat, mixed):
     torch.cuda.synchronize()
     assert torch.equal(X1, X2)
     fac.free()
+
+
+def test_graph_buckets_replay_and_keep_results(cat):
+    """SPIKE_SERVE_GRAPHS: FP64 solves run as power-of-two column buckets from captured graphs;
+    every result equals the plain server's bit for bit (zero padding columns do not change the
+    others on batch-invariant handles; replays are the direct launches)."""
+    rng = np.random.default_rng(21)
+    jobs = [(i, int(rng.integers(1, 12)), "NT"[int(rng.integers(0, 2))]) for i in (0, 1, 2, 4) for _ in range(6)]
+    Fs = [rng.uniform(-1, 1, size=(m, CAT[i][0])) for i, m, _ in jobs]
+    outs = {}
+    for graphs in (False, True):
+        res = []
+        with serve.Server(8 << 30, streams=1, max_batch_rhs=16, graphs=graphs) as S:
+            for i, band in enumerate(cat):
+                if not CAT[i][4]:
+                    S.add_matrix(i, band, CAT[i][1], CAT[i][1])
+            for (i, m, tr), F in zip(jobs, Fs):  # one at a time: the same merges in both servers
+                rid, X = S.submit(i, F, trans=tr)
+                S.wait(rid)
+                res.append(X.copy())
+            st = S.stats()
+        outs[graphs] = (res, st)
+    for a, b in zip(outs[False][0], outs[True][0]):
+        assert np.array_equal(a, b)
+    assert outs[True][1]["graph_replays"] > 0 and outs[False][1]["graph_replays"] == 0
+    for (i, m, tr), F, X in zip(jobs, Fs, outs[True][0]):
+        _check(cat[i], CAT[i][1], F, X, tr, True)
+
+
+def test_tuned_worker_counts(cat):
+    """SPIKE_SERVE_TUNED: the first factorization of each size class runs spike_tune and later
+    ones reuse its worker count; served results still match the oracle."""
+    rng = np.random.default_rng(22)
+    bands = {0: cat[1], 1: inputs.make_band(21_000, 32, 32, seed=77, dd=1.1)[0]}  # one size class
+    with serve.Server(8 << 30, streams=2, max_batch_rhs=16, tuned=True, nrhs_hint=4) as S:
+        for i, b in bands.items():
+            S.add_matrix(i, torch.from_numpy(b).cuda(), 32, 32)
+        reqs = []
+        for i in (0, 1, 0, 1):
+            F = rng.uniform(-1, 1, size=(3, bands[i].shape[0]))
+            rid, X = S.submit(i, F, trans="N", mixed=bool(i))
+            reqs.append((rid, i, F, X))
+        for rid, i, F, X in reqs:
+            S.wait(rid)
+            _check(bands[i], 32, F, X, "N", True)
+        assert S.stats()["tuned_classes"] == 1
