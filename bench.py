@@ -632,6 +632,38 @@ def serving_leg(dev, requests, streams, max_batch, passes=2, seed=None, batch_sy
     return out
 
 
+def profile_case(case):
+    """One small factor + N + T solve for a profiler capture (inputs > L2, a few GB at most)."""
+    import torch
+    from paper_1811_03559_gb300 import inputs, spike
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    n, p = 262_144, 148
+    if case == "pivot":
+        k, m = 64, 8
+        pr = inputs.make_problem(n, k, k, m, seed=2, dist="normal", dd=0.3, keep_sign=True)
+        kw = {"pivot": 1}
+    else:
+        k, m = 128, 64
+        pr = inputs.make_problem(n, k, k, m, seed=1, dd=1.01)
+        kw = {"mixed": True, "stage_balance": True}
+    band = torch.from_numpy(pr["band"]).to(dev)
+    FN = torch.from_numpy(pr["F"]).to(dev)
+    FT = torch.from_numpy(inputs.band_matvec(pr["band"], k, k, pr["xstar"], "T")).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    fac = spike.Factorization(band, k, k, p, nrhs_hint=m, **kw)
+    X1, X2 = FN.clone(), FT.clone()
+    fac.solve(X1, "N")
+    fac.solve(X2, "T")
+    torch.cuda.synchronize()
+    ms = 1e3 * (time.perf_counter() - t0)
+    be = max(float(spike.backward_error(band, k, k, X1, FN, "N").max()),
+             float(spike.backward_error(band, k, k, X2, FT, "T").max()))
+    fac.free()
+    print(json.dumps({"profile_case": case, "n": n, "k": k, "nrhs": m, "p": p, "wall_ms": ms, "backward_error": be}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -661,7 +693,13 @@ def main():
                     help="eviction policy of the serving engine (SPIKE_SERVE_EVICT_LRU / _COST)")
     ap.add_argument("--serve-batch-systems", type=int, default=1,
                     help="matrices whose FP64 requests may share one solve (spike_solve_batch)")
+    ap.add_argument("--profile-case", choices=["pivot", "mixed"], default=None,
+                    help="run one small case for a profiler capture (n = 262,144; pivot: k = 64, nrhs = 8, "
+                         "factor + N + T; mixed: k = 128, nrhs = 64, FP32 factor + refined N + T) and exit")
     args = ap.parse_args()
+    if args.profile_case:
+        profile_case(args.profile_case)
+        return
     if args.e2e_steps is None:
         args.e2e_steps = args.steps
     n, k, p, m, dd, seed = args.n, args.k, args.p, args.nrhs, args.dd, 1
