@@ -673,7 +673,7 @@ struct FactorLayout {
          o_st = 0, mem = 0;
   bool split = false;
   size_t o_sfrag[2] = {0, 0}, o_srexp[2] = {0, 0}, o_snorm = 0;
-  size_t s_band = 0, s_z = 0, s_zoff = 0, s_leaf = 0, s_tmp = 0, tmp_bytes = 0, scr = 0;
+  size_t band_stage = 0, s_z = 0, s_zoff = 0, s_leaf = 0, s_tmp = 0, tmp_bytes = 0, scr = 0;
   std::vector<int64_t> zoff;
 };
 
@@ -735,7 +735,8 @@ static void factor_layout(const Plan &pl, int pivot, int f32, int64_t ldab, bool
   }
   L.mem = off;
   off = 0;
-  L.s_band = band_dev ? 0 : carve(sizeof(double) * (size_t)n * ldab);
+  // a host band is staged in an allocation of its own, freed once the setup kernels have read it
+  L.band_stage = band_dev ? 0 : sizeof(double) * (size_t)n * ldab;
   L.s_z = carve(es * (size_t)L.zacc);
   L.s_zoff = carve(sizeof(int64_t) * (size_t)nlv);
   L.s_leaf = carve(sizeof(LeafDev) * (size_t)nlv);
@@ -759,7 +760,7 @@ extern "C" int spike_factor_bytes(int64_t n, int kl, int ku, int p, int pivot, c
   factor_layout(pl, pivot, f32, (int64_t)kl + ku + 1, host_band == 0,
                 (opt && (opt->flags & SPIKE_FLAG_BORROW_BAND)) != 0, L, opt ? opt->flags : 0);
   *resident = (int64_t)L.mem;
-  *transient = (int64_t)L.scr;
+  *transient = (int64_t)(L.scr + L.band_stage);
   return 0;
 }
 
@@ -942,7 +943,7 @@ static int factor_impl(const double *band, int64_t ldab, int64_t n, int kl, int 
   }
 
   // factor-time scratch: staged band (host input), Z, per-merge temporaries
-  const size_t s_band = FL.s_band, s_z = FL.s_z, s_zoff = FL.s_zoff, s_leaf = FL.s_leaf, s_tmp = FL.s_tmp;
+  const size_t s_z = FL.s_z, s_zoff = FL.s_zoff, s_leaf = FL.s_leaf, s_tmp = FL.s_tmp;
   const size_t tmp_bytes = FL.tmp_bytes, soff = FL.scr;
   char *fscr = nullptr;
   {
@@ -952,18 +953,25 @@ static int factor_impl(const double *band, int64_t ldab, int64_t n, int kl, int 
       return fail(SPIKE_ENOMEM);
     }
   }
+  double *bstage = nullptr;  // staged host band
   auto fail2 = [&](int code) {
     cudaFreeAsync(fscr, s);
+    if (bstage) cudaFreeAsync(bstage, s);
     return fail(code);
   };
   const double *dband = band;
   if (!band_dev) {
-    double *b = (double *)(fscr + s_band);
-    if (cudaMemcpyAsync(b, band, sizeof(double) * (size_t)n * ldab, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+    cudaError_t e = dev_alloc((void **)&bstage, FL.band_stage, s);
+    if (e != cudaSuccess) {
+      g_cuda_err = std::string("cudaMallocAsync: ") + cudaGetErrorString(e);
+      bstage = nullptr;
+      return fail2(SPIKE_ENOMEM);
+    }
+    if (cudaMemcpyAsync(bstage, band, FL.band_stage, cudaMemcpyHostToDevice, s) != cudaSuccess) {
       g_cuda_err = "cudaMemcpyAsync band";
       return fail2(SPIKE_ECUDA);
     }
-    dband = b;
+    dband = bstage;
   }
   char *zbuf = fscr + s_z;  // element size es
   int64_t *dzoff = (int64_t *)(fscr + s_zoff);
@@ -1006,6 +1014,10 @@ static int factor_impl(const double *band, int64_t ldab, int64_t n, int kl, int 
       (rc = launch_zinit(dleaf, nlv, k, c->couple, zbuf, dzoff, c->f32, s)) != 0) {
     g_cuda_err = std::string("setup kernels: ") + cudaGetErrorString((cudaError_t)rc);
     return fail2(SPIKE_ECUDA);
+  }
+  if (bstage) {  // the setup kernels were the band's last readers (stream order frees it after them)
+    cudaFreeAsync(bstage, s);
+    bstage = nullptr;
   }
   if (c->timing) cudaEventRecord(c->fev[1], s);
   // 2. block factorizations and spike sweeps (Sec. 2.3): truncated sweeps for the
