@@ -787,6 +787,7 @@ def main():
     if dist:
         dist.barrier()
     peak_meas = spike.measure_fp64_peak(torch.cuda.current_stream().cuda_stream) if rank == 0 else None
+    pipes = spike.measure_pipes(torch.cuda.current_stream().cuda_stream) if rank == 0 else None
 
     # accuracy of the last timed step (GPU residual from the original band)
     be_n = float(spike.backward_error(band, k, k, F1, F1src, "N").max())
@@ -853,7 +854,7 @@ def main():
     band_h = torch.from_numpy(pr["band"]).pin_memory()
     F1h = torch.empty((m, n), dtype=torch.float64).pin_memory()
     F2hp = torch.empty((m, n), dtype=torch.float64).pin_memory()
-    e2e_s = 0.0
+    e2e_s, e2e_phase = 0.0, {}
     if args.no_e2e:
         args.e2e_steps = 0
     e2e_warm = max(1, args.warmup)  # the same W untimed steps as the device-timed leg
@@ -863,12 +864,18 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         fac = spike.Factorization(band_h.numpy(), k, k, p, nrhs_hint=m, stream=0, stage_balance=True)
+        t1 = time.perf_counter()  # each call returns once its stream is idle (results read back)
         fac.solve(F1h.numpy(), "N")
+        t2 = time.perf_counter()
         fac.solve(F2hp.numpy(), "T")
+        t3 = time.perf_counter()
         fac.free()
-        dt = time.perf_counter() - t0
+        t4 = time.perf_counter()
+        dt = t4 - t0
         if it >= e2e_warm:
             e2e_s += dt
+            for key, v in zip(("factor", "solve_n", "solve_t", "free"), (t1 - t0, t2 - t1, t3 - t2, t4 - t3)):
+                e2e_phase.setdefault(key, []).append(1e3 * v)
     e2e_step_s = e2e_s / args.e2e_steps if args.e2e_steps > 0 else float("nan")
     e2e_ms, e2e_value = e2e_step_s * 1e3, world * bytes_step / e2e_step_s / 1e9
     if dist is not None and args.e2e_steps > 0:  # max over ranks, as for the device-timed value
@@ -924,7 +931,8 @@ def main():
         "e2e": {"value": e2e_value, "unit": "GB/s",
                 "h2d_bytes_per_step": int(8 * n * (2 * k + 1) + 2 * 8 * n * m),
                 "d2h_bytes_per_step": int(2 * 8 * n * m), "steps": args.e2e_steps, "warmup": e2e_warm,
-                "ms_per_step": e2e_ms},
+                "ms_per_step": e2e_ms,
+                "phases_ms": {key: round(float(np.mean(v)), 2) for key, v in e2e_phase.items()}},
         "variants": {"mixed_fp32_fp64_refinement": mixed, "mixed_precision_workload": mixed_workload,
                      "large_dominant_grid": grid, "pivoting_workload": pivoting,
                      "cuda_graphs_repeated_solves": graphs},
@@ -932,6 +940,7 @@ def main():
         "tuning": tuning,
         "gpu_launches": int(launches),
         "clocks": clocks,
+        "pipes": pipes,
     }
     if not args.no_cpu and rank == 0 and world == 1:  # the CPU baseline is a single-GPU figure
         line["cpu_baseline"] = cpu_oracle_sample(k, m, dd, args.cpu_sample, seed)

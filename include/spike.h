@@ -16,7 +16,9 @@
  *          (the LAPACK band layout; ldab >= kl+ku+1).  Other entries are ignored.
  *   F    : F(i,c) at F[c*ldf + i], ldf >= n.  Overwritten by X.
  * Pointers may be device memory or host memory (pageable or pinned); host
- * buffers are staged through device memory inside the call.
+ * buffers are staged through device memory inside the call, except a pinned
+ * (page-locked and mapped) FP64 band, which the factorization's setup kernels
+ * read in place through its device address.
  *
  * Return codes: 0 on success.  -i: argument i is invalid (LAPACK info style,
  * arguments counted from 1).  SPIKE_E* (below): allocation, CUDA or internal
@@ -216,7 +218,9 @@ int spike_solve_ex(spike_handle h, double *F, int64_t ldf, int nrhs, char trans)
  * touching a GPU.  *resident: held by the handle until spike_free (block factors,
  * spike tips, reduced-system LUs and, with SPIKE_FLAG_MIXED, the FP64 band copy).
  * *transient: scratch that spike_factor allocates and frees inside the call (the
- * spike right-hand sides, plus a staged copy of the band when host_band != 0).
+ * spike right-hand sides, plus, for FP64 handles, a staged copy of the band when
+ * host_band != 0: the bound for a pageable band, as a pinned one is read in place
+ * and a mixed handle copies a host band straight into its FP64 band).
  * Neither counts the handle's descriptor buffer (a few hundred KB at most) nor solve
  * scratch (see spike_solve_ws).  Returns 0, -i for an invalid argument i, or
  * SPIKE_ENOTSUP. */
@@ -313,6 +317,22 @@ int spike_get_timings(spike_handle h, double *ms, int count);
  * per SM), in TFLOP/s (2 flop per FMA).  The roofline denominator of the FP64
  * kernels.  Synchronises `stream`. */
 int spike_measure_fp64_peak(void *stream, double *tflops);
+
+/* Throughput probes of the arithmetic pipes the design choices rest on, on the current
+ * device (2 CTAs of 512 threads per SM, 8 independent dependent chains per thread or warp,
+ * each timed with CUDA events after a short untimed launch).  out[0..count) receives, in
+ * this order (entries past 7 are left 0):
+ *   0  DFMA, TFLOP/s (2 flop per FMA; the same loop as spike_measure_fp64_peak)
+ *   1  FP64 mma.sync.m8n8k4 (DMMA), TFLOP/s
+ *   2  FP32 FMA, TFLOP/s
+ *   3  bf16 mma.sync.m16n8k16 with FP32 accumulation, TFLOP/s
+ *   4  ms of the even warps running DFMA chains, odd warps idle
+ *   5  ms of the odd warps running DMMA chains (the same FMA count), even warps idle
+ *   6  ms of both at once in alternate warps: about max(4, 5) if DFMA and DMMA issue to
+ *      separate pipes, about 4 + 5 if they share one.
+ * Synchronises `stream`.  Returns 0, -2 (out NULL), -3 (count < 1), SPIKE_ENOMEM or
+ * SPIKE_ECUDA. */
+int spike_measure_pipes(void *stream, double *out, int count);
 
 /* The machine constant K = K2/K1 of the load-balancing model (Sec. 3.3: solve cost per
  * row and right-hand side over factorization cost per row and band column), measured

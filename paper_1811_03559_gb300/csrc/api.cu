@@ -324,6 +324,18 @@ static bool is_device_ptr(const void *p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// The device address of page-locked host memory mapped into the device's address space
+// (cudaHostAlloc / cudaMallocHost, or cudaHostRegister with the mapped flag), else null:
+// kernels may read such a buffer in place over the host link.  Pageable memory gives null.
+static const void *mapped_host_ptr(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 // pointer into the spike-tip store: level lv, spike s (0 V, 1 W), leaf i, tip t (0 top, 1 bottom)
 static inline double *TIP(spike_ctx *c, int lv, int s, int i, int t) {
   return c->spk + tip_index(lv, s, i, t, c->nleaves, c->k);
@@ -735,8 +747,9 @@ static void factor_layout(const Plan &pl, int pivot, int f32, int64_t ldab, bool
   }
   L.mem = off;
   off = 0;
-  // a host band is staged in an allocation of its own, freed once the setup kernels have read it
-  L.band_stage = band_dev ? 0 : sizeof(double) * (size_t)n * ldab;
+  // a pageable host band is staged in an allocation of its own, freed once the setup kernels
+  // have read it (a pinned one is read in place; mixed handles copy it into their FP64 band)
+  L.band_stage = (band_dev || f32) ? 0 : sizeof(double) * (size_t)n * ldab;
   L.s_z = carve(es * (size_t)L.zacc);
   L.s_zoff = carve(sizeof(int64_t) * (size_t)nlv);
   L.s_leaf = carve(sizeof(LeafDev) * (size_t)nlv);
@@ -959,15 +972,31 @@ static int factor_impl(const double *band, int64_t ldab, int64_t n, int kl, int 
     if (bstage) cudaFreeAsync(bstage, s);
     return fail(code);
   };
+  // Where the setup kernels read the band: device memory as given; a mixed handle's FP64 copy
+  // (filled straight from host memory); pinned host memory in place, through its mapped device
+  // address (the repack streams it over the host link once, with no staging buffer); otherwise
+  // a staged device copy.
   const double *dband = band;
-  if (!band_dev) {
-    cudaError_t e = dev_alloc((void **)&bstage, FL.band_stage, s);
+  bool band_in_b64 = false;
+  if (!band_dev && c->f32) {
+    if (cudaMemcpyAsync(c->band64, band, sizeof(double) * (size_t)n * ldab, cudaMemcpyHostToDevice, s) !=
+        cudaSuccess) {
+      g_cuda_err = "cudaMemcpyAsync band";
+      return fail2(SPIKE_ECUDA);
+    }
+    dband = c->band64;
+    band_in_b64 = true;
+  } else if (!band_dev) {
+    dband = (const double *)mapped_host_ptr(band);
+  }
+  if (!band_dev && !dband) {
+    cudaError_t e = dev_alloc((void **)&bstage, sizeof(double) * (size_t)n * ldab, s);
     if (e != cudaSuccess) {
       g_cuda_err = std::string("cudaMallocAsync: ") + cudaGetErrorString(e);
       bstage = nullptr;
       return fail2(SPIKE_ENOMEM);
     }
-    if (cudaMemcpyAsync(bstage, band, FL.band_stage, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+    if (cudaMemcpyAsync(bstage, band, sizeof(double) * (size_t)n * ldab, cudaMemcpyHostToDevice, s) != cudaSuccess) {
       g_cuda_err = "cudaMemcpyAsync band";
       return fail2(SPIKE_ECUDA);
     }
@@ -995,7 +1024,7 @@ static int factor_impl(const double *band, int64_t ldab, int64_t n, int kl, int 
   }
   if (c->timing) cudaEventRecord(c->fev[0], s);
   // 1. repack the band into per-leaf LU storage; couplings; Z right-hand sides
-  if (c->f32 && !borrow &&
+  if (c->f32 && !borrow && !band_in_b64 &&
       cudaMemcpyAsync(c->band64, dband, sizeof(double) * (size_t)n * ldab, cudaMemcpyDeviceToDevice, s) !=
                     cudaSuccess) {
     g_cuda_err = "band copy";

@@ -976,6 +976,88 @@ extern "C" int spike_backward_error_noalloc(const double *band, int64_t ldab, in
   return 0;
 }
 
+namespace spk {
+// -------------------------------------------------------- pipe probes
+// Throughput loops for spike_measure_pipes.  Each thread (or warp, for mma.sync) runs 8
+// independent dependent chains; `sel` picks which warps run: bit 0 the even warps, bit 1
+// the odd warps (3 = all), so one kernel gives the solo and the mixed runs.
+__device__ __forceinline__ bool probe_runs(int sel) {
+  const int w = threadIdx.x >> 5;
+  return (w & 1) ? (sel & 2) != 0 : (sel & 1) != 0;
+}
+
+// DFMA chains (sel selects the warps) or, with dmma_sel, mma.sync.m8n8k4.f64 chains on the
+// other selection: the shared-pipe experiment runs both in alternate warps.
+__global__ void __launch_bounds__(512) k_pipe_fp64(double *out, int iters, int dfma_sel, int dmma_sel) {
+  double r = 0.0;
+  if (probe_runs(dfma_sel)) {
+    double a[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = threadIdx.x * 1e-3 + i;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) a[i] = fma(a[i], 1.0000001, 1e-9);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) r += a[i];
+  } else if (probe_runs(dmma_sel)) {
+    // per warp: 8 accumulator pairs of an 8x8 f64 tile, A and B fragments fixed
+    const double fa = 1.0 + threadIdx.x * 1e-7, fb = 1e-3;
+    double c[8][2];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) c[i][0] = c[i][1] = i;
+    // one mma.sync m8n8k4 = 256 FMAs per warp, 8 per lane: iters / 8 of them per chain give a
+    // lane the DFMA loop's iters FMAs per chain
+    const int n = iters / 8;
+    for (int it = 0; it < n; ++it) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+                     : "+d"(c[i][0]), "+d"(c[i][1])
+                     : "d"(fa), "d"(fb));
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) r += c[i][0] + c[i][1];
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = r;
+}
+
+__global__ void __launch_bounds__(512) k_pipe_fp32(float *out, int iters) {
+  float a[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) a[i] = threadIdx.x * 1e-3f + i;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = fmaf(a[i], 1.0000001f, 1e-9f);
+  }
+  float r = 0.f;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) r += a[i];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = r;
+}
+
+// mma.sync.m16n8k16 bf16 -> f32, 8 independent accumulator tiles per warp
+__global__ void __launch_bounds__(512) k_pipe_bf16(float *out, int iters) {
+  const uint32_t a0 = 0x3f803f80u, a1 = 0x3f003f00u, b0 = 0x3c003c00u;
+  float c[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) c[i][0] = c[i][1] = c[i][2] = c[i][3] = 0.f;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                   "{%0,%1,%2,%3};\n"
+                   : "+f"(c[i][0]), "+f"(c[i][1]), "+f"(c[i][2]), "+f"(c[i][3])
+                   : "r"(a0), "r"(a1), "r"(a0), "r"(a1), "r"(b0), "r"(b0));
+  }
+  float r = 0.f;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) r += c[i][0] + c[i][1] + c[i][2] + c[i][3];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = r;
+}
+
+}  // namespace spk
+
 extern "C" int spike_measure_fp64_peak(void *stream, double *tflops) {
   if (!tflops) return -2;
   cudaStream_t s = (cudaStream_t)stream;
@@ -1000,5 +1082,62 @@ extern "C" int spike_measure_fp64_peak(void *stream, double *tflops) {
   cudaFreeAsync(out, s);
   if (!ok || ms <= 0.0f) return SPIKE_ECUDA;
   *tflops = 2.0 * 8.0 * (double)iters * blocks * threads / (ms * 1e-3) / 1e12;
+  return 0;
+}
+
+extern "C" int spike_measure_pipes(void *stream, double *out, int count) {
+  if (!out) return -2;
+  if (count < 1) return -3;
+  for (int i = 0; i < count; ++i) out[i] = 0.0;
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return SPIKE_ECUDA;
+  const int blocks = 2 * sms, threads = 512, iters = 8192;
+  const size_t nthr = (size_t)blocks * threads;
+  double *buf = nullptr;
+  if (spk::dev_alloc((void **)&buf, sizeof(double) * nthr, s) != cudaSuccess) return SPIKE_ENOMEM;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  bool ok = true;
+  // time one launch (after an untimed short one of the same kernel), in ms
+  auto timed = [&](auto launch) {
+    launch(iters / 8);
+    cudaEventRecord(e0, s);
+    launch(iters);
+    cudaEventRecord(e1, s);
+    spk::count_launch(2);
+    float ms = 0.0f;
+    ok = ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms > 0.0f;
+    return (double)ms;
+  };
+  const double fma_flop = 2.0 * 8.0 * (double)iters * nthr;  // 8 chains x iters FMAs per thread
+  auto fp64 = [&](int dsel, int msel) {
+    return timed([&](int it) { spk::k_pipe_fp64<<<blocks, threads, 0, s>>>(buf, it, dsel, msel); });
+  };
+  // the DFMA rate from the peak probe's kernel (the roofline denominator), the rest from the
+  // selectable kernel, which also runs the solo and mixed halves of the shared-pipe experiment
+  const double t_dfma = timed([&](int it) { spk::k_dfma_probe<<<blocks, threads, 0, s>>>(buf, it, 1.0000001, 1e-9); });
+  const double t_dmma = fp64(0, 3);
+  const double t_even_dfma = fp64(1, 0), t_odd_dmma = fp64(0, 2), t_mix = fp64(1, 2);
+  const double t_fp32 = timed([&](int it) { spk::k_pipe_fp32<<<blocks, threads, 0, s>>>((float *)buf, it); });
+  const double t_bf16 = timed([&](int it) { spk::k_pipe_bf16<<<blocks, threads, 0, s>>>((float *)buf, it); });
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(buf, s);
+  if (!ok || cudaGetLastError() != cudaSuccess) return SPIKE_ECUDA;
+  // per warp: 8 chains of iters / 8 m8n8k4 MMAs of 256 FMAs (the same FMAs as the DFMA loop);
+  // bf16: 8 chains of iters m16n8k16 MMAs of 2048 FMAs
+  const double mma64_flop = 2.0 * 8.0 * (double)(iters / 8) * 256.0 * (nthr / 32);
+  const double bf16_flop = 2.0 * 8.0 * (double)iters * 2048.0 * (nthr / 32);
+  const double vals[7] = {fma_flop / (t_dfma * 1e-3) / 1e12,
+                          mma64_flop / (t_dmma * 1e-3) / 1e12,
+                          fma_flop / (t_fp32 * 1e-3) / 1e12,
+                          bf16_flop / (t_bf16 * 1e-3) / 1e12,
+                          t_even_dfma,
+                          t_odd_dmma,
+                          t_mix};
+  for (int i = 0; i < count && i < 7; ++i) out[i] = vals[i];
   return 0;
 }

@@ -56,7 +56,7 @@ EXPORTS = ["spike_plan", "spike_factor", "spike_factor_ex", "spike_solve", "spik
            "spike_free", "spike_strerror", "spike_last_cuda_error", "spike_backward_error_noalloc",
            "spike_measure_fp64_peak", "spike_factor_bytes", "spike_solve_workspace", "spike_solve_ws",
            "spike_measure_K", "spike_tune", "spike_solve_batch", "spike_solve_batch_workspace",
-           "spike_release_cached", "spike_residual", "spike_factor_batch"]
+           "spike_release_cached", "spike_residual", "spike_factor_batch", "spike_measure_pipes"]
 SPIKE_ELIMIT = -1006
 NOALLOC_MAX_NRHS = 1024
 
@@ -104,6 +104,7 @@ def lib():
         L.spike_backward_error_noalloc.argtypes = [dp, i64, i64, i32, i32, dp, dp, i32, ctypes.c_char, vp, dp]
         L.spike_get_timings.argtypes = [vp, dp, i32]
         L.spike_measure_fp64_peak.argtypes = [vp, dp]
+        L.spike_measure_pipes.argtypes = [vp, dp, i32]
         L.spike_factor_bytes.argtypes = [i64, i32, i32, i32, i32, ctypes.POINTER(SpikeOptions), i32,
                                          ctypes.POINTER(i64), ctypes.POINTER(i64)]
         L.spike_solve_workspace.argtypes = [vp, i32, ctypes.c_char, i32, ctypes.POINTER(i64)]
@@ -291,6 +292,20 @@ def measure_fp64_peak(stream=None):
     if rc != 0:
         raise SpikeError(rc, "spike_measure_fp64_peak")
     return out.value
+
+
+PIPE_KEYS = ("dfma_tflops", "dmma_tflops", "fp32_fma_tflops", "bf16_mma_sync_tflops",
+             "dfma_even_warps_ms", "dmma_odd_warps_ms", "both_alternate_warps_ms")
+
+
+def measure_pipes(stream=None):
+    """Throughput probes of the FP64 FMA, FP64 MMA, FP32 FMA and bf16 MMA pipes and the
+    DFMA/DMMA shared-pipe experiment (spike_measure_pipes), as a dict."""
+    out = np.zeros(len(PIPE_KEYS))
+    rc = lib().spike_measure_pipes(ctypes.c_void_p(stream or 0), out.ctypes.data_as(ctypes.c_void_p), len(PIPE_KEYS))
+    if rc != 0:
+        raise SpikeError(rc, "spike_measure_pipes")
+    return dict(zip(PIPE_KEYS, out.tolist()))
 
 
 def kernel_launches():

@@ -128,6 +128,35 @@ def test_host_pointers_match_device():
     np.testing.assert_array_equal(Xh, Xd)
 
 
+@pytest.mark.parametrize("mixed", [False, True])
+def test_pinned_host_band_matches_device(mixed):
+    """A pinned host band (read in place by the setup kernels for FP64 handles, copied straight
+    into the FP64 band of mixed ones), a pageable one (staged) and a device one give the same
+    bits, for host and device right-hand sides, N and T."""
+    n, kl, ku, p, m = 30_011, 9, 5, 12, 4
+    pr = inputs.make_problem(n, kl, ku, m, seed=31, dd=1.05)
+    band = np.ascontiguousarray(pr["band"])
+    pinned = torch.from_numpy(band).pin_memory()
+    assert pinned.is_pinned()
+    facs = [spike.factor(b, kl, ku, p, mixed=mixed) for b in (_dev(band), pinned.numpy(), band.copy())]
+    for trans in ("N", "T"):
+        F = inputs.band_matvec(band, kl, ku, pr["xstar"], trans)
+        outs = []
+        for i, fac in enumerate(facs):
+            X = _dev(F)
+            fac.solve(X, trans)
+            outs.append(X.cpu().numpy())
+            Fh = torch.from_numpy(F.copy()).pin_memory() if i == 1 else None
+            Xh = Fh.numpy() if Fh is not None else F.copy()
+            fac.solve(Xh, trans)
+            outs.append(Xh.copy())
+        for o in outs[1:]:
+            np.testing.assert_array_equal(o, outs[0])
+        check(band, kl, ku, F, outs[0], trans)
+    for fac in facs:
+        fac.free()
+
+
 def test_refactor_and_reuse_for_both_transposes():
     pr = inputs.make_problem(9000, 10, 10, 2, seed=21, dd=1.1)
     fac = spike.factor(_dev(pr["band"]), 10, 10, 7)
