@@ -1092,12 +1092,13 @@ static int factor_impl(const double *band, int64_t ldab, int64_t n, int kl, int 
       *out = c;
       return 0;
     }
+    std::vector<SweepDesc> pairs;
+    for (int i = 0; i < nlv; ++i) {
+      if (pivot) pairs.push_back(ltop[i]);
+      pairs.push_back(lbot[i]);
+      pairs.push_back(ub[i]);
+    }
     if (!pivot) {
-      std::vector<SweepDesc> pairs;
-      for (int i = 0; i < nlv; ++i) {
-        pairs.push_back(lbot[i]);
-        pairs.push_back(ub[i]);
-      }
       Arena ar;
       const size_t off = ar.put(pairs);
       if ((rc = ensure(&c->dargs, &c->dargs_bytes, ar.h.size(), s)) != 0) return fail2(rc);
@@ -1113,18 +1114,21 @@ static int factor_impl(const double *band, int64_t ldab, int64_t n, int kl, int 
       }
       if (c->timing) cudaEventRecord(c->fev[2], s);
     } else {
-      rc = launch_factor_piv(dleaf, nlv, k, c->ldf, (double *)c->fbc, (double *)c->dinvc, c->ipiv, c->status, s);
+      // block GEPP, then the block's pivoted L sweeps and U sweep, in one launch
+      Arena ar;
+      const size_t off = ar.put(pairs);
+      if ((rc = ensure(&c->dargs, &c->dargs_bytes, ar.h.size(), s)) != 0) return fail2(rc);
+      if (cudaMemcpyAsync(c->dargs, ar.h.data(), ar.h.size(), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        g_cuda_err = "sweep descriptors";
+        return fail2(SPIKE_ECUDA);
+      }
+      rc = launch_factor_piv(dleaf, nlv, k, c->ldf, (double *)c->fbc, (double *)c->dinvc, c->ipiv, c->status,
+                             (const SweepDesc *)(c->dargs + off), s);
       if (rc != 0) {
         g_cuda_err = std::string("factor kernel: ") + cudaGetErrorString((cudaError_t)rc);
         return fail2(SPIKE_ECUDA);
       }
       if (c->timing) cudaEventRecord(c->fev[2], s);
-      Pipeline pp;
-      pp.st = s;
-      std::vector<SweepDesc> none_v(nlv, empty_sweep());
-      pp.stage(ltop, lbot, LN, LN, c->ldf, c->dofs, k);
-      pp.stage(ub, none_v, -1, -1, c->ldf, c->dofs, k);
-      if ((rc = pp.run(c)) != 0) return fail2(rc);
     }
   }
   if ((rc = launch_tips0(dleaf, nlv, k, zbuf, dzoff, c->spk, s, c->f32)) != 0) {

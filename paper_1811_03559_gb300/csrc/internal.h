@@ -160,8 +160,9 @@ int launch_zinit(const LeafDev *leaves, int nleaves, int k, const double *couple
 int launch_factor_nopiv(const LeafDev *leaves, int nleaves, int k, int ldf, void *fb, void *dinv, void *zbuf,
                         const int64_t *zoff, const unsigned long long *amax_bits, double boost_eps,
                         unsigned long long *status, const SweepDesc *sweeps, void *stream, int f32);
+// sweeps: three per block (pivoted L sweep of the top spike, of the bottom spike, U sweep of both)
 int launch_factor_piv(const LeafDev *leaves, int nleaves, int k, int ldf, double *fb, double *dinv, int *ipiv,
-                      unsigned long long *status, void *stream);
+                      unsigned long long *status, const SweepDesc *sweeps, void *stream);
 // One block of one system for the multi-system factorization (FP64, no pivoting): its geometry,
 // the system's bandwidth and storage (ldf, factor and reciprocal bases, the block's Z columns),
 // the system's max|a_ij| and status words, and the two spike sweeps that follow its LU.

@@ -19,6 +19,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -397,228 +398,532 @@ int launch_factor_nopiv(const LeafDev *leaves, int nleaves, int k, int ldf, void
 }
 
 // ------------------------------------------------------ pivoting block LU
-// Unblocked banded GEPP of one leaf (Sec. 5.1): the pivot is the first entry of
-// largest magnitude among the k+1 band candidates; rows are swapped across the
-// columns j..j+2k (U fill up to kl+ku superdiagonals); multipliers are stored
-// unpermuted (interleaved form, swaps applied during the sweeps).  The UL of the
-// last block is this LU of Q A Q (Sec. 5.2).
-__global__ void __launch_bounds__(NTHREADS)
-    k_factor_piv(const LeafDev *leaves, int k, int ldf, double *fb_all, double *dinv_all, int *ipiv_all,
-                 unsigned long long *status) {
-  const LeafDev L = leaves[blockIdx.x];
-  const int64_t nl = L.len;
-  double *fb = fb_all + L.start * (int64_t)ldf;
-  double *dinv = dinv_all + L.start;
-  int *ipiv = ipiv_all + L.start;
-  const int dofs = 2 * k;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  __shared__ int s_p, s_zero;
-  for (int64_t j = 0; j < nl; ++j) {
-    const int64_t last = min(j + k, nl - 1);
-    if (warp == 0) {
-      double best = -1.0;
-      int64_t bi = j;
-      for (int64_t r = j + lane; r <= last; r += 32) {
-        const double v = fabs(fb[j * ldf + dofs + r - j]);
-        if (v > best) {
-          best = v;
-          bi = r;
-        }
-      }
-      for (int o = 16; o; o >>= 1) {
-        const double ov = __shfl_down_sync(FULLMASK, best, o);
-        const int64_t oi = __shfl_down_sync(FULLMASK, bi, o);
-        if (ov > best || (ov == best && oi < bi)) {
-          best = ov;
-          bi = oi;
-        }
-      }
-      if (lane == 0) {
-        s_p = (int)(bi - j);
-        s_zero = !(best > 0.0);
-        if (s_zero) {
-          const int64_t gcol = L.rev ? (L.start + nl - 1 - j) : (L.start + j);
-          atomicMin(&status[1], (unsigned long long)(gcol + 1));
-          if (isnan(best)) atomicOr(&status[2], 1ull);
-        }
-      }
-    }
-    __syncthreads();
-    const int64_t p = j + s_p;
-    if (tid == 0) ipiv[j] = (int)p;
-    if (s_zero) {
-      if (tid == 0) dinv[j] = 0.0;
-      __syncthreads();
-      continue;
-    }
-    const int64_t cmax = min(j + 2 * k, nl - 1);
-    if (p != j) {
-      for (int64_t c = j + tid; c <= cmax; c += NTHREADS) {
-        double *a = &fb[c * ldf + dofs + j - c];
-        double *b = &fb[c * ldf + dofs + p - c];
-        const double t = *a;
-        *a = *b;
-        *b = t;
-      }
-    }
-    __syncthreads();
-    const double rinv = 1.0 / fb[j * ldf + dofs];
-    if (tid == 0) dinv[j] = rinv;
-    for (int64_t r = j + 1 + tid; r <= last; r += NTHREADS) fb[j * ldf + dofs + r - j] *= rinv;
-    __syncthreads();
-    const int nr = (int)(last - j);
-    const int ncl = (int)(cmax - j);
-    for (int idx = tid; idx < nr * ncl; idx += NTHREADS) {
-      const int64_t r = j + 1 + idx % nr, c = j + 1 + idx / nr;
-      fb[c * ldf + dofs + r - c] -= fb[j * ldf + dofs + r - j] * fb[c * ldf + dofs + j - c];
-    }
-    __syncthreads();
-  }
-}
+// Blocked banded GEPP of one leaf (Sec. 5.1), right-looking over panels of PNB columns.  The
+// pivot of a column is the first entry of largest magnitude among its k + 1 band candidates;
+// U fills up to kl + ku = 2k superdiagonals; the multipliers are stored as computed at their
+// own step (not permuted by later interchanges: the sweeps apply the interchanges interleaved
+// with the L columns); ipiv holds leaf-local rows and dinv the pivots' reciprocals (0 for an
+// all-zero column, whose step then changes nothing).  The UL of the last block is this LU of
+// Q A Q (Sec. 5.2), stored in the reversed local frame.  Per panel j0 .. j0 + jb - 1:
+//  (a) the panel's rows j0 .. j0 + jb + k - 1 (all candidate rows of its columns) are loaded
+//      into shared memory;
+//  (b) panel GEPP in shared memory: per column, warp 0 picks the pivot (first row of largest
+//      magnitude) and interchanges the two rows across the whole panel (earlier columns too,
+//      so that L11 and L21 are the permuted factors of a block LU); all threads then update
+//      the panel's later columns and write this column's multipliers to the leaf storage;
+//  (c) the panel's L columns are scaled and its U rows written back;
+//  (d) the trailing columns j0 + jb .. j0 + jb + 2k - 1 (the reach of the U fill), in chunks
+//      of cw columns: the window rows are gathered through the panel's row permutation,
+//      U12 = L11^{-1} A12 (one column per thread), A22 -= L21 U12 (register tiles), stored.
+// In exact arithmetic this performs the eliminations of the unblocked algorithm; entries of a
+// row beyond its fill reach are zero, so gathering them through the permutation changes nothing.
+constexpr int PNB = 32;
+constexpr size_t PIV_SMEM_MAX = 220 * 1024;  // dynamic shared memory budget of the kernel (a CTA may use 227 KB)
 
-// The same GEPP with the active window in shared memory.  At column j the window holds rows
-// j..j+k (the pivot candidates) and columns j..j+2k (the U fill, Sec. 5.1), plus one spare
-// row and one spare column: row j+k+1 and column j+2k+1 enter while step j updates, so a
-// column costs two CTA barriers.  Columns live in circular slots (c mod (2k+2)); rows are
-// reached through a slot map (row r -> map[r mod (k+2)]), so a row interchange swaps two
-// map entries instead of moving data.  Step j:
-//   A (warp 0): pivot = first row of largest |a_rj| among rows j..j+k; swap the map
-//     entries of rows j and p; 1 / pivot (0 for an all-zero column, whose step then changes
-//     nothing, as in the global-memory kernel).
-//   B (all): a_rc -= a_rj (u_c / pivot) for r in (j, j+k], c in (j, j+2k] (lanes over
-//     columns, warps over rows); write row j of U and the multipliers a_rj / pivot of
-//     column j to the leaf's band storage; load row j+k+1 and clear column j+2k+1.
-// Same storage, pivots and reciprocals as k_factor_piv (multipliers unpermuted, interleaved).
-constexpr int PIV_SMEM_MAX = 200 * 1024;
-
-__global__ void __launch_bounds__(NTHREADS)
-    k_factor_piv_smem(const LeafDev *leaves, int k, int ldf, double *fb_all, double *dinv_all, int *ipiv_all,
-                      unsigned long long *status) {
-  extern __shared__ __align__(16) unsigned char piv_raw[];
-  const int CS = 2 * k + 2, M = k + 2;
-  double *Wn = (double *)piv_raw;      // M row slots x CS column slots
-  int *map = (int *)(Wn + (size_t)M * CS);
-  __shared__ double s_rinv;
-  const LeafDev L = leaves[blockIdx.x];
+__device__ void factor_piv_leaf(const LeafDev &L, int k, int ldf, double *fb_all, double *dinv_all, int *ipiv_all,
+                                unsigned long long *status, int cw, double *smem) {
+  const int PLD = PNB + k + 1;  // panel: PNB columns x PLD rows, column-major
+  const int TLD = cw + 1;       // trailing chunk: PNB + k rows x TLD, row-major
+  double *P = smem;
+  double *Wt = P + (size_t)PNB * PLD;
+  int *perm = (int *)(Wt + (size_t)(PNB + k) * TLD);
+  __shared__ double s_rinv[PNB];
   const int nl = (int)L.len;
   double *fb = fb_all + L.start * (int64_t)ldf;
   double *dinv = dinv_all + L.start;
   int *ipiv = ipiv_all + L.start;
   const int dofs = 2 * k;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (nl <= 0) return;
-  // rows and columns by offset from j: row j + d sits in row slot map[(jm + d) mod M], column
-  // j + e in column slot (jc + e) mod CS; 0 <= d <= k + 1 and 0 <= e <= 2k + 1, so one wrap
-  auto wrapM = [&](int x) { return x >= M ? x - M : x; };
-  auto wrapC = [&](int x) { return x >= CS ? x - CS : x; };
-  // band entry (r, c) of the leaf before elimination (zero outside the band)
-  auto orig = [&](int r, int c) -> double {
-    if (r < 0 || r >= nl || c < 0 || c >= nl || r - c > k || c - r > 2 * k) return 0.0;
-    return fb[(int64_t)c * ldf + dofs + r - c];
-  };
-  for (int i = tid; i < M; i += NTHREADS) map[i] = i;
-  // rows 0..k (slots 0..k), columns 0..2k+1
-  for (int idx = tid; idx < (k + 1) * CS; idx += NTHREADS) {
-    const int r = idx / CS, c = idx - r * CS;
-    Wn[(size_t)r * CS + c] = (c <= 2 * k) ? orig(r, c) : 0.0;
+  // leaf-local (r, c) -> storage index; stored entries have -2k <= r - c <= k
+  auto at = [&](int r, int c) -> int64_t { return (int64_t)c * ldf + dofs + r - c; };
+  auto stored = [&](int r, int c) { return r - c <= k && c - r <= dofs; };
+  for (int j0 = 0; j0 < nl; j0 += PNB) {
+    const int jb = min(PNB, nl - j0);
+    const int prow = min(jb + k, nl - j0);
+    // (a)
+    for (int idx = tid; idx < PNB * PLD; idx += NTHREADS) {
+      const int c = idx / PLD, r = idx - c * PLD;
+      P[idx] = (c < jb && r < prow && stored(r, c)) ? fb[at(j0 + r, j0 + c)] : 0.0;
+    }
+    for (int r = tid; r < prow; r += NTHREADS) perm[r] = r;
+    __syncthreads();
+    // (b)
+    for (int c = 0; c < jb; ++c) {
+      const int dl = min(c + k, prow - 1);
+      if (warp == 0) {
+        double best = -1.0;
+        int bd = c;
+        for (int r = c + lane; r <= dl; r += 32) {
+          const double v = fabs(P[c * PLD + r]);
+          if (v > best) {
+            best = v;
+            bd = r;
+          }
+        }
+        for (int o = 16; o; o >>= 1) {
+          const double ov = __shfl_xor_sync(FULLMASK, best, o);
+          const int od = __shfl_xor_sync(FULLMASK, bd, o);
+          if (ov > best || (ov == best && od < bd)) {
+            best = ov;
+            bd = od;
+          }
+        }
+        const bool zero = !(best > 0.0);
+        if (bd != c) {
+          for (int cc = lane; cc < jb; cc += 32) {
+            const double t = P[cc * PLD + c];
+            P[cc * PLD + c] = P[cc * PLD + bd];
+            P[cc * PLD + bd] = t;
+          }
+        }
+        __syncwarp();
+        if (lane == 0) {
+          if (bd != c) {
+            const int t = perm[c];
+            perm[c] = perm[bd];
+            perm[bd] = t;
+          }
+          ipiv[j0 + c] = j0 + bd;
+          if (zero) {
+            const int64_t gcol = L.rev ? (L.start + nl - 1 - (j0 + c)) : (L.start + j0 + c);
+            atomicMin(&status[1], (unsigned long long)(gcol + 1));
+            if (isnan(best)) atomicOr(&status[2], 1ull);
+          }
+          const double ri = zero ? 0.0 : 1.0 / P[c * PLD + c];
+          s_rinv[c] = ri;
+          dinv[j0 + c] = ri;
+        }
+      }
+      __syncthreads();
+      // column c stays unscaled in P until (c); q = 0 writes the multiplier, q > 0 updates column c + q
+      const double rinv = s_rinv[c];
+      const int nr = dl - c, ncl = jb - c;
+      for (int idx = tid; idx < nr * ncl; idx += NTHREADS) {
+        const int q = idx / nr, r = c + 1 + (idx - q * nr);
+        const double l = P[c * PLD + r] * rinv;
+        if (q == 0) {
+          fb[at(j0 + r, j0 + c)] = l;
+        } else {
+          double *pc = P + (c + q) * PLD;
+          pc[r] = fma(-l, pc[c], pc[r]);
+        }
+      }
+      __syncthreads();
+    }
+    // (c)
+    for (int idx = tid; idx < jb * PLD; idx += NTHREADS) {
+      const int c = idx / PLD, r = idx - c * PLD;
+      if (r < prow) {
+        if (r > c) P[idx] *= s_rinv[c];
+        else if (c - r <= dofs) fb[at(j0 + r, j0 + c)] = P[idx];
+      }
+    }
+    __syncthreads();
+    // (d)
+    const int nt = min(dofs, nl - j0 - jb);
+    for (int q0 = 0; q0 < nt; q0 += cw) {
+      const int nq = min(cw, nt - q0);
+      for (int base = tid; base < prow * nq; base += NTHREADS * 8) {  // 8 loads in flight per thread
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int idx = base + u * NTHREADS;
+          const int qq = idx / prow, r = idx - qq * prow;
+          const int sr = (idx < prow * nq) ? perm[r] : 0, c = jb + q0 + qq;
+          v[u] = (idx < prow * nq && stored(sr, c)) ? fb[at(j0 + sr, j0 + c)] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int idx = base + u * NTHREADS;
+          if (idx < prow * nq) Wt[(idx % prow) * TLD + idx / prow] = v[u];
+        }
+      }
+      __syncthreads();
+      for (int qq = tid; qq < nq; qq += NTHREADS) {
+        double x[PNB];
+#pragma unroll
+        for (int a = 0; a < PNB; ++a) x[a] = (a < jb) ? Wt[a * TLD + qq] : 0.0;
+#pragma unroll
+        for (int b = 0; b < PNB - 1; ++b) {
+          const double xb = x[b];
+#pragma unroll
+          for (int a = b + 1; a < PNB; ++a) x[a] = fma(-P[b * PLD + a], xb, x[a]);
+        }
+#pragma unroll
+        for (int a = 0; a < PNB; ++a)
+          if (a < jb) Wt[a * TLD + qq] = x[a];
+      }
+      __syncthreads();
+      const int nrr = prow - jb;
+      const int RT = (nrr + 31) / 32, CT = (nq + 15) / 16;
+      for (int tile = warp; tile < RT * CT; tile += NTHREADS / 32) {
+        const int i0 = (tile % RT) * 32, qq0 = (tile / RT) * 16;
+        const int i = i0 + lane;
+        const bool vi = i < nrr;
+        // U12 row a is zero beyond column a + 2k (relative to j0): rows a < q + jb - 2k vanish
+        const int astart = max(0, q0 + qq0 + jb - dofs);
+        double acc[16];
+        double *wrow = Wt + (size_t)(jb + (vi ? i : 0)) * TLD + qq0;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) acc[q] = (vi && qq0 + q < nq) ? wrow[q] : 0.0;
+        for (int a = astart; a < jb; ++a) {
+          const double l = vi ? P[a * PLD + jb + i] : 0.0;
+          const double *trow = Wt + (size_t)a * TLD + qq0;
+#pragma unroll
+          for (int q = 0; q < 16; ++q) acc[q] = fma(-l, trow[q], acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+          if (vi && qq0 + q < nq) wrow[q] = acc[q];
+      }
+      __syncthreads();
+      for (int idx = tid; idx < prow * nq; idx += NTHREADS) {
+        const int qq = idx / prow, r = idx - qq * prow;
+        const int c = jb + q0 + qq;
+        if (stored(r, c)) fb[at(j0 + r, j0 + c)] = Wt[r * TLD + qq];
+      }
+      __syncthreads();
+    }
   }
-  __syncthreads();
-  int jm = 0, jc = 0;
-  // the entering row j + k + 1 is read one step ahead (thread tid holds column j + 1 + tid)
-  double nxt = (tid <= 2 * k) ? orig(k + 1, 1 + tid) : 0.0;
-  for (int j = 0; j < nl; ++j) {
-    const int dl = min(k, nl - 1 - j);      // rows j .. j + dl are candidates
-    const int ec = min(2 * k, nl - 1 - j);  // columns j .. j + ec hold U fill
-    // A: pivot search on column j
-    if (warp == 0) {
+}
+
+// The same block GEPP with look-ahead, for bandwidths whose two panel buffers fit in shared
+// memory.  The panel factorization is a chain of small dependent steps and the trailing update
+// is throughput-bound FP64 work, so they overlap: with panel i factored,
+//  (T1) all warps update the columns of panel i+1 by panel i (interchanges, U12 by a warp-wide
+//       triangular solve, A22 -= L21 U12) and build panel i+1 in the other buffer (its top k rows
+//       are the updated A22 rows, the rest come from the leaf storage);
+//  (T2) warp 0 factors panel i+1 (lanes over rows for the updates, over columns for the
+//       interchanges, no CTA barrier) while warps 1..7 update the remaining trailing columns of
+//       panel i (up to column j0 + jb + 2k), synchronised by a named barrier among themselves.
+// Panel i+1 reads only its own columns, which T1 completed; T2's two parts write disjoint
+// columns.  Results are those of factor_piv_leaf up to the summation order of the updates.
+__device__ __forceinline__ void bar_rest() { asm volatile("bar.sync 1, %0;" ::"n"(NTHREADS - 32) : "memory"); }
+
+__device__ void factor_piv_leaf_la(const LeafDev &L, int k, int ldf, double *fb_all, double *dinv_all,
+                                   int *ipiv_all, unsigned long long *status, int cw, double *smem) {
+  const int PLD = PNB + k + 1;  // panels: PNB columns x PLD rows, column-major (two buffers)
+  const int TLD = cw + 1;       // trailing chunk: PNB + k rows x TLD, row-major
+  double *Pbuf0 = smem;
+  double *Pbuf1 = smem + (size_t)PNB * PLD;
+  double *Wt = smem + (size_t)2 * PNB * PLD;
+  int *perm0 = (int *)(Wt + (size_t)(PNB + k) * TLD);
+  int *perm1 = perm0 + (PNB + k);
+  const int nl = (int)L.len;
+  double *fb = fb_all + L.start * (int64_t)ldf;
+  double *dinv = dinv_all + L.start;
+  int *ipiv = ipiv_all + L.start;
+  const int dofs = 2 * k;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  auto at = [&](int r, int c) -> int64_t { return (int64_t)c * ldf + dofs + r - c; };
+  auto stored = [&](int r, int c) { return r - c <= k && c - r <= dofs; };
+
+  // GEPP of the panel in P (rows [0, prow) of the window at j0, jb columns) by warp 0
+  auto panel = [&](double *P, int *perm, int j0, int jb, int prow) {
+    for (int c = 0; c < jb; ++c) {
+      const int dl = min(c + k, prow - 1);
       double best = -1.0;
-      int bd = 0;
-      for (int d = lane; d <= dl; d += 32) {
-        const double v = fabs(Wn[(size_t)map[wrapM(jm + d)] * CS + jc]);
+      int bd = c;
+      for (int r = c + lane; r <= dl; r += 32) {
+        const double v = fabs(P[c * PLD + r]);
         if (v > best) {
           best = v;
-          bd = d;
+          bd = r;
         }
       }
       for (int o = 16; o; o >>= 1) {
-        const double ov = __shfl_down_sync(FULLMASK, best, o);
-        const int od = __shfl_down_sync(FULLMASK, bd, o);
+        const double ov = __shfl_xor_sync(FULLMASK, best, o);
+        const int od = __shfl_xor_sync(FULLMASK, bd, o);
         if (ov > best || (ov == best && od < bd)) {
           best = ov;
           bd = od;
         }
       }
+      const bool zero = !(best > 0.0);
+      if (bd != c) {
+        for (int cc = lane; cc < jb; cc += 32) {
+          const double t = P[cc * PLD + c];
+          P[cc * PLD + c] = P[cc * PLD + bd];
+          P[cc * PLD + bd] = t;
+        }
+      }
       if (lane == 0) {
-        ipiv[j] = j + bd;
-        const bool zero = !(best > 0.0);
+        if (bd != c) {
+          const int t = perm[c];
+          perm[c] = perm[bd];
+          perm[bd] = t;
+        }
+        ipiv[j0 + c] = j0 + bd;
         if (zero) {
-          const int64_t gcol = L.rev ? (L.start + nl - 1 - j) : (L.start + j);
+          const int64_t gcol = L.rev ? (L.start + nl - 1 - (j0 + c)) : (L.start + j0 + c);
           atomicMin(&status[1], (unsigned long long)(gcol + 1));
           if (isnan(best)) atomicOr(&status[2], 1ull);
         }
-        if (bd != 0) {
-          const int b = wrapM(jm + bd);
-          const int t = map[jm];
-          map[jm] = map[b];
-          map[b] = t;
-        }
-        const double piv = Wn[(size_t)map[jm] * CS + jc];
-        const double ri = zero ? 0.0 : 1.0 / piv;
-        s_rinv = ri;
-        dinv[j] = ri;
       }
+      __syncwarp();
+      const double rinv = zero ? 0.0 : 1.0 / P[c * PLD + c];
+      if (lane == 0) dinv[j0 + c] = rinv;
+      for (int r = c + 1 + lane; r <= dl; r += 32) {
+        const double l = P[c * PLD + r] * rinv;
+        P[c * PLD + r] = l;
+        fb[at(j0 + r, j0 + c)] = l;
+        for (int cc = c + 1; cc < jb; ++cc) P[cc * PLD + r] = fma(-l, P[cc * PLD + c], P[cc * PLD + r]);
+      }
+      __syncwarp();
     }
-    __syncthreads();
-    // B: trailing update, write-out of row j of U and column j of L, next row and column in
-    const double rinv = s_rinv;
-    const double *Wj = Wn + (size_t)map[jm] * CS;
-    {
+    for (int idx = lane; idx < jb * PNB; idx += 32) {
+      const int c = idx / PNB, r = idx - c * PNB;
+      if (r <= c && c - r <= dofs) fb[at(j0 + r, j0 + c)] = P[c * PLD + r];
+    }
+  };
+  // gather rows [0, prow) of columns [jb + q0, jb + q0 + nq) (relative to j0) through perm into Wt,
+  // by the threads t0 + (0 .. nth-1); 8 loads in flight per thread
+  auto gather = [&](const int *perm, int j0, int jb, int prow, int q0, int nq, int t0, int nth) {
+    const int tot = prow * nq;
+    for (int base = t0; base < tot; base += nth * 8) {
       double v[8];
-      int cs[8];
-      int nq = 0;
-      for (int e = 1 + lane; e <= ec && nq < 8; e += 32) {
-        cs[nq] = wrapC(jc + e);
-        v[nq] = Wj[cs[nq]] * rinv;
-        ++nq;
-      }
-      for (int d = 1 + warp; d <= dl; d += NTHREADS / 32) {
-        double *Wr = Wn + (size_t)map[wrapM(jm + d)] * CS;
-        const double a = Wr[jc];
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
-          if (q < nq) Wr[cs[q]] = fma(-a, v[q], Wr[cs[q]]);
+      for (int u = 0; u < 8; ++u) {
+        const int idx = base + u * nth;
+        const int qq = idx / prow, r = idx - qq * prow;
+        const int sr = (idx < tot) ? perm[r] : 0, c = jb + q0 + qq;
+        v[u] = (idx < tot && stored(sr, c)) ? fb[at(j0 + sr, j0 + c)] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int idx = base + u * nth;
+        if (idx < tot) {
+          const int qq = idx / prow, r = idx - qq * prow;
+          Wt[r * TLD + qq] = v[u];
+        }
       }
     }
-    for (int e = tid; e <= ec; e += NTHREADS) fb[(int64_t)(j + e) * ldf + dofs - e] = Wj[wrapC(jc + e)];
-    for (int d = 1 + tid; d <= dl; d += NTHREADS)
-      fb[(int64_t)j * ldf + dofs + d] = Wn[(size_t)map[wrapM(jm + d)] * CS + jc] * rinv;
-    {
-      const int cn = wrapC(jc + 2 * k + 1);
-      if (j + k + 1 < nl) {
-        double *Wn_new = Wn + (size_t)map[wrapM(jm + k + 1)] * CS;  // the slot row j-1 left
-        if (tid <= 2 * k) Wn_new[wrapC(jc + 1 + tid)] = nxt;
+  };
+  // U12 = L11^{-1} A12 on Wt column qq by one warp (lanes <-> rows), for up to 4 columns at once
+  auto trsm_warp = [&](const double *P, int jb, const int *cols, int ncol) {
+    double x[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) x[u] = (u < ncol && lane < jb) ? Wt[lane * TLD + cols[u]] : 0.0;
+    for (int b = 0; b + 1 < jb; ++b) {
+      const double lb = (lane > b) ? P[b * PLD + lane] : 0.0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const double xb = __shfl_sync(FULLMASK, x[u], b);
+        if (lane > b) x[u] = fma(-lb, xb, x[u]);
       }
-      nxt = (tid <= 2 * k) ? orig(j + k + 2, j + 2 + tid) : 0.0;
-      for (int d = 1 + tid; d <= k; d += NTHREADS) Wn[(size_t)map[wrapM(jm + d)] * CS + cn] = 0.0;
     }
-    jm = wrapM(jm + 1);
-    jc = wrapC(jc + 1);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (u < ncol && lane < jb) Wt[lane * TLD + cols[u]] = x[u];
+  };
+  // U12 = L11^{-1} A12 on Wt column qq by one thread
+  auto trsm_thread = [&](const double *P, int jb, int qq) {
+    double x[PNB];
+#pragma unroll
+    for (int a = 0; a < PNB; ++a) x[a] = (a < jb) ? Wt[a * TLD + qq] : 0.0;
+#pragma unroll
+    for (int b = 0; b < PNB - 1; ++b) {
+      const double xb = x[b];
+#pragma unroll
+      for (int a = b + 1; a < PNB; ++a) x[a] = fma(-P[b * PLD + a], xb, x[a]);
+    }
+#pragma unroll
+    for (int a = 0; a < PNB; ++a)
+      if (a < jb) Wt[a * TLD + qq] = x[a];
+  };
+  // A22 -= L21 U12 on one tile of 32 rows x C columns of Wt (rows jb + i0.., columns qq0..);
+  // with dst the results go to the next panel (column-major, row i), else back to Wt
+  auto gemm_tile = [&](const double *P, int jb, int nrr, int nq, int i0, int qq0, int astart, double *dst, auto cn) {
+    constexpr int C = decltype(cn)::value;
+    const int i = i0 + lane;
+    const bool vi = i < nrr;
+    double acc[C];
+    double *wrow = Wt + (size_t)(jb + (vi ? i : 0)) * TLD + qq0;
+#pragma unroll
+    for (int q = 0; q < C; ++q) acc[q] = (vi && qq0 + q < nq) ? wrow[q] : 0.0;
+    for (int a = astart; a < jb; ++a) {
+      const double l = vi ? P[a * PLD + jb + i] : 0.0;
+      const double *trow = Wt + (size_t)a * TLD + qq0;
+#pragma unroll
+      for (int q = 0; q < C; ++q) acc[q] = fma(-l, trow[q], acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < C; ++q)
+      if (vi && qq0 + q < nq) {
+        if (dst) dst[(qq0 + q) * PLD + i] = acc[q];
+        else wrow[q] = acc[q];
+      }
+  };
+
+  // panel 0
+  {
+    const int jb = min(PNB, nl), prow = min(jb + k, nl);
+    for (int idx = tid; idx < PNB * PLD; idx += NTHREADS) {
+      const int c = idx / PLD, r = idx - c * PLD;
+      Pbuf0[idx] = (c < jb && r < prow && stored(r, c)) ? fb[at(r, c)] : 0.0;
+    }
+    for (int r = tid; r < prow; r += NTHREADS) perm0[r] = r;
     __syncthreads();
+    if (warp == 0) panel(Pbuf0, perm0, 0, jb, prow);
+    __syncthreads();
+  }
+  double *P = Pbuf0, *Pn = Pbuf1;
+  int *perm = perm0, *permn = perm1;
+  for (int j0 = 0; j0 < nl; j0 += PNB) {
+    const int jb = min(PNB, nl - j0), prow = min(jb + k, nl - j0);
+    const int nrr = prow - jb;
+    const int nt = min(dofs, nl - j0 - jb);  // trailing columns reached by this panel
+    const int j1 = j0 + jb;
+    const int jb1 = max(0, min(PNB, nl - j1)), prow1 = max(0, min(jb1 + k, nl - j1));
+    const int la = min(jb1, nt);  // columns of the next panel that this one updates
+    // (T1)
+    if (la > 0) {
+      gather(perm, j0, jb, prow, 0, la, tid, NTHREADS);
+      __syncthreads();
+      {
+        int cols[4], ncol = 0;
+        for (int qq = warp; qq < la && ncol < 4; qq += NTHREADS / 32) cols[ncol++] = qq;
+        if (ncol > 0) trsm_warp(P, jb, cols, ncol);
+      }
+      __syncthreads();
+      const int RT = (nrr + 31) / 32, CT = (la + 7) / 8;
+      for (int tile = warp; tile < RT * CT; tile += NTHREADS / 32) {
+        const int i0 = (tile % RT) * 32, qq0 = (tile / RT) * 8;
+        gemm_tile(P, jb, nrr, la, i0, qq0, max(0, qq0 + jb - dofs), Pn, std::integral_constant<int, 8>());
+      }
+      // U12 rows to the storage; the rest of the next panel from the storage
+      for (int idx = tid; idx < jb * la; idx += NTHREADS) {
+        const int qq = idx / jb, r = idx - qq * jb;
+        if (stored(r, jb + qq)) fb[at(j0 + r, j1 + qq)] = Wt[r * TLD + qq];
+      }
+      for (int base = tid; base < PNB * PLD; base += NTHREADS * 4) {
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int idx = base + u * NTHREADS;
+          const int c = idx / PLD, r = idx - c * PLD;
+          v[u] = (idx < PNB * PLD && c < jb1 && r < prow1 && stored(r, c) && !(c < la && r < nrr))
+                     ? fb[at(j1 + r, j1 + c)]
+                     : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int idx = base + u * NTHREADS;
+          const int c = idx / PLD, r = idx - c * PLD;
+          if (idx < PNB * PLD && !(c < la && r < nrr)) Pn[idx] = v[u];
+        }
+      }
+      for (int r = tid; r < prow1; r += NTHREADS) permn[r] = r;
+      __syncthreads();
+    } else if (jb1 > 0) {  // the next panel lies beyond this one's reach (2k < PNB)
+      for (int idx = tid; idx < PNB * PLD; idx += NTHREADS) {
+        const int c = idx / PLD, r = idx - c * PLD;
+        Pn[idx] = (c < jb1 && r < prow1 && stored(r, c)) ? fb[at(j1 + r, j1 + c)] : 0.0;
+      }
+      for (int r = tid; r < prow1; r += NTHREADS) permn[r] = r;
+      __syncthreads();
+    }
+    // (T2)
+    if (warp == 0) {
+      if (jb1 > 0) panel(Pn, permn, j1, jb1, prow1);
+    } else {
+      const int t2 = tid - 32, nw = NTHREADS / 32 - 1;
+      for (int q0 = la; q0 < nt; q0 += cw) {
+        const int nq = min(cw, nt - q0);
+        gather(perm, j0, jb, prow, q0, nq, t2, NTHREADS - 32);
+        bar_rest();
+        if (nq >= 64) {
+          for (int qq = t2; qq < nq; qq += NTHREADS - 32) trsm_thread(P, jb, qq);
+        } else {
+          int cols[4], ncol = 0;
+          for (int qq = warp - 1; qq < nq && ncol < 4; qq += nw) cols[ncol++] = qq;
+          if (ncol > 0) trsm_warp(P, jb, cols, ncol);
+          for (int qq0 = warp - 1 + 4 * nw; qq0 < nq; qq0 += 4 * nw) {
+            ncol = 0;
+            for (int qq = qq0; qq < nq && ncol < 4; qq += nw) cols[ncol++] = qq;
+            trsm_warp(P, jb, cols, ncol);
+          }
+        }
+        bar_rest();
+        const int RT = (nrr + 31) / 32, CT = (nq + 15) / 16;
+        for (int tile = warp - 1; tile < RT * CT; tile += nw) {
+          const int i0 = (tile % RT) * 32, qq0 = (tile / RT) * 16;
+          gemm_tile(P, jb, nrr, nq, i0, qq0, max(0, q0 + qq0 + jb - dofs), nullptr,
+                    std::integral_constant<int, 16>());
+        }
+        bar_rest();
+        for (int idx = t2; idx < prow * nq; idx += NTHREADS - 32) {
+          const int qq = idx / prow, r = idx - qq * prow;
+          const int c = jb + q0 + qq;
+          if (stored(r, c)) fb[at(j0 + r, j0 + c)] = Wt[r * TLD + qq];
+        }
+        bar_rest();
+      }
+    }
+    __syncthreads();
+    double *tp = P;
+    P = Pn;
+    Pn = tp;
+    int *tq = perm;
+    perm = permn;
+    permn = tq;
   }
 }
 
+template <int KIND>
+__device__ void piv_sweep_run(const SweepDesc &D, int k, int ldf, int dofs, double *pwin);
+
+// One block per CTA: its GEPP, then its spike sweeps (Sec. 2.3 with the pivoted factors of
+// Sec. 5.1), so a block's whole factor stage is one CTA's work, as for the non-pivoting LU:
+// sweeps[3 b] and sweeps[3 b + 1] are pivoted L sweeps (the top spike's full sweep and the
+// bottom spike's truncated one), sweeps[3 b + 2] the U sweep over both spikes.  lookahead
+// selects factor_piv_leaf_la (two panel buffers) over factor_piv_leaf.
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_factor_piv(const LeafDev *leaves, int k, int ldf, double *fb_all, double *dinv_all, int *ipiv_all,
+                 unsigned long long *status, int cw, int lookahead, const SweepDesc *sweeps) {
+  extern __shared__ __align__(16) unsigned char pb_raw[];
+  double *smem = (double *)pb_raw;
+  const LeafDev L = leaves[blockIdx.x];
+  if (lookahead) factor_piv_leaf_la(L, k, ldf, fb_all, dinv_all, ipiv_all, status, cw, smem);
+  else factor_piv_leaf(L, k, ldf, fb_all, dinv_all, ipiv_all, status, cw, smem);
+  const int dofs = 2 * k;
+  const SweepDesc *sw = sweeps + 3 * (int64_t)blockIdx.x;
+  __syncthreads();
+  piv_sweep_run<LN>(sw[0], k, ldf, dofs, smem);
+  __syncthreads();
+  piv_sweep_run<LN>(sw[1], k, ldf, dofs, smem);
+  __syncthreads();
+  sweep_run<double>(sw[2], ldf, dofs, smem);
+}
+
+// Shared memory of the block GEPP (one or two panel buffers) for trailing chunk width cw.
+static size_t piv_blk_smem(int k, int cw, int npanel) {
+  return sizeof(double) * ((size_t)npanel * PNB * (PNB + k + 1) + (size_t)(PNB + k) * (cw + 1)) +
+         sizeof(int) * (size_t)npanel * (PNB + k);
+}
+
 int launch_factor_piv(const LeafDev *leaves, int nleaves, int k, int ldf, double *fb, double *dinv, int *ipiv,
-                      unsigned long long *status, void *stream) {
-  const size_t smem = sizeof(double) * (size_t)(k + 2) * (2 * k + 2) + sizeof(int) * (size_t)(k + 2);
-  if (smem <= PIV_SMEM_MAX && k <= 127) {  // 8 columns per lane cover the 2k fill columns; a thread per entering entry
-    const int e = smem_at_least((const void *)k_factor_piv_smem, smem);
-    if (e) return e;
-    k_factor_piv_smem<<<nleaves, NTHREADS, smem, (cudaStream_t)stream>>>(leaves, k, ldf, fb, dinv, ipiv, status);
-  } else {
-    k_factor_piv<<<nleaves, NTHREADS, 0, (cudaStream_t)stream>>>(leaves, k, ldf, fb, dinv, ipiv, status);
+                      unsigned long long *status, const SweepDesc *sweeps, void *stream) {
+  const size_t swp = std::max(SWEEP_SMEM, sizeof(double) * (size_t)(NTHREADS / 32) * (k + 2));
+  // look-ahead when two panel buffers and a trailing chunk of at least PNB columns (the next
+  // panel's, staged in the same array) fit; the chunk is as wide as the columns left after the
+  // next panel's (at most 128, a multiple of 16)
+  for (int la = 1; la >= 0; --la) {
+    const int want = la ? 2 * k - PNB : 2 * k;
+    const int cwmin = la ? PNB : 16;
+    const int cwmax = std::max(cwmin, std::min(128, (want + 15) / 16 * 16));
+    for (int cw = cwmax; cw >= cwmin; cw -= 16) {
+      const size_t smem = std::max(piv_blk_smem(k, cw, la ? 2 : 1), swp);
+      if (smem > PIV_SMEM_MAX) continue;
+      const int e = smem_at_least((const void *)k_factor_piv, smem);
+      if (e) return e;
+      k_factor_piv<<<nleaves, NTHREADS, smem, (cudaStream_t)stream>>>(leaves, k, ldf, fb, dinv, ipiv, status, cw,
+                                                                      la, sweeps);
+      count_launch();
+      return (int)cudaGetLastError();
+    }
   }
-  count_launch();
-  return (int)cudaGetLastError();
+  return SPIKE_ENOTSUP;
 }
 
 // ------------------------------------------------------ blocked sweep engine
@@ -1027,9 +1332,7 @@ int launch_sweeps(const SweepDesc *descs, int ncta, int per_cta, int ldf, int do
 constexpr int LPRE = 4;  // multipliers a lane prefetches per step (k <= 128; wider bands read the rest directly)
 
 template <int KIND>
-__global__ void __launch_bounds__(NTHREADS) k_piv_sweep(const SweepDesc *descs, int k, int ldf, int dofs) {
-  extern __shared__ double pwin[];
-  const SweepDesc D = descs[blockIdx.x];
+__device__ void piv_sweep_run(const SweepDesc &D, int k, int ldf, int dofs, double *pwin) {
   if (D.ncols <= 0 || D.r1 <= D.r0) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int WIN = k + 1;
@@ -1169,6 +1472,12 @@ __global__ void __launch_bounds__(NTHREADS) k_piv_sweep(const SweepDesc *descs, 
     }
     __syncwarp();
   }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(NTHREADS) k_piv_sweep(const SweepDesc *descs, int k, int ldf, int dofs) {
+  extern __shared__ double pwin[];
+  piv_sweep_run<KIND>(descs[blockIdx.x], k, ldf, dofs, pwin);
 }
 
 int launch_piv_sweep(int kind, const SweepDesc *descs, int ndesc, int k, int ldf, int dofs, void *stream) {

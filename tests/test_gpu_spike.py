@@ -306,6 +306,35 @@ def test_pivoting_matches_gepp_when_p1():
     assert metrics.forward_error(X, xo) <= 1e-14 * cond
 
 
+@pytest.mark.parametrize("k,n", [(40, 3000), (128, 3000), (300, 2400)])
+def test_pivoting_one_block_matches_gepp(k, n):
+    """One pivoted block at bandwidths that run the look-ahead block GEPP with one trailing chunk
+    (k = 40), with several (k = 128), and the single-buffer block GEPP (k = 300): the pivots are
+    those of the oracle's banded GEPP, so the results agree to rounding times the condition."""
+    pr = inputs.make_problem(n, k, k, 2, seed=7, dist="normal", dd=0.3, keep_sign=True)
+    assert oracle.BandLU(pr["band"], k, k).info == 0
+    from oracle import condest
+    cond = condest.cond1_estimate(pr["band"], k, k)
+    for trans in ("N", "T"):
+        F = pr["F"]
+        X, _ = gpu_solve(pr["band"], k, k, F, 1, trans, pivot=1)
+        xo, _ = oracle.gbsv(pr["band"], k, k, F, trans)
+        be = metrics.backward_error(pr["band"], k, k, X, F, trans)
+        bo = metrics.backward_error(pr["band"], k, k, xo, F, trans)
+        assert be <= BERR
+        # two solutions with backward errors be, bo differ by about cond * (be + bo) (the bound of
+        # test_pivoting_workload, with the same allowance for the estimator and first-order terms)
+        assert metrics.forward_error(X, xo) <= max(1e-12, 20.0 * cond * (be + bo)), (trans, cond, be, bo)
+
+
+@pytest.mark.parametrize("k,p,n", [(128, 3, 6000), (300, 2, 4000)])
+@pytest.mark.parametrize("trans", ["N", "T"])
+def test_pivoting_wide_bands(k, p, n, trans):
+    pr = inputs.make_problem(n, k, k, 3, seed=11 + p, dist="normal", dd=0.3, keep_sign=True, trans=trans)
+    X, fac = gpu_solve(pr["band"], k, k, pr["F"], p, trans, pivot=1)
+    assert metrics.backward_error(pr["band"], k, k, X, pr["F"], trans) <= BERR
+
+
 def test_pivot_zero_column_reports_singular():
     n, k = 400, 3
     band, _ = inputs.make_band(n, k, k, seed=1, dist="normal", dd=0.5, keep_sign=True)
