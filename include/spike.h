@@ -68,6 +68,10 @@ extern "C" {
  * spike_get_info reports the steps and the final backward error).  Non-pivoting
  * only (SPIKE_ENOTSUP with pivot = 1). */
 #define SPIKE_FLAG_MIXED 4
+/* Default partition ratio R13 of pivoting factorizations (see spike_options.R13): the
+ * fastest of 1.5, 2, 2.5 and the formula for factor + N + T solve on the pivoting
+ * workload (n = 262,144, k = 16 and 64, nrhs = 8, p = 148) on GB300. */
+#define SPIKE_PIVOT_R13 1.5
 /* Batch-invariant solves: every right-hand side of a solve gets the same bits whatever
  * the number of columns solved with it and its position among them.  The window
  * products of the triangular sweeps are then summed over a fixed set of sub-ranges
@@ -141,7 +145,12 @@ typedef struct {
   /* cudaStream_t for all work of the handle; NULL = the legacy default stream. */
   void *stream;
   /* > 0: use this partition ratio R13 = n1/n3 (R12 = R13/2) instead of the formula or
-   * SPIKE_FLAG_STAGE_BALANCE -- for ratio sweeps and tuned configurations (Sec. 3.3). */
+   * SPIKE_FLAG_STAGE_BALANCE -- for ratio sweeps and tuned configurations (Sec. 3.3).
+   * Pivoting factorizations (pivot = 1) without this or SPIKE_FLAG_STAGE_BALANCE use
+   * SPIKE_PIVOT_R13: the formula models the non-pivoting costs, whereas the pivoted end
+   * blocks' GEPP costs several times a middle block's per row and the pivoted L sweeps of
+   * a solve are a larger share.  spike_plan has no pivot argument: pass
+   * R13 = SPIKE_PIVOT_R13 to it for the plan of a pivoting factorization. */
   double R13;
   /* SPIKE_FLAG_MIXED: stop refining a column once its FP64 backward error is <= this
    * (<= 0 selects SPIKE_MIXED_TOL). */

@@ -758,6 +758,13 @@ static void factor_layout(const Plan &pl, int pivot, int f32, int64_t ldab, bool
   L.scr = off;
 }
 
+// The partition ratio requested by opt, with the pivoting default (spike_options.R13).
+static double plan_r13(const spike_options *opt, int pivot) {
+  const double r13 = opt ? opt->R13 : 0.0;
+  if (r13 > 0.0 || !pivot || (opt && (opt->flags & SPIKE_FLAG_STAGE_BALANCE))) return r13;
+  return SPIKE_PIVOT_R13;
+}
+
 extern "C" int spike_factor_bytes(int64_t n, int kl, int ku, int p, int pivot, const spike_options *opt,
                                   int host_band, int64_t *resident, int64_t *transient) {
   if (!resident) return -8;
@@ -765,7 +772,7 @@ extern "C" int spike_factor_bytes(int64_t n, int kl, int ku, int p, int pivot, c
   if (pivot != 0 && pivot != 1) return -5;
   Plan pl;
   const int rc = make_plan(n, kl, ku, p, opt ? opt->K : 0.0, opt ? opt->nrhs_hint : 0, opt ? opt->flags : 0,
-                     opt ? opt->R13 : 0.0, pl);
+                           plan_r13(opt, pivot), pl);
   if (rc != 0) return rc;
   const int f32 = (opt && (opt->flags & SPIKE_FLAG_MIXED)) ? 1 : 0;
   if (f32 && pivot) return SPIKE_ENOTSUP;
@@ -822,7 +829,7 @@ static int factor_impl(const double *band, int64_t ldab, int64_t n, int kl, int 
   }
   Plan pl;
   int rc = make_plan(n, kl, ku, p, opt ? opt->K : 0.0, opt ? opt->nrhs_hint : 0, opt ? opt->flags : 0,
-                     opt ? opt->R13 : 0.0, pl);
+                     plan_r13(opt, pivot), pl);
   if (rc != 0) return map_plan_rc(rc);
   pl.pivot = pivot;
 

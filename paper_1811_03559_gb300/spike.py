@@ -70,6 +70,7 @@ FLAG_FP64_RESIDUAL = 64
 NUMERICS_NAN_PIVOT = 1
 NUMERICS_SINGULAR_INTERFACE = 2
 MIXED_TOL = 1e-14
+PIVOT_R13 = 1.5  # default partition ratio of pivoting factorizations (spike.h SPIKE_PIVOT_R13)
 STAGES = ["factor", "setup", "block_lu", "spikes", "reduced", "solve_n", "solve_n_d", "solve_n_reduced",
           "solve_n_retrieval", "solve_t", "solve_t_s", "solve_t_reduced", "solve_t_d"]
 

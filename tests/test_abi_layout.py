@@ -56,3 +56,4 @@ def test_numerics_bits_match_header():
     hdr = open(os.path.join(ROOT, "include", "spike.h")).read()
     assert "#define SPIKE_NUMERICS_NAN_PIVOT %d" % spike.NUMERICS_NAN_PIVOT in hdr
     assert "#define SPIKE_NUMERICS_SINGULAR_INTERFACE %d" % spike.NUMERICS_SINGULAR_INTERFACE in hdr
+    assert "#define SPIKE_PIVOT_R13 %g" % spike.PIVOT_R13 in hdr
