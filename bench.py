@@ -513,7 +513,8 @@ def tuning_leg(band, k, nrhs):
             "seconds": time.perf_counter() - t0}
 
 
-def serving_leg(dev, requests, streams, max_batch, passes=2, seed=None, batch_systems=1, evict="lru"):
+def serving_leg(dev, requests, streams, max_batch, passes=2, seed=None, batch_systems=1, evict="lru",
+                fp64_residual=False):
     """Many-matrix serving workload (inputs.SERVING) through the native serving engine.
 
     The catalogue bands live in device memory (the caller's; the budget covers the
@@ -546,7 +547,7 @@ def serving_leg(dev, requests, streams, max_batch, passes=2, seed=None, batch_sy
     arena = torch.empty(cap, dtype=torch.float64).pin_memory().numpy()
     budget = int(cfg["budget_gb"] * 1e9)
     S = serve.Server(budget, streams=streams, max_batch_rhs=max_batch, nrhs_hint=16, batch_systems=batch_systems,
-                     evict=evict)
+                     evict=evict, fp64_residual=fp64_residual)
     for i in used:
         S.add_matrix(i, bands[i], int(ks[i]), int(ks[i]))
     out = {"workload": "%d requests, Poisson %g/s, %d matrices (n log-uniform [%d, %d], k uniform {4..128 step 4}, "
@@ -555,6 +556,7 @@ def serving_leg(dev, requests, streams, max_batch, passes=2, seed=None, batch_sy
                           cfg["nrhs_max"], round(100 * cfg["trans_t"]), round(100 * cfg["mixed"]), cfg["budget_gb"]),
            "matrices_used": len(used), "catalogue_gb": sum(8.0 * ns[i] * (2 * ks[i] + 1) for i in used) / 1e9,
            "streams": streams, "max_batch_rhs": max_batch, "batch_systems": batch_systems, "evict": evict,
+           "mixed_residual": "FP64 FMAs" if fp64_residual else "tensor cores (digit planes of op(A) kept per handle)",
            "catalogue_gen_s": t_gen,
            "data": "synthetic (torch generator on the device for the bands, seeded per matrix)", "passes": []}
     launches0 = spike.kernel_launches()
@@ -707,6 +709,9 @@ def main():
     ap.add_argument("--serve-streams", type=int, default=8)
     ap.add_argument("--serve-batch", type=int, default=64)
     ap.add_argument("--serve-passes", type=int, default=2)
+    ap.add_argument("--serve-tensor-residual", action="store_true",
+                    help="mixed-precision serving handles keep op(A)'s digit planes and form their residuals on "
+                         "the tensor cores (default: FP64 FMAs, smaller handles)")
     ap.add_argument("--serve-evict", choices=("lru", "cost"), default="lru",
                     help="eviction policy of the serving engine (SPIKE_SERVE_EVICT_LRU / _COST)")
     ap.add_argument("--serve-batch-systems", type=int, default=1,
@@ -914,7 +919,8 @@ def main():
     serving = None
     if not args.no_serve and extras:
         serving = serving_leg(dev, args.serve_requests, args.serve_streams, args.serve_batch, args.serve_passes,
-                              batch_systems=args.serve_batch_systems, evict=args.serve_evict)
+                              batch_systems=args.serve_batch_systems, evict=args.serve_evict,
+                              fp64_residual=not args.serve_tensor_residual)
         serving["cpu_baseline"] = cpu_serve
 
     if rank != 0:

@@ -64,6 +64,11 @@ typedef struct spike_server_s *spike_server;
  * uses the fastest.  The tuning runs on the worker that meets the class first and allocates
  * its own n x nrhs_hint right-hand sides outside the budget. */
 #define SPIKE_SERVE_TUNED 4
+/* Mixed-precision factorizations form their refinement residuals with FP64 FMAs
+ * (SPIKE_FLAG_FP64_RESIDUAL): no digit planes of op(A), so a mixed handle takes about
+ * 24 (kl + ku) bytes per row instead of about 56 (kl + ku), and more of them stay resident
+ * under the budget; each residual then runs on the FP64 pipe. */
+#define SPIKE_SERVE_FP64_RESIDUAL 8
 
 typedef struct {
   int64_t budget_bytes;    /* device bytes for factorizations, their scratch and the workspaces (> 0) */

@@ -967,6 +967,30 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 template <typename T, int C>
 __device__ __forceinline__ void window_fma(T *acc, const T *tw, const T *xrow, int64_t xstep, int64_t xcs,
                                            int col_base, int lastc, int count) {
+  // Row-major X with this warp's C columns contiguous and 16-byte aligned: one 16-byte load per
+  // 16 / sizeof(T) columns (the same FMAs in the same order as the element-wise loop below).
+  constexpr int V = 16 / (int)sizeof(T);
+  constexpr int NV = (C >= V) ? C / V : 1;
+  if (C >= V && C % V == 0 && xcs == 1 && col_base + C - 1 <= lastc && xstep % V == 0 &&
+      ((uintptr_t)(xrow + col_base) & 15) == 0) {
+    using VT = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    const VT *xv = reinterpret_cast<const VT *>(xrow + col_base);
+    const int64_t vstep = xstep / V;
+    for (int j = 0; j < count; ++j) {
+      const T t = tw[j * NB];
+      VT x[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) x[v] = xv[v];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const T *e = reinterpret_cast<const T *>(&x[v]);
+#pragma unroll
+        for (int u = 0; u < V; ++u) acc[v * V + u] = fma(t, e[u], acc[v * V + u]);
+      }
+      xv += vstep;
+    }
+    return;
+  }
   int64_t coff[C];
 #pragma unroll
   for (int q = 0; q < C; ++q) coff[q] = (int64_t)min(col_base + q, lastc) * xcs;

@@ -297,6 +297,7 @@ void worker(spike_server_s *S, int w) {
       o.K = S->cfg.K;
       o.nrhs_hint = S->cfg.nrhs_hint > 0 ? S->cfg.nrhs_hint : 16;
       o.flags = SPIKE_FLAG_STAGE_BALANCE | SPIKE_FLAG_BATCH_INVARIANT | (prec ? SPIKE_FLAG_MIXED : 0) |
+                ((prec && (S->cfg.flags & SPIKE_SERVE_FP64_RESIDUAL)) ? SPIKE_FLAG_FP64_RESIDUAL : 0) |
                 (M.host ? 0 : SPIKE_FLAG_BORROW_BAND) |
                 ((S->cfg.flags & SPIKE_SERVE_GRAPHS) && !prec ? SPIKE_FLAG_GRAPHS : 0);
       // SPIKE_SERVE_TUNED: the size class's measured worker count, or tune it now

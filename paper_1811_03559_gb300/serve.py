@@ -15,6 +15,7 @@ from . import spike
 DRYRUN = 1
 GRAPHS = 2
 TUNED = 4
+FP64_RESIDUAL = 8  # SPIKE_SERVE_FP64_RESIDUAL
 EVICT_LRU, EVICT_COST = 0, 1
 
 
@@ -79,11 +80,13 @@ class Server:
     recently used first) or "cost" (greedy-dual size-frequency, spike_serve.h)."""
 
     def __init__(self, budget_bytes, streams=4, max_batch_rhs=64, p=0, nrhs_hint=0, K=0.0, dryrun=False,
-                 dryrun_factor_us=0, dryrun_solve_us=0, batch_systems=0, evict="lru", graphs=False, tuned=False):
+                 dryrun_factor_us=0, dryrun_solve_us=0, batch_systems=0, evict="lru", graphs=False, tuned=False,
+                 fp64_residual=False):
         self._keep = {}
         cfg = ServerConfig(budget_bytes=int(budget_bytes), streams=streams, max_batch_rhs=max_batch_rhs, p=p,
                            nrhs_hint=nrhs_hint, K=K,
-                           flags=(DRYRUN if dryrun else 0) | (GRAPHS if graphs else 0) | (TUNED if tuned else 0),
+                           flags=(DRYRUN if dryrun else 0) | (GRAPHS if graphs else 0) | (TUNED if tuned else 0) |
+                                 (FP64_RESIDUAL if fp64_residual else 0),
                            dryrun_factor_us=dryrun_factor_us, dryrun_solve_us=dryrun_solve_us,
                            batch_systems=batch_systems, evict_policy={"lru": EVICT_LRU, "cost": EVICT_COST}[evict])
         h = ctypes.c_void_p()

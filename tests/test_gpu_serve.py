@@ -74,15 +74,17 @@ def test_served_solves_match_oracle(cat):
         assert st["batches"] <= 60
 
 
-@pytest.mark.parametrize("trans,mixed", [("N", False), ("T", False), ("N", True), ("T", True)])
-def test_alone_equals_in_mix(cat, trans, mixed):
+@pytest.mark.parametrize("trans,mixed,fp64_residual", [("N", False, False), ("T", False, False), ("N", True, False),
+                                                       ("T", True, False), ("N", True, True), ("T", True, True)])
+def test_alone_equals_in_mix(cat, trans, mixed, fp64_residual):
     """A request served alone and the same request served inside a burst (merged with other
-    requests on its matrix, other matrices solving concurrently) return the same bits."""
+    requests on its matrix, other matrices solving concurrently) return the same bits, with the
+    mixed-precision refinement residuals on the tensor cores or (fp64_residual) on FP64 FMAs."""
     i = 1
     n, k = CAT[i][0], CAT[i][1]
     rng = np.random.default_rng(17)
     F = rng.uniform(-1, 1, size=(3, n))
-    with serve.Server(8 << 30, streams=1, max_batch_rhs=64) as S:
+    with serve.Server(8 << 30, streams=1, max_batch_rhs=64, fp64_residual=fp64_residual) as S:
         for j, band in enumerate(cat):
             S.add_matrix(j, band, CAT[j][1], CAT[j][1], pivot=CAT[j][4])
         rid, X_alone = S.submit(i, F, trans=trans, mixed=mixed)
