@@ -152,6 +152,30 @@ template <typename T>
 __device__ void sweep_run(const SweepDesc &D, int ldf, int dofs, T *sm);
 
 // -------------------------------------------------- non-pivoting block LU
+// Row stride of the U12 chunk in shared memory: odd for FP64 (conflict-free column access);
+// a multiple of 4 for FP32, so a row's 16 columns are read as four 16-byte loads.
+template <typename T>
+constexpr int FACTOR_TLD = (sizeof(T) == 4) ? CW + 4 : CW + 1;
+
+// v[0..15] = p[0..15] (p 16-byte aligned for FP32)
+template <typename T>
+__device__ __forceinline__ void load16(const T *p, T (&v)[16]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float4 x = q[i];
+      v[4 * i] = x.x;
+      v[4 * i + 1] = x.y;
+      v[4 * i + 2] = x.z;
+      v[4 * i + 3] = x.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = p[i];
+  }
+}
+
 // Blocked right-looking band LU (no pivoting, diagonal boosting, Sec. 2.3) of one
 // leaf, with the L-sweep of the top spike fused as extra columns: for a middle
 // leaf, Z[:, 0:k] <- L^{-1} [R_top; 0] as the factorization proceeds (the first
@@ -169,7 +193,7 @@ __device__ void factor_leaf(const LeafDev &L, int k, int ldf, T *fb_all, T *dinv
   const bool fuse = L.top_nbr && L.bot_nbr;
   const int kz = fuse ? k : 0;
   const int PLD = NB + k + 1;
-  const int TLD = CW + 1;
+  const int TLD = FACTOR_TLD<T>;
   T *P = smem;                // NB columns x PLD rows, column-major
   T *T12 = smem + NB * PLD;   // NB rows x TLD, row-major
   __shared__ T s_rinv;
@@ -310,9 +334,10 @@ __device__ void factor_leaf(const LeafDev &L, int k, int ldf, T *fb_all, T *dinv
         }
         for (int a = astart; a < jb; ++a) {
           const T l = vi ? P[a * PLD + jb + i] : (T)0;
-          const T *trow = T12 + a * TLD + qq0;
+          T u[16];
+          load16(T12 + a * TLD + qq0, u);
 #pragma unroll
-          for (int q = 0; q < 16; ++q) acc[q] = fma(-l, trow[q], acc[q]);
+          for (int q = 0; q < 16; ++q) acc[q] = fma(-l, u[q], acc[q]);
         }
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
@@ -365,7 +390,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_factor_tasks(const FactorTask *
 
 int launch_factor_tasks(const FactorTask *tasks, int ntasks, int maxk, unsigned *queue, void *stream) {
   if (ntasks <= 0) return 0;
-  size_t smem = sizeof(double) * ((size_t)NB * (NB + maxk + 1) + (size_t)NB * (CW + 1));
+  size_t smem = sizeof(double) * ((size_t)NB * (NB + maxk + 1) + (size_t)NB * FACTOR_TLD<double>);
   if (smem < SWEEP_SMEM) smem = SWEEP_SMEM;
   const int e = smem_at_least((const void *)k_factor_tasks, smem);
   if (e) return e;
@@ -379,7 +404,7 @@ int launch_factor_nopiv(const LeafDev *leaves, int nleaves, int k, int ldf, void
                         const int64_t *zoff, const unsigned long long *amax_bits, double boost_eps,
                         unsigned long long *status, const SweepDesc *sweeps, void *stream, int f32) {
   const size_t es = f32 ? sizeof(float) : sizeof(double);
-  size_t smem = es * ((size_t)NB * (NB + k + 1) + (size_t)NB * (CW + 1));
+  size_t smem = es * ((size_t)NB * (NB + k + 1) + (size_t)NB * (f32 ? FACTOR_TLD<float> : FACTOR_TLD<double>));
   if (smem < SWEEP_SMEM) smem = SWEEP_SMEM;
   cudaError_t e;
   if (f32) {
