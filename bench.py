@@ -36,6 +36,7 @@ sys.path.insert(0, ROOT)
 METRIC = "n=1M k=128 factor+solve GB/s & % roofline vs FP64; serving p50/p99, solves/s"
 # FP64 FMA peak derived from unit counts and clock: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 FMA: 4 x 32 lanes per SM and clock
 FP64_PEAK_NOTE = "derived: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (the recipe's 1.25 TFLOP/s nominal); " \
                  "peak_measured is the library's DFMA probe (spike_measure_fp64_peak) run in this process"
 
@@ -859,6 +860,12 @@ def main():
                    "stages_ms": {key: round(float(np.mean(v)), 3) for key, v in stg.items()}}
             if use_mixed:
                 out["refine_steps_N_T"] = refs[-1]
+                # the FP32 block stage (block LU + fused spike sweeps) against the FP32 FMA peak
+                _, po, pf = spike.plan(n, k, k, p, nrhs_hint=nr, stage_balance=True)
+                bl = method_flops(po, pf, k, nr)["block_lu"] / (out["stages_ms"]["block_lu"] * 1e-3) / 1e12
+                out["block_stage_fp32"] = {"tflops": bl, "frac_fp32_peak": bl / FP32_PEAK_TFLOPS,
+                                           "peak_note": "derived FP32 FMA peak %.2f TFLOP/s (152 SMs x 128 FMA/clk x 2 "
+                                                        "flop x 2.07 GHz)" % FP32_PEAK_TFLOPS}
             return out
 
         mx = variant(m, True)
