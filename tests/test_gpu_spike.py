@@ -335,6 +335,24 @@ def test_pivoting_wide_bands(k, p, n, trans):
     assert metrics.backward_error(pr["band"], k, k, X, pr["F"], trans) <= BERR
 
 
+@pytest.mark.parametrize("kl,ku,p", [(3, 9, 1), (3, 9, 4), (9, 2, 1), (9, 2, 5)])
+@pytest.mark.parametrize("trans", ["N", "T"])
+def test_pivoting_unequal_bandwidths(kl, ku, p, trans):
+    """kl != ku with pivoting: the blocks are padded to k = max(kl, ku) (Sec. 2.1) and the GEPP's
+    candidates beyond kl are zero; against the oracle's banded GEPP (kl, ku as given)."""
+    n = 3000
+    pr = inputs.make_problem(n, kl, ku, 2, seed=40 + kl + p, dist="normal", dd=0.5, keep_sign=True, trans=trans)
+    assert oracle.BandLU(pr["band"], kl, ku).info == 0
+    X, _ = gpu_solve(pr["band"], kl, ku, pr["F"], p, trans, pivot=1)
+    xo, _ = oracle.gbsv(pr["band"], kl, ku, pr["F"], trans)
+    be = metrics.backward_error(pr["band"], kl, ku, X, pr["F"], trans)
+    bo = metrics.backward_error(pr["band"], kl, ku, xo, pr["F"], trans)
+    assert be <= BERR
+    from oracle import condest
+    cond = condest.cond1_estimate(pr["band"], kl, ku)
+    assert metrics.forward_error(X, xo) <= max(1e-12, 20.0 * cond * (be + bo)), (cond, be, bo)
+
+
 def test_pivot_zero_column_reports_singular():
     n, k = 400, 3
     band, _ = inputs.make_band(n, k, k, seed=1, dist="normal", dd=0.5, keep_sign=True)
