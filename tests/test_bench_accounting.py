@@ -67,3 +67,33 @@ def test_two_partitions_do_the_work_of_one_lu():
     assert fsweeps == 0 and ssweeps == 2 * 2 * n * k * m
     f = bench.method_flops(offs, flags, k, m)
     assert f["block_lu"] - lu <= 4 * 2 * k ** 3
+
+
+def _gepp_flops_brute(nl, k):
+    """Flops of an unblocked banded GEPP on nl rows whose U fills to 2k superdiagonals: per column,
+    one multiply per multiplier (the rows below within k) and one FMA (2 flops) per update of (row
+    below, column to the right within 2k) -- counted by walking the columns."""
+    f = 0
+    for j in range(nl):
+        below = min(k, nl - 1 - j)
+        right = min(2 * k, nl - 1 - j)
+        f += below + 2 * below * right
+    return f
+
+
+def test_pivot_block_flops_leading_terms():
+    """bench.pivot_block_flops: the GEPP term is 4k^2 + k flop per row (the brute-force count
+    above, up to the end rows where fewer rows remain below and to the right), middle blocks add
+    2k^2 (L sweep of the top spike, k columns) + 8k^2 (U sweep of both spikes, 2k columns and 2k
+    superdiagonals) per row, and each end block adds 8k^3 for its truncated sweeps."""
+    k = 8
+    offs = np.array([0, 300, 700, 1100, 1400])
+    got = bench.pivot_block_flops(offs, k)
+    sizes = np.diff(offs)
+    want = sum(s * (4 * k * k + k) for s in sizes) + sum(s * 10 * k * k for s in sizes[1:-1]) + 2 * 8 * k ** 3
+    assert got == pytest.approx(want, rel=1e-12)
+    # the GEPP term agrees with the brute-force count to within the end effects (< 2k rows' worth)
+    for s in sizes:
+        brute = _gepp_flops_brute(int(s), k)
+        assert s * (4 * k * k + k) - brute <= 2 * k * (4 * k * k + k)
+        assert brute <= s * (4 * k * k + k)
