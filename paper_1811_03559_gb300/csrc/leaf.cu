@@ -315,6 +315,45 @@ __device__ void factor_leaf(const LeafDev &L, int k, int ldf, T *fb_all, T *dinv
       const int RT = (kc + 31) / 32, CT = (nq + 15) / 16;
       for (int tile = warp; tile < RT * CT; tile += NTHREADS / 32) {
         const int i0 = (tile % RT) * 32, qq0 = (tile / RT) * 16;
+        if (sizeof(T) == 8 && jb == NB && kc == k && (k & 31) == 0 && i0 + 32 == k) {
+          // The last row tile of a full window: the multiplier of row i0 + l in panel column a is
+          // zero for a < l (band edge), a triangle that lanes <-> rows would walk at full cost on
+          // the FP64 pipe.  Lane (p, h) updates row i0 + p over columns a = p..31 and then row
+          // i0 + 31 - p over a = 31 - p..31 (33 steps), on 8 of the tile's 16 columns.  Each entry
+          // gets the same nonzero products in the same order as below.
+          const int p = lane & 15, qb = qq0 + 8 * (lane >> 4);
+          auto row_io = [&](int ii, T *c8, bool store) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const int qq = qb + q, qabs = q0 + qq;
+              if (qq < nq) {
+                T *e = (qabs < kc) ? &fb[(j0 + jb + qabs) * ldf + k + ii - qabs]
+                                   : &Z[(int64_t)(qabs - kc) * nl + j0 + jb + ii];
+                if (store) *e = c8[q];
+                else c8[q] = *e;
+              } else if (!store) {
+                c8[q] = (T)0;
+              }
+            }
+          };
+          T c8[8];
+          row_io(i0 + p, c8, false);
+          for (int v = 0; v < 33; ++v) {
+            const bool first = v < 32 - p;
+            if (v == 32 - p) {
+              row_io(i0 + p, c8, true);
+              row_io(i0 + 31 - p, c8, false);
+            }
+            const int row = first ? i0 + p : i0 + 31 - p;
+            const int a = first ? p + v : v - 1;
+            const T l = P[a * PLD + jb + row];
+            const T *tr = T12 + a * TLD + qb;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) c8[q] = fma(-l, tr[q], c8[q]);
+          }
+          row_io(i0 + 31 - p, c8, true);
+          continue;
+        }
         const int i = i0 + lane;
         const bool vi = i < kc;
         const int qa = q0 + qq0;                       // first absolute column of the tile
@@ -1027,6 +1066,56 @@ __device__ __forceinline__ void window_fma(T *acc, const T *tw, const T *xrow, i
   }
 }
 
+// The 32 window rows of a full window that form a triangle with the block (forward sweeps: window
+// rows [0, 32), block row a couples to window row j only for j >= a; backward: rows [kw - 32, kw),
+// only for j - (kw - 32) <= 31 - a).  Walked with lanes <-> block rows, half the products there are
+// zeros, and on the FP64 pipe a predicated-off or zero product costs as much as a useful one.  Here
+// lane l (p = l mod 16, half h = l / 16) walks block rows p and 31 - p, the 32 - p window rows of
+// the first and then the p + 1 of the second (33 steps in all), over the h-th half of this warp's
+// C columns; the sums then go by shuffles to the lanes that own those rows and are added to acc.
+// Each row's products are summed in window order.
+template <typename T, int C>
+__device__ __forceinline__ void window_tri(T *acc, const T *tw0, const T *x0, int64_t xstep, int64_t xcs,
+                                           int col_base, int lastc, bool fwd) {
+  constexpr int H = C / 2;
+  const int lane = threadIdx.x & 31, p = lane & 15, h = lane >> 4;
+  int64_t coff[H];
+#pragma unroll
+  for (int q = 0; q < H; ++q) coff[q] = (int64_t)min(col_base + h * H + q, lastc) * xcs;
+  T cur[H], sav[H];
+#pragma unroll
+  for (int q = 0; q < H; ++q) {
+    cur[q] = (T)0;
+    sav[q] = (T)0;
+  }
+  for (int v = 0; v < 33; ++v) {
+    const bool first = v < 32 - p;
+    if (v == 32 - p) {
+#pragma unroll
+      for (int q = 0; q < H; ++q) {
+        sav[q] = cur[q];
+        cur[q] = (T)0;
+      }
+    }
+    const int row = first ? p : 31 - p;
+    const int jj = fwd ? (first ? p + v : v - 1) : (first ? v : v - (32 - p));
+    const T t = tw0[jj * NB + row];
+    const T *xr = x0 + jj * xstep;
+#pragma unroll
+    for (int q = 0; q < H; ++q) cur[q] = fma(t, xr[coff[q]], cur[q]);
+  }
+  // row r < 16: sav of lanes r (first half of the columns) and r + 16 (second half);
+  // row r >= 16: cur of lanes 31 - r and 47 - r
+  const int s0 = (lane < 16) ? lane : 31 - lane, s1 = s0 + 16;
+#pragma unroll
+  for (int q = 0; q < H; ++q) {
+    const T a0 = __shfl_sync(FULLMASK, sav[q], s0), a1 = __shfl_sync(FULLMASK, cur[q], s0);
+    const T b0 = __shfl_sync(FULLMASK, sav[q], s1), b1 = __shfl_sync(FULLMASK, cur[q], s1);
+    acc[q] += (lane < 16) ? a0 : a1;
+    acc[H + q] += (lane < 16) ? b0 : b1;
+  }
+}
+
 template <typename T>
 __device__ void sweep_run(const SweepDesc &D, int ldf, int dofs, T *sm) {
   if (D.ncols <= 0 || D.r1 <= D.r0) return;
@@ -1193,7 +1282,31 @@ __device__ void sweep_run(const SweepDesc &D, int ldf, int dofs, T *sm) {
         const int per = (jce - jc0 + nsplit - 1) / nsplit;
         // A predicated-off DFMA still occupies the FP64 pipe, so the accumulation loop is
         // instantiated for the exact column count; edge columns are clamped, not predicated.
+        // FP64, one warp group per column group and a full window in one staged chunk: the window's
+        // triangle rows take window_tri (33 steps over half the columns instead of 32 over all)
+        const bool tri = sizeof(T) == 8 && !fixed && nsplit == 1 && pre && jlo == 0 && jhi == kw && kw >= 32 &&
+                         cpw >= 2;
         auto partial = [&](int sp) {
+          if (tri) {
+            const int m0 = FWD ? 32 : 0, m1 = FWD ? kw : kw - 32, t0 = FWD ? 0 : kw - 32;
+            const T *tm = Tw + (m0 - jc0) * NB + lane, *xm = dx + wrow(m0) * D.x_rs;
+            const T *tt = Tw + (t0 - jc0) * NB, *xt = dx + wrow(t0) * D.x_rs;
+            const int64_t step = D.x_rs;
+            if (cpw <= 2) {
+              window_fma<T, 2>(acc, tm, xm, step, D.x_cs, col_base, lastc, m1 - m0);
+              window_tri<T, 2>(acc, tt, xt, step, D.x_cs, col_base, lastc, FWD);
+            } else if (cpw <= 4) {
+              window_fma<T, 4>(acc, tm, xm, step, D.x_cs, col_base, lastc, m1 - m0);
+              window_tri<T, 4>(acc, tt, xt, step, D.x_cs, col_base, lastc, FWD);
+            } else if (cpw <= 8) {
+              window_fma<T, 8>(acc, tm, xm, step, D.x_cs, col_base, lastc, m1 - m0);
+              window_tri<T, 8>(acc, tt, xt, step, D.x_cs, col_base, lastc, FWD);
+            } else {
+              window_fma<T, 16>(acc, tm, xm, step, D.x_cs, col_base, lastc, m1 - m0);
+              window_tri<T, 16>(acc, tt, xt, step, D.x_cs, col_base, lastc, FWD);
+            }
+            return;
+          }
           const int js = min(jce, jc0 + sp * per), je = min(jce, js + per);
           const T *xw = dx + wrow(js) * D.x_rs;
           const int64_t step = D.x_rs;  // wrow(j+1) = wrow(j) + 1 in both sweep directions
