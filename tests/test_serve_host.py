@@ -303,3 +303,27 @@ def test_unknown_eviction_policy_is_refused():
     cfg = serve.ServerConfig(budget_bytes=1 << 28, streams=1, max_batch_rhs=4, flags=serve.DRYRUN, evict_policy=7)
     h = serve.ctypes.c_void_p()
     assert serve._lib().spike_server_create(serve.ctypes.byref(cfg), serve.ctypes.byref(h)) == -1
+
+
+@pytest.mark.parametrize("fp64_residual", [True, False])
+def test_fp64_residual_mixed_handles_fit_a_smaller_budget(fp64_residual):
+    """SPIKE_SERVE_FP64_RESIDUAL: a mixed-precision factorization is reserved without the digit planes
+    of the tensor-core residual.  A budget between the two sizes admits it with the option and refuses
+    it (SPIKE_ENOMEM) without."""
+    n, k, p = 20_000, 64, 8
+    kw = dict(mixed=True, host_band=True, nrhs_hint=16, stage_balance=True)
+    small = sum(spike.factor_bytes(n, k, k, p, 0, fp64_residual=True, **kw))
+    large = sum(spike.factor_bytes(n, k, k, p, 0, fp64_residual=False, **kw))
+    budget = small + (8 << 20)
+    assert budget < large
+    with serve.Server(budget, streams=1, p=p, dryrun=True, fp64_residual=fp64_residual) as S:
+        S.add_matrix(0, _band(n, k), k, k)
+        rid, X = S.submit(0, np.ones((1, n)), mixed=True)
+        if fp64_residual:
+            S.wait(rid)
+            st = S.stats()
+            assert st["factorizations"] == 1 and st["failed"] == 0 and st["peak_bytes"] <= budget
+        else:
+            with pytest.raises(spike.SpikeError) as e:
+                S.wait(rid)
+            assert e.value.code == spike.SPIKE_ENOMEM
